@@ -1,0 +1,209 @@
+/*
+ * pide2d -- C ABI of a GB300 (sm_103a) solver for two-asset European options
+ * under an exponential Levy model with a bivariate Normal Tempered Stable
+ * (NTS) jump measure, following Moda, in 't Hout, Vanmaele and Benth,
+ * "Numerical valuation of European options under two-asset
+ * infinite-activity exponential Levy models" (arXiv 2511.02700).
+ *
+ * What is computed (paper references in brackets):
+ *   u_t = A_w u - r_w u on a uniform log-price grid   [Sec. 3.1, eq. 3.7]
+ *   weights w_l of the modified midpoint rule          [eq. 3.5]
+ *   artificial diffusion sigma_w sigma_w^T            [eq. 3.3, eq. 3.6]
+ *   jump sum B_w V by zero-padded 2D FFT correlation  [eqs. 3.10-3.17]
+ *   semi-Lagrangian theta-scheme with damping          [eqs. 3.19-3.23]
+ *   fixed-point iteration, stop rule, extrapolation    [eqs. 3.24-3.26]
+ *   in the order of Algorithm 1.
+ *
+ * Grid.  h = 2L/N, s_m = s_center - L + m h, m = 0..N per axis; the nodes
+ * 0 and N carry the far-field value g(s, tau) (Dirichlet); the interior
+ * nodes 1..N-1 are unknowns; ln S0 = s_center is node N/2.  The jump grid
+ * is z_l = (l + 1/2) h, l = -N/2..N/2-1 (z_max^III = L).  Value arrays
+ * exchanged through this ABI are (N+1) x (N+1) doubles, row-major
+ * [m2][m1] (m1 fastest, the vector ordering of eq. 3.7).
+ *
+ * Memory and streams.  The caller owns every byte of device memory: it
+ * passes one workspace of pide2d_workspace_bytes() bytes (device memory,
+ * 256-byte aligned) to pide2d_create(), and the library never allocates
+ * device memory.  All kernels run on the CUDA stream given at creation;
+ * a call returns after the work it queued has finished only where stated.
+ * The handle itself (a small host struct) is allocated by pide2d_create()
+ * and freed by pide2d_destroy().
+ *
+ * Errors.  Every entry point returns a pide2d_status; nothing throws across
+ * the ABI.  A non-OK status leaves a message readable by
+ * pide2d_last_error().  After PIDE2D_ERR_CUDA the handle must only be
+ * destroyed.
+ */
+#ifndef PIDE2D_H
+#define PIDE2D_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PIDE2D_OK = 0,
+    PIDE2D_ERR_ARG = 1,            /* invalid argument or model parameter      */
+    PIDE2D_ERR_CUDA = 2,           /* a CUDA runtime call or launch failed     */
+    PIDE2D_ERR_WORKSPACE = 3,      /* workspace NULL, too small or misaligned  */
+    PIDE2D_ERR_NOT_CONVERGED = 4,  /* fixed-point cap reached (eq. 3.25 unmet) */
+    PIDE2D_ERR_STATE = 5,          /* call not valid in the handle's state     */
+    PIDE2D_ERR_UNSUPPORTED = 6     /* valid but not provided by this build     */
+} pide2d_status;
+
+/* payoff phi of the contract; g(s, tau) is phi with K replaced by K e^{-r tau} */
+enum {
+    PIDE2D_PUT_AVG = 0,     /* max(K - (S1 + S2)/2, 0): the paper's Sec. 4 option  */
+    PIDE2D_CALL_AVG = 1,    /* max((S1 + S2)/2 - K, 0)                            */
+    PIDE2D_PUT_ASSET1 = 2   /* max(K - S1, 0): single-asset reduction (tests)     */
+};
+
+/* arithmetic of the transforms (FFT, DST, interpolation); state, weights,
+ * reductions and the stop test are FP64 in both modes */
+enum { PIDE2D_FP64 = 0, PIDE2D_FP32_BULK = 1 };
+
+/* Spatial grid [Sec. 3.2, uniform in log price]. */
+typedef struct {
+    int n;                /* N: power of two, 8 <= N <= 4096 (FP64: N <= 2048)  */
+    int n_z;              /* N_z: 0 or N/2 (z_max^III = L); other values ERR_ARG */
+    double s_center[2];   /* ln S0 per axis (node N/2)                            */
+    double half_width;    /* L > 0                                                */
+    int sl_order;         /* semi-Lagrangian interpolation: 1 linear, 3 cubic     */
+                          /* (0 selects 3, the paper's choice, Sec. 4)            */
+    int precision;        /* PIDE2D_FP64 or PIDE2D_FP32_BULK                      */
+} pide2d_grid;
+
+/* NTS model in the paper's notation [Sec. 4, Table 2, Appendix A]. */
+typedef struct {
+    double alpha;         /* 0 <= alpha < 1 (tempered-stable index)               */
+    double delta;         /* > 0                                                  */
+    double lambda;        /* > 0                                                  */
+    double eta[2];        /* Brownian drift of the subordinated BM                */
+    double rho[3];        /* rho11, rho12, rho22: positive definite               */
+    double r;             /* riskless rate                                        */
+    double sigma_cov[3];  /* sigma sigma^T of eq. 2.3 (0 in all the paper's runs) */
+} pide2d_model;
+
+typedef struct {
+    int payoff;           /* PIDE2D_PUT_AVG, PIDE2D_CALL_AVG, PIDE2D_PUT_ASSET1   */
+    double strike;        /* K > 0                                                */
+    double maturity;      /* T > 0                                                */
+} pide2d_contract;
+
+/* Optional settings; pass NULL for the defaults in brackets. */
+typedef struct {
+    int kmax;             /* fixed-point iteration cap per time step [100]        */
+    int damping;          /* 1: first step = four theta = 1 steps of dt/4 [1]     */
+} pide2d_options;
+
+typedef struct {
+    int steps_done;       /* time steps completed (damped first step counts 1)    */
+    int fp_iters_total;   /* fixed-point iterations summed over all steps         */
+    int fp_iters_max;     /* largest per-step count                               */
+    double last_resid;    /* last eq. 3.25 quantity of the last step              */
+    double cell_iters;    /* N^2 * (fixed-point iterations + 1) summed: the number */
+                          /* of grid-cell applications of B_w                     */
+} pide2d_stats;
+
+typedef struct pide2d pide2d_t;
+
+/* Bytes of device workspace pide2d_create() needs for this grid.
+ * Errors: ERR_ARG for an invalid grid. */
+pide2d_status pide2d_workspace_bytes(const pide2d_grid* grid, size_t* bytes);
+
+/* Precomputes everything Algorithm 1 lists before time stepping, on the
+ * device: the weights w (eq. 3.5; FP64), sigma_w sigma_w^T, kappa_w, r_w
+ * (eqs. 3.3, 3.6; FP64), the weight spectrum conj(fft(C_1)) (eq. 3.13),
+ * the payoff with cell averaging (eq. 3.18) and B_w V^0.
+ * theta in [0.5, 1], dt > 0 with T/dt an integer (N_t), fp_tol > 0 (eq. 3.25).
+ * workspace: device pointer, >= pide2d_workspace_bytes(), 256-byte aligned,
+ * owned by the caller and used exclusively by this handle until destroy.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * Blocks until the precomputation has finished.  On error *out is NULL.
+ * Errors: ERR_ARG (grid, model -- rho not PD, alpha outside [0,1), delta or
+ * lambda not positive, E[exp L_i(1)] infinite, i.e. lambda <= eta_i + rho_ii/2
+ * by the Table A6 exponent --, contract, theta, dt, tol), ERR_WORKSPACE,
+ * ERR_CUDA. */
+pide2d_status pide2d_create(const pide2d_grid* grid, const pide2d_model* model,
+                            const pide2d_contract* contract, double theta, double dt,
+                            double fp_tol, const pide2d_options* opts,
+                            void* workspace, size_t workspace_bytes, void* cuda_stream,
+                            pide2d_t** out);
+
+/* One time step of Algorithm 1 (the first call performs the four damped
+ * steps when damping is on).  Synchronises with the stream once per
+ * fixed-point iteration to read the eq. 3.25 quantity.
+ * fp_iters / fp_resid: optional outputs (NULL allowed).
+ * Errors: ERR_STATE after the last step, ERR_NOT_CONVERGED (state advanced
+ * with the last iterate), ERR_CUDA. */
+pide2d_status pide2d_step(pide2d_t* h, int* fp_iters, double* fp_resid);
+
+/* Runs the remaining time steps, then writes the value at the valuation
+ * node (N/2, N/2) = S0 to *price (FP64).  values_out: NULL or a pointer
+ * (device or host) to (N+1)^2 doubles receiving V^{N_t} [m2][m1].
+ * stats: optional.  Blocks until done. */
+pide2d_status pide2d_solve(pide2d_t* h, double* price, double* values_out, pide2d_stats* stats);
+
+/* Copies the current value array V^n, (N+1)^2 doubles [m2][m1], to dst
+ * (device or host pointer).  Blocks until the copy has finished. */
+pide2d_status pide2d_get_values(pide2d_t* h, double* dst);
+
+/* Copies the device-computed quadrature data: omega_out (optional) receives
+ * the (N)^2 weights w_{l1 l2} as [l2 + N/2][l1 + N/2] (eq. 3.5); rates_out
+ * (optional, 9 doubles) receives sum w, r_w, kappa_w^1, kappa_w^2,
+ * a11, a12, a22 (sigma_w sigma_w^T), b1, b2 (b = kappa_w - diag(a)/2, the
+ * log-space departure drift).  Pointers may be device or host. */
+pide2d_status pide2d_get_weights(pide2d_t* h, double* omega_out, double* rates_out);
+
+/* The jump sum (B_w U)(s_m) at the interior nodes for a caller field:
+ * U is (N+1)^2 doubles [m2][m1] (device or host) whose interior nodes are
+ * used; every node outside the interior takes g(s, tau) when far_field is
+ * 1, or 0 when it is 0.  out (device or host, (N+1)^2 doubles) receives B_w U
+ * at the interior nodes; its other entries are left unchanged.  Runs the
+ * same FFT kernels as the time stepping (eq. 3.17).  Blocks. */
+pide2d_status pide2d_apply_jump(pide2d_t* h, const double* U, double tau, int far_field,
+                                double* out);
+
+/* Kernel classes of the time loop, for pide2d_profile_read(). */
+enum {
+    PIDE2D_KERNEL_PREP = 0,            /* W = T_SL[...] and Y^{n,0} (Algorithm 1 steps 2-3)   */
+    PIDE2D_KERNEL_ROW_FORWARD_FULL,    /* row pass of B_w Y^{n,0} (with far field)            */
+    PIDE2D_KERNEL_ROW_FORWARD_INCR,    /* row pass of B_w of a fixed-point increment           */
+    PIDE2D_KERNEL_COL_FULL,            /* column pass (FFT, product, inverse FFT), full rows   */
+    PIDE2D_KERNEL_COL_INCR,            /* column pass of an increment                          */
+    PIDE2D_KERNEL_ROW_INVERSE_FULL,    /* inverse row pass + first residual + row DST          */
+    PIDE2D_KERNEL_ROW_INVERSE_INCR,    /* inverse row pass + residual update + row DST         */
+    PIDE2D_KERNEL_DST_COL,             /* column DST, eigenvalue division, column DST          */
+    PIDE2D_KERNEL_DST_ROW,             /* row DST back, state update, eq. 3.25 maximum         */
+    PIDE2D_KERNEL_CLASSES = 9
+};
+
+typedef struct {
+    int launches[16];                  /* per class, since profiling was enabled               */
+    double ms[16];                     /* summed CUDA-event durations per class                */
+} pide2d_kernel_times;
+
+/* Tracing: enable != 0 brackets every later time-loop kernel launch with a
+ * pair of CUDA events on the handle's stream and clears earlier records;
+ * enable == 0 stops recording.  The events are host-side resources created
+ * on demand and kept until destroy (no device memory).  Errors: ERR_CUDA. */
+pide2d_status pide2d_profile(pide2d_t* h, int enable);
+
+/* Waits for the stream, then sums the recorded event pairs per kernel class
+ * into *out.  Errors: ERR_ARG (out NULL), ERR_CUDA. */
+pide2d_status pide2d_profile_read(pide2d_t* h, pide2d_kernel_times* out);
+
+/* Human-readable message for the last non-OK status on this handle (or of
+ * the last failed pide2d_create when h is NULL).  Never NULL. */
+const char* pide2d_last_error(const pide2d_t* h);
+
+/* Frees the handle (not the workspace).  NULL is ignored. */
+void pide2d_destroy(pide2d_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIDE2D_H */

@@ -1,0 +1,240 @@
+"""Thin ctypes binding of the pide2d C ABI (include/pide2d.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  The functions keep the C names; ``Solver`` is a convenience
+wrapper that takes its device workspace from PyTorch and runs on a PyTorch
+stream.  If the library has not been built, ``lib()`` raises -- there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from ctypes import POINTER, byref, c_double, c_int, c_size_t, c_void_p
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpide2d.so")
+
+PIDE2D_OK = 0
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_WORKSPACE", 4: "ERR_NOT_CONVERGED",
+          5: "ERR_STATE", 6: "ERR_UNSUPPORTED"}
+PIDE2D_PUT_AVG, PIDE2D_CALL_AVG, PIDE2D_PUT_ASSET1 = 0, 1, 2
+PIDE2D_FP64, PIDE2D_FP32_BULK = 0, 1
+
+
+class pide2d_grid(ctypes.Structure):
+    _fields_ = [("n", c_int), ("n_z", c_int), ("s_center", c_double * 2), ("half_width", c_double),
+                ("sl_order", c_int), ("precision", c_int)]
+
+
+class pide2d_model(ctypes.Structure):
+    _fields_ = [("alpha", c_double), ("delta", c_double), ("lambda_", c_double), ("eta", c_double * 2),
+                ("rho", c_double * 3), ("r", c_double), ("sigma_cov", c_double * 3)]
+
+
+class pide2d_contract(ctypes.Structure):
+    _fields_ = [("payoff", c_int), ("strike", c_double), ("maturity", c_double)]
+
+
+class pide2d_options(ctypes.Structure):
+    _fields_ = [("kmax", c_int), ("damping", c_int)]
+
+
+class pide2d_stats(ctypes.Structure):
+    _fields_ = [("steps_done", c_int), ("fp_iters_total", c_int), ("fp_iters_max", c_int),
+                ("last_resid", c_double), ("cell_iters", c_double)]
+
+
+class PideError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_LIB = None
+
+
+def lib():
+    """The loaded CUDA library (raises if it was not built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"pide2d CUDA library missing ({LIB_PATH}); "
+                               "build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        L.pide2d_workspace_bytes.argtypes = [POINTER(pide2d_grid), POINTER(c_size_t)]
+        L.pide2d_create.argtypes = [POINTER(pide2d_grid), POINTER(pide2d_model), POINTER(pide2d_contract),
+                                    c_double, c_double, c_double, POINTER(pide2d_options), c_void_p, c_size_t,
+                                    c_void_p, POINTER(c_void_p)]
+        L.pide2d_step.argtypes = [c_void_p, POINTER(c_int), POINTER(c_double)]
+        L.pide2d_solve.argtypes = [c_void_p, POINTER(c_double), c_void_p, POINTER(pide2d_stats)]
+        L.pide2d_get_values.argtypes = [c_void_p, c_void_p]
+        L.pide2d_get_weights.argtypes = [c_void_p, c_void_p, c_void_p]
+        L.pide2d_apply_jump.argtypes = [c_void_p, c_void_p, c_double, c_int, c_void_p]
+        L.pide2d_last_error.argtypes = [c_void_p]
+        L.pide2d_last_error.restype = ctypes.c_char_p
+        L.pide2d_destroy.argtypes = [c_void_p]
+        L.pide2d_destroy.restype = None
+        for name in ("pide2d_workspace_bytes", "pide2d_create", "pide2d_step", "pide2d_solve",
+                     "pide2d_get_values", "pide2d_get_weights", "pide2d_apply_jump"):
+            getattr(L, name).restype = c_int
+        _LIB = L
+    return _LIB
+
+
+def _check(status, handle=None):
+    if status != PIDE2D_OK and status != 4:
+        raise PideError(status, lib().pide2d_last_error(handle).decode())
+    return status
+
+
+# ------------------------------------------------------------------ C names
+def pide2d_workspace_bytes(grid: pide2d_grid) -> int:
+    n = c_size_t(0)
+    _check(lib().pide2d_workspace_bytes(byref(grid), byref(n)))
+    return n.value
+
+
+def pide2d_create(grid, model, contract, theta, dt, fp_tol, opts, workspace, workspace_bytes, stream):
+    h = c_void_p(0)
+    _check(lib().pide2d_create(byref(grid), byref(model), byref(contract), theta, dt, fp_tol,
+                               byref(opts) if opts is not None else None, c_void_p(workspace),
+                               workspace_bytes, c_void_p(stream), byref(h)))
+    return h
+
+
+def pide2d_step(h):
+    k = c_int(0)
+    r = c_double(0.0)
+    st = _check(lib().pide2d_step(h, byref(k), byref(r)), h)
+    return k.value, r.value, st
+
+
+def pide2d_solve(h, values_out_ptr=None):
+    price = c_double(0.0)
+    stats = pide2d_stats()
+    st = _check(lib().pide2d_solve(h, byref(price), c_void_p(values_out_ptr) if values_out_ptr else None,
+                                   byref(stats)), h)
+    return price.value, stats, st
+
+
+def pide2d_get_values(h, dst_ptr):
+    _check(lib().pide2d_get_values(h, c_void_p(dst_ptr)), h)
+
+
+def pide2d_get_weights(h, omega_ptr, rates_ptr):
+    _check(lib().pide2d_get_weights(h, c_void_p(omega_ptr) if omega_ptr else None,
+                                    c_void_p(rates_ptr) if rates_ptr else None), h)
+
+
+def pide2d_apply_jump(h, U_ptr, tau, far_field, out_ptr):
+    _check(lib().pide2d_apply_jump(h, c_void_p(U_ptr), tau, int(far_field), c_void_p(out_ptr)), h)
+
+
+def pide2d_last_error(h=None) -> str:
+    return lib().pide2d_last_error(h).decode()
+
+
+def pide2d_destroy(h):
+    lib().pide2d_destroy(h)
+
+
+# ------------------------------------------------------------------ helpers
+def make_grid(n, precision=PIDE2D_FP64, sl_order=3, s0=(100.0, 100.0), half_width=2.5):
+    g = pide2d_grid()
+    g.n = n
+    g.n_z = 0
+    g.s_center[0] = math.log(s0[0])
+    g.s_center[1] = math.log(s0[1])
+    g.half_width = half_width
+    g.sl_order = sl_order
+    g.precision = precision
+    return g
+
+
+def make_model(alpha, delta, lam, eta, rho, r, sigma_cov=(0.0, 0.0, 0.0)):
+    m = pide2d_model()
+    m.alpha, m.delta, m.lambda_ = alpha, delta, lam
+    m.eta[0], m.eta[1] = eta
+    m.rho[0], m.rho[1], m.rho[2] = rho
+    m.r = r
+    m.sigma_cov[0], m.sigma_cov[1], m.sigma_cov[2] = sigma_cov
+    return m
+
+
+def model_from_subordinated_bm(alpha, kappa, beta, sigma, corr, r):
+    """Unit-mean tempered-stable subordinator with variance kappa (Table A5:
+    lambda = (1-alpha)/kappa, delta = lambda^(1-alpha)/Gamma(1-alpha)),
+    Brownian drift beta and covariance [[s1^2, c s1 s2], [c s1 s2, s2^2]]."""
+    lam = (1.0 - alpha) / kappa
+    delta = lam ** (1.0 - alpha) / math.gamma(1.0 - alpha)
+    s1, s2 = sigma
+    return make_model(alpha, delta, lam, beta, (s1 * s1, corr * s1 * s2, s2 * s2), r)
+
+
+def make_contract(payoff=PIDE2D_PUT_AVG, strike=100.0, maturity=1.0):
+    c = pide2d_contract()
+    c.payoff, c.strike, c.maturity = payoff, strike, maturity
+    return c
+
+
+class Solver:
+    """One pricing: device workspace from PyTorch, kernels on a PyTorch stream."""
+
+    def __init__(self, grid, model, contract, n_steps, theta=0.5, tol=1e-10, kmax=100, damping=True,
+                 device="cuda", stream=None):
+        import torch
+        self.torch = torch
+        self.grid = grid
+        self.n = grid.n
+        nbytes = pide2d_workspace_bytes(grid)
+        self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        base = (self.ws.data_ptr() + 255) & ~255
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        opts = pide2d_options()
+        opts.kmax, opts.damping = kmax, 1 if damping else 0
+        self.h = pide2d_create(grid, model, contract, theta, contract.maturity / n_steps, tol, opts, base,
+                               nbytes, self.stream.cuda_stream)
+        self.workspace_bytes = nbytes
+
+    def step(self):
+        return pide2d_step(self.h)
+
+    def solve(self, values=False):
+        torch = self.torch
+        out = None
+        if values:
+            out = torch.empty((self.n + 1, self.n + 1), dtype=torch.float64, device=self.ws.device)
+        price, stats, status = pide2d_solve(self.h, out.data_ptr() if out is not None else None)
+        return price, out, stats, status
+
+    def values(self):
+        out = self.torch.empty((self.n + 1, self.n + 1), dtype=self.torch.float64, device=self.ws.device)
+        pide2d_get_values(self.h, out.data_ptr())
+        return out
+
+    def weights(self):
+        torch = self.torch
+        om = torch.empty((self.n, self.n), dtype=torch.float64, device=self.ws.device)
+        rates = torch.empty(9, dtype=torch.float64)
+        pide2d_get_weights(self.h, om.data_ptr(), rates.data_ptr())
+        return om, rates
+
+    def apply_jump(self, U, tau, far_field=True):
+        torch = self.torch
+        U = U.to(device=self.ws.device, dtype=torch.float64).contiguous()
+        out = torch.zeros_like(U)
+        pide2d_apply_jump(self.h, U.data_ptr(), tau, far_field, out.data_ptr())
+        return out
+
+    def close(self):
+        if self.h:
+            pide2d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

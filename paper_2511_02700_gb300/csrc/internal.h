@@ -1,0 +1,153 @@
+// Host-side interface between the pide2d translation units: argument blocks
+// of the kernels and their launchers.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace pide {
+
+// State element: FP64 mode keeps double; FP32-bulk mode keeps a double-float
+// pair (hi, lo) in a float2 so every state update runs on FP32 units.
+template <typename R> struct state_t;
+template <> struct state_t<float> { using type = float2; };
+template <> struct state_t<double> { using type = double; };
+template <typename R> using St = typename state_t<R>::type;
+
+// spectrum column groups: 16 bytes of complex values per (group, row)
+template <typename R> __host__ __device__ constexpr int cgroup() { return 16 / (2 * (int)sizeof(R)); }
+// DST column groups: 16 bytes of real values per (group, row)
+template <typename R> __host__ __device__ constexpr int rgroup() { return 16 / (int)sizeof(R); }
+
+enum FwdMode { FWD_FULL = 0, FWD_FULL0 = 1, FWD_INCR = 2, FWD_WEIGHTS = 3 };
+enum ColMode { COL_FULL = 0, COL_INCR = 1 };
+enum InvMode { INV_FULL = 0, INV_INCR = 1, INV_OUT = 2 };
+
+struct Geometry {
+    int N, P;          // grid and padded transform length (P = 2N)
+    int rows;          // rows of the spectrum buffer (P + 2)
+    int ng;            // spectrum column groups
+    int nge;           // DST column groups (N / rgroup)
+    int ldS;           // pitch (elements) of state fields, (N+1) rows
+    int ldR;           // pitch (elements) of R fields, (N+1) rows
+    int eoff;          // index offset of node m in the exp tables (N/2 + 3)
+};
+
+template <typename R> struct FwdArgs {
+    Geometry g;
+    int mode;
+    const St<R>* Y;          // FULL/FULL0: field whose interior is transformed
+    const R* D;              // INCR: increment field (ring zero)
+    const double* omega;     // WEIGHTS: N x N weights [l2][l1]
+    const R* E1; const R* E2;// e^{s_m} tables (transform precision)
+    R Kd;                    // K e^{-r tau} for the far field
+    int payoff;
+    void* S;                 // spectrum out (cpx<R>, or cpx<double> for WEIGHTS)
+    int pair0, npairs;       // row pairs (rho = 2 (pair0 + p), +1)
+    const void* tw;          // twiddles of the transform precision
+};
+
+template <typename R> struct ColArgs {
+    Geometry g;
+    int mode;
+    void* S;                 // cpx<R> spectrum, in place
+    const void* Wh;          // cpx<R> conj(w^)/P^2, layout [group][k2][c]
+    int rlo, rhi;            // spectrum rows holding data
+    const void* tw;
+};
+
+template <typename R> struct InvArgs {
+    Geometry g;
+    int mode;
+    int do_resid;
+    const void* S;
+    St<R>* BY;               // FULL: set, INCR: accumulate
+    double* out;             // OUT: plain FP64 result field (pitch ldS)
+    const St<R>* Y;          // FULL: Y^0 (with ring)
+    const St<R>* W;          // FULL: W
+    R* r;                    // residual field (R)
+    const R* D;              // INCR: increment field
+    R htt, cid, d11, d22, d12, rw;   // h_t theta, 1 + h_t theta r_w, a11/(2h^2), a22/(2h^2), a12/(4h^2), r_w
+    R* E;                    // DST rows output
+    const void* tw;
+};
+
+template <typename R> struct DstColArgs {
+    Geometry g;
+    R* E;
+    const R* sin2;           // sin^2(pi k / (2N)), k = 0..N
+    double c0, c1, c2, scale;// lambda = c0 + c1 sin2[k1] + c2 sin2[k2]; scale = (2/N)^2
+    const void* tw;
+};
+
+template <typename R> struct DstRowArgs {
+    Geometry g;
+    const R* E;
+    St<R>* Y;
+    R* D;                    // increment out (interior)
+    void* resid;             // R-typed max |D| / max(1, |Y|) as unsigned bits
+    const void* tw;
+};
+
+template <typename R> struct PrepArgs {
+    Geometry g;
+    const St<R>* V[4];       // history, latest first
+    int hcount;
+    const St<R>* BV;
+    St<R>* W;
+    St<R>* Y;
+    R htm;                   // h_t (1 - theta)
+    R rw, d11, d22, d12;     // r_w and D coefficients
+    int o1, o2, nt;          // SL: first tap offsets, taps per axis (2 or 4)
+    R w1[4], w2[4];          // SL weights per axis
+    const double* E1d; const double* E2d;   // e^{s} in FP64
+    double Kd_prev, Kd_now;  // K e^{-r tau_{n-1}}, K e^{-r tau_n}
+    int payoff;
+};
+
+// launchers (sweep.cu), explicitly instantiated for float and double
+template <typename R> cudaError_t launch_row_forward(const FwdArgs<R>& a, cudaStream_t s);
+template <typename R> cudaError_t launch_col(const ColArgs<R>& a, cudaStream_t s);
+template <typename R> cudaError_t launch_row_inverse(const InvArgs<R>& a, cudaStream_t s);
+template <typename R> cudaError_t launch_dst_col(const DstColArgs<R>& a, cudaStream_t s);
+template <typename R> cudaError_t launch_dst_row(const DstRowArgs<R>& a, cudaStream_t s);
+template <typename R> cudaError_t launch_prep(const PrepArgs<R>& a, cudaStream_t s);
+// omega-hat: forward column FFT of the FP64 row spectra, written as cpx<RO>
+template <typename RO> cudaError_t launch_weights_col(const Geometry& g, const void* Sd, void* Wh,
+                                                       const void* twd, cudaStream_t s);
+template <typename R> cudaError_t launch_state_from_double(const Geometry& g, const double* src, int ld_src,
+                                                          St<R>* dst, cudaStream_t s);
+template <typename R> cudaError_t launch_state_to_double(const Geometry& g, const St<R>* src, double* dst,
+                                                        int ld_dst, cudaStream_t s);
+
+// precompute (precompute.cu)
+struct LevyParams {
+    double alpha, nu, c1, logpref, Ri11, Ri12, Ri22, b1, b2;  // l(z) pieces
+    double pref0;            // delta / (pi sqrt(det rho))
+    double gamma_nu;         // Gamma(nu)
+};
+struct WeightJob {
+    int N;
+    double h;
+    int M2;                  // z_II / h
+    const double* gl_near_x; const double* gl_near_w; int n_near;
+    const double* gl_far_x; const double* gl_far_w; int n_far;
+};
+cudaError_t launch_weights(const LevyParams& L, const WeightJob& j, double* omega, double* partials,
+                           int* nblocks, cudaStream_t s);
+cudaError_t launch_moment(const LevyParams& L, double H, const double* glx, const double* glw, int ngl,
+                          double tsh, double* out3, cudaStream_t s);
+cudaError_t launch_finalize(const double* partials, int nblocks, const double* moment, double r,
+                            const double* sigma_cov, double* params, cudaStream_t s);
+cudaError_t launch_tables(int N, double s_lo1, double s_lo2, double h, double* E1d, double* E2d,
+                          float* E1f, float* E2f, double* sin2, cudaStream_t s);
+template <typename R> cudaError_t launch_twiddles(int P, void* tw, cudaStream_t s);
+template <typename R> cudaError_t launch_payoff(const Geometry& g, const double* E1d, const double* E2d,
+                                               double s_lo1, double s_lo2, double h, double K, int payoff,
+                                               const double* glx, const double* glw, int ngl,
+                                               St<R>* V, cudaStream_t s);
+template <typename R> cudaError_t launch_ring(const Geometry& g, const double* E1d, const double* E2d,
+                                             double Kd, int payoff, St<R>* Y, cudaStream_t s);
+
+}  // namespace pide

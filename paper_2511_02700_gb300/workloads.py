@@ -1,0 +1,78 @@
+"""Seeded synthetic workloads: the input generators shared by the tests, the
+benchmark and the oracle checks.  Only parameters and random draws live
+here -- none of the method's arithmetic.
+
+The five workloads restate the benchmark configurations of the build: a
+put on the average of two assets, K = 100, S0 = (100, 100), r = 0.03,
+bivariate NTS jumps from a unit-mean tempered-stable subordinator with
+variance kappa, Brownian drift beta, volatilities sigma and correlation corr,
+on a uniform log grid ln 100 +- 2.5 with N nodes per axis.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    n: int
+    steps: int
+    alpha: float
+    kappa: float = 0.5
+    beta: tuple = (-0.10, -0.05)
+    sigma: tuple = (0.20, 0.25)
+    corr: float = 0.3
+    r: float = 0.03
+    strike: float = 100.0
+    maturity: float = 1.0
+    theta: float = 0.5
+    tol: float = 1e-10
+    precision: str = "fp64"        # "fp64" or "fp32"
+    sl_order: int = 3
+    half_width: float = 2.5
+
+
+# plain FP64 pricing, 128^2 grid, 32 steps, tol 1e-10
+PLAIN_FP64_128 = Workload("plain_fp64_128", n=128, steps=32, alpha=0.25, tol=1e-10, precision="fp64")
+
+
+def convergence_sweep(precision: str):
+    """alpha in {0.25, 0.5, 0.75} x N in {256, 512, 1024}, steps N/4, tol 1e-8."""
+    return [Workload(f"sweep_a{a}_n{n}_{precision}", n=n, steps=n // 4, alpha=a, tol=1e-8,
+                     precision=precision)
+            for a in (0.25, 0.5, 0.75) for n in (256, 512, 1024)]
+
+
+# large single solve: 4096^2 grid (8192^2 padded transforms), alpha 0.5, 1024 steps, tol 1e-7
+LARGE_FP32_4096 = Workload("large_fp32_4096", n=4096, steps=1024, alpha=0.5, tol=1e-7, precision="fp32")
+
+
+def batch_draw(count: int = 512, seed: int = 2511027):
+    """Independent pricings with seed-drawn parameters (uniform ranges)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(count):
+        a = float(rng.uniform(0.1, 0.45))
+        kap = float(rng.uniform(0.2, 1.0))
+        s = (float(rng.uniform(0.1, 0.4)), float(rng.uniform(0.1, 0.4)))
+        c = float(rng.uniform(-0.6, 0.6))
+        b = (float(rng.uniform(-0.2, 0.2)), float(rng.uniform(-0.2, 0.2)))
+        K = float(rng.uniform(80.0, 120.0))
+        T = float(rng.uniform(0.1, 2.0))
+        n = int(rng.choice([128, 256, 512]))
+        out.append(Workload(f"batch_{i}", n=n, steps=n // 4, alpha=a, kappa=kap, beta=b, sigma=s, corr=c,
+                            strike=K, maturity=T, precision="fp32"))
+    return out
+
+
+def random_field(n: int, seed: int, lo: float = 0.0, hi: float = 100.0) -> np.ndarray:
+    """(n+1) x (n+1) FP64 field, uniform in [lo, hi], for operator checks."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.uniform(lo, hi, size=(n + 1, n + 1))
+
+
+def with_(w: Workload, **kw) -> Workload:
+    return replace(w, **kw)

@@ -38,3 +38,22 @@ def paper_sets():
                      rho=(v[5], v[6], v[7]), r=v[8])
         out[name] = (m, Contract(PUT_AVG, v[10], v[9]))
     return out
+
+
+def oracle_inputs(w):
+    """Oracle model/grid/contract for a workloads.Workload."""
+    import oracle as O
+    m = O.model_from_subordinated_bm(w.alpha, w.kappa, w.beta, w.sigma, w.corr, w.r)
+    g = O.Grid(w.n, half_width=w.half_width)
+    c = O.Contract(O.PUT_AVG, w.strike, w.maturity)
+    return m, g, c
+
+
+def gpu_solver(w, payoff=0, **kw):
+    """CUDA-path Solver (through the C ABI) for a workloads.Workload."""
+    from paper_2511_02700_gb300 import binding as B
+    prec = B.PIDE2D_FP64 if w.precision == "fp64" else B.PIDE2D_FP32_BULK
+    grid = B.make_grid(w.n, prec, w.sl_order, half_width=w.half_width)
+    model = B.model_from_subordinated_bm(w.alpha, w.kappa, w.beta, w.sigma, w.corr, w.r)
+    contract = B.make_contract(payoff, w.strike, w.maturity)
+    return B.Solver(grid, model, contract, w.steps, theta=w.theta, tol=w.tol, **kw)

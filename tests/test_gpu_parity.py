@@ -1,0 +1,140 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64
+CPU oracle on the same seeded inputs.
+
+Tolerances: FP64 mode 1e-10 relative (at the valuation node and in
+max-norm over the region of interest, relative to the max-norm of the
+oracle there); FP32-bulk mode 1e-5 relative.  Operator checks (weights,
+jump sum) use bounds derived from the arithmetic: FP64 quadrature of the
+weights agrees to ~1e-13, the FP64 FFT correlation to ~1e-13 of
+sum(w) max|U|, the FP32 one to ~1e-6 of it.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from conftest import gpu_solver, oracle_inputs
+from paper_2511_02700_gb300.workloads import PLAIN_FP64_128, Workload, random_field, with_
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import oracle as O  # noqa: E402
+
+
+def roi_mask(n, half_width=2.5):
+    s = math.log(100.0) - half_width + np.arange(n + 1) * (2 * half_width / n)
+    S = np.exp(s)
+    m1 = (S <= 300.0)
+    M = np.outer(m1, m1)
+    M[0, :] = M[-1, :] = M[:, 0] = M[:, -1] = False
+    return M
+
+
+@pytest.mark.parametrize("n,alpha", [(16, 0.25), (64, 0.5), (128, 0.25), (128, 0.75)])
+def test_weights_and_rates_match_oracle(n, alpha):
+    w = Workload("w", n=n, steps=n // 4, alpha=alpha)
+    s = gpu_solver(w)
+    om, rates = s.weights()
+    om = om.cpu().numpy()
+    m, g, _ = oracle_inputs(w)
+    pre = O.precompute(m, g)
+    nz = pre.omega != 0
+    assert np.array_equal(om != 0, nz)
+    assert np.max(np.abs(om[nz] / pre.omega[nz] - 1.0)) < 1e-11
+    ref = [pre.sum_w, pre.r_w, pre.kappa_w[0], pre.kappa_w[1], pre.a[0, 0], pre.a[0, 1], pre.a[1, 1],
+           pre.b[0], pre.b[1]]
+    r = rates.numpy()
+    for a, b in zip(r, ref):
+        assert abs(a - b) <= 1e-11 * max(abs(b), 1e-3), (r, ref)
+
+
+@pytest.mark.parametrize("precision,n", [("fp64", 8), ("fp64", 16), ("fp64", 64), ("fp64", 256),
+                                         ("fp32", 16), ("fp32", 128), ("fp32", 512)])
+@pytest.mark.parametrize("far", [1, 0])
+def test_jump_operator_matches_oracle(precision, n, far):
+    w = Workload("j", n=n, steps=4, alpha=0.5, precision=precision)
+    s = gpu_solver(w)
+    U = random_field(n, seed=n + 7 * far)
+    tau = 0.37
+    B_gpu = s.apply_jump(torch.from_numpy(U), tau, far_field=bool(far)).cpu().numpy()[1:-1, 1:-1]
+    m, g, c = oracle_inputs(w)
+    pre = O.precompute(m, g)
+    Ue = O.extend(g, c, m.r, U[1:-1, 1:-1], tau, far=bool(far))
+    B_ref = O.jump_fft(g, pre.omega, Ue)
+    scale = pre.sum_w * np.abs(Ue).max()
+    tol = 1e-13 if precision == "fp64" else 2e-6
+    err = np.abs(B_gpu - B_ref).max()
+    assert err <= tol * scale, (err, scale)
+
+
+@pytest.mark.parametrize("n,alpha,sl", [(16, 0.25, 3), (16, 0.75, 1), (32, 0.5, 3), (64, 0.25, 1),
+                                        (64, 0.75, 3)])
+def test_fp64_solve_matches_oracle(n, alpha, sl):
+    w = Workload("s", n=n, steps=max(4, n // 4), alpha=alpha, tol=1e-13, sl_order=sl)
+    s = gpu_solver(w)
+    price, V, stats, st = s.solve(values=True)
+    assert st == 0
+    V = V.cpu().numpy()
+    m, g, c = oracle_inputs(w)
+    ref = O.Scheme(m, g, c, w.steps, theta=w.theta, tol=w.tol, sl_order=sl).solve()
+    scale = np.abs(ref.V).max()
+    assert np.abs(V - ref.V).max() <= 1e-10 * scale
+    assert abs(price - ref.price) <= 1e-10 * abs(ref.price)
+
+
+def test_plain_fp64_128_workload():
+    """The 128^2, 32-step, tol 1e-10 FP64 workload: price and ROI max-norm."""
+    w = PLAIN_FP64_128
+    s = gpu_solver(w)
+    price, V, stats, st = s.solve(values=True)
+    V = V.cpu().numpy()
+    m, g, c = oracle_inputs(w)
+    ref = O.Scheme(m, g, c, w.steps, theta=w.theta, tol=w.tol, sl_order=w.sl_order).solve()
+    roi = roi_mask(w.n)
+    scale = np.abs(ref.V[roi]).max()
+    assert abs(price - ref.price) <= 1e-10 * abs(ref.price), (price, ref.price)
+    assert np.abs(V - ref.V)[roi].max() <= 1e-10 * scale
+    assert stats.steps_done == w.steps
+
+
+@pytest.mark.parametrize("n,alpha", [(64, 0.25), (128, 0.5)])
+def test_fp32_bulk_solve_matches_oracle(n, alpha):
+    w = Workload("f", n=n, steps=n // 4, alpha=alpha, tol=1e-10, precision="fp32")
+    s = gpu_solver(w)
+    price, V, stats, st = s.solve(values=True)
+    V = V.cpu().numpy()
+    m, g, c = oracle_inputs(w)
+    ref = O.Scheme(m, g, c, w.steps, theta=w.theta, tol=w.tol, sl_order=w.sl_order).solve()
+    roi = roi_mask(n)
+    scale = np.abs(ref.V[roi]).max()
+    assert abs(price - ref.price) <= 1e-5 * abs(ref.price), (price, ref.price)
+    assert np.abs(V - ref.V)[roi].max() <= 1e-5 * scale
+
+
+@pytest.mark.parametrize("payoff", [1, 2])
+def test_other_payoffs_fp64(payoff):
+    w = Workload("p", n=32, steps=8, alpha=0.5, tol=1e-13)
+    s = gpu_solver(w, payoff=payoff)
+    price, V, stats, st = s.solve(values=True)
+    m, g, _ = oracle_inputs(w)
+    c = O.Contract(payoff, w.strike, w.maturity)
+    ref = O.Scheme(m, g, c, w.steps, tol=w.tol, sl_order=w.sl_order).solve()
+    assert np.abs(V.cpu().numpy() - ref.V).max() <= 1e-10 * np.abs(ref.V).max()
+
+
+def test_step_api_and_state_errors():
+    from paper_2511_02700_gb300 import binding as B
+    w = Workload("st", n=16, steps=3, alpha=0.25, tol=1e-12)
+    s = gpu_solver(w)
+    k1, r1, st1 = s.step()      # damped first step: four substeps
+    assert st1 == 0 and k1 >= 4 and r1 < w.tol
+    for _ in range(2):
+        k, r, st = s.step()
+        assert st == 0 and 1 <= k < 100
+    with pytest.raises(B.PideError) as e:
+        s.step()
+    assert "ERR_STATE" in str(e.value)
