@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Benchmark of the pide2d time step on one GB300.
+
+Workload (default): the large single solve -- put on the average, 4096^2
+log grid (8192^2 padded transforms), NTS with alpha = 0.5, kappa = 0.5,
+1024 time steps, fixed-point tol 1e-7, FP32-bulk transforms.  A "step" is
+one theta time step of Algorithm 1 (SL preparation, one full B_w sweep and
+the fixed-point loop, each iteration one B_w sweep plus the DST diffusion
+solve).  Unit of work: one cell-iteration = one grid cell (N^2 per sweep)
+through one application of B_w; a step with k fixed-point iterations
+processes N^2 (k + 1) of them.
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle instead
+(on a bounded sample of the same workload).  Under torchrun (N > 1) every
+rank runs an independent replica (the solve does not shard); value is the
+sum of the units over the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-iterations/s of 2D PIDE step vs FP64 plain at ≤1e-5 error; %HBM roofline"
+UNIT = "cell-iterations/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def args_parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=4096, help="grid size (default: the large 4096^2 workload)")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(n):
+    from paper_2511_02700_gb300.workloads import LARGE_FP32_4096, with_
+    w = LARGE_FP32_4096
+    if n != w.n:
+        w = with_(w, name=f"large_fp32_{n}", n=n, steps=n // 4)
+    return w
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        sm = [c for c, _, _ in rows]
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(m for _, m, _ in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- roofline
+def algorithmic_bytes(cls, n, hcount=4):
+    """Algorithmic HBM bytes of one launch of a kernel class, FP32-bulk mode
+    (complex spectra 8 B, state 8 B double-float, R fields 4 B)."""
+    P = 2 * n
+    H = P // 2 + 1
+    cells = n * n
+    spec_full = (P + 2) * H * 8
+    spec_n = n * H * 8
+    wh = P * H * 8
+    return {
+        0: (8 * hcount + 8 + 16) * cells,                      # prep: V history, BV -> W, Y
+        1: 8 * cells + spec_full,                              # row forward full: Y -> S
+        2: 4 * cells + spec_n,                                 # row forward incr: D -> S
+        3: spec_full + wh + spec_n,                            # column pass full
+        4: spec_n + wh + spec_n,                               # column pass incr
+        5: spec_n + 8 * cells + 16 * cells + 4 * cells + 4 * cells,   # inverse full: S, BY, W+Y, r, E
+        6: spec_n + 16 * cells + 8 * cells + 4 * cells + 4 * cells,   # inverse incr: S, BY, r, D, E
+        7: 8 * cells,                                          # column DST
+        8: 4 * cells + 16 * cells + 4 * cells,                 # row DST back: E, Y, D
+    }[cls]
+
+
+KERNEL_NAMES = ["k_prep", "k_row_forward(full)", "k_row_forward(incr)", "k_col(full)", "k_col(incr)",
+                "k_row_inverse(full)", "k_row_inverse(incr)", "k_dst_col", "k_dst_row"]
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def recorded_traffic(kernel, n):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source (sha256 of sweep.cu), else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_2511_02700_gb300", "csrc", "sweep.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    e = d.get(kernel)
+    if not e or e.get("sweep_cu_sha256") != sha:
+        return None
+    return float(e["dram_bytes_per_launch"]) * (n * n) / float(e["n"] ** 2)
+
+
+# --------------------------------------------------------------------------- oracle arm
+def oracle_sample(steps, warmup, n_sample=512):
+    """FP64 CPU oracle on a bounded sample of the workload: same model,
+    tolerance and scheme on an n_sample^2 grid; times `steps` time steps
+    after `warmup` (the damped first step included in the warm-up)."""
+    import oracle as O
+    w = workload(4096)
+    m = O.model_from_subordinated_bm(w.alpha, w.kappa, w.beta, w.sigma, w.corr, w.r)
+    g = O.Grid(n_sample, half_width=w.half_width)
+    c = O.Contract(O.PUT_AVG, w.strike, w.maturity)
+    t0 = time.perf_counter()
+    S = O.Scheme(m, g, c, n_sample // 4, theta=w.theta, tol=w.tol, sl_order=w.sl_order)
+    it = S.iterate()
+    setup = time.perf_counter() - t0
+    for _ in range(max(1, warmup)):
+        next(it)
+    units = 0
+    t0 = time.perf_counter()
+    done = 0
+    for _ in range(steps):
+        try:
+            _, k = next(it)
+        except StopIteration:
+            break
+        units += n_sample * n_sample * (k + 1)
+        done += 1
+    dt = time.perf_counter() - t0
+    return {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle, {n_sample}^2 grid of the same model/tol, {done} time steps after "
+                      f"{max(1, warmup)} warm-up steps ({dt:.1f} s; setup {setup:.1f} s); numpy/scipy "
+                      "single-threaded FFT and sparse LU"}
+
+
+def run_reference(a):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    cb = oracle_sample(a.steps, a.warmup)
+    w = workload(a.n)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n": w.n, "alpha": w.alpha, "tol": w.tol,
+                       "oracle_sample_n": 512},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- our arm
+def run_ours(a):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_2511_02700_gb300 import binding as B
+    from paper_2511_02700_gb300 import build as libbuild
+    libbuild.build()
+    w = workload(a.n)
+    n = w.n
+    prec = B.PIDE2D_FP32_BULK if w.precision == "fp32" else B.PIDE2D_FP64
+    grid = B.make_grid(n, prec, w.sl_order, half_width=w.half_width)
+    model = B.model_from_subordinated_bm(w.alpha, w.kappa, w.beta, w.sigma, w.corr, w.r)
+    contract = B.make_contract(B.PIDE2D_PUT_AVG, w.strike, w.maturity)
+    stream = torch.cuda.Stream(dev)
+    t0 = time.perf_counter()
+    s = B.Solver(grid, model, contract, w.steps, theta=w.theta, tol=w.tol, device=dev, stream=stream)
+    create_s = time.perf_counter() - t0
+    if a.warmup + a.steps > w.steps:
+        raise SystemExit("warmup + steps exceeds the workload's time steps")
+    for _ in range(a.warmup):
+        s.step()
+    B.pide2d_profile(s.h, 1)
+    clocks = ClockSampler(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    units = 0
+    iters = []
+    for _ in range(a.steps):
+        k, r, st = s.step()
+        iters.append(k)
+        units += n * n * (k + 1)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        torch.distributed.barrier()
+    ck = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    B.pide2d_profile(s.h, 0)
+    kt = B.pide2d_profile_read(s.h)
+    launches = [kt.launches[i] for i in range(9)]
+    kms = [kt.ms[i] for i in range(9)]
+    # aggregate over ranks
+    t_max = ms
+    units_all = units
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        uu = torch.tensor([float(units)], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dist.all_reduce(uu, op=dist.ReduceOp.SUM)
+        t_max, units_all = float(tt.item()), float(uu.item())
+    value = units_all / (t_max / 1e3)
+    # roofline of the dominant kernel class
+    top = max(range(9), key=lambda i: kms[i])
+    bytes_per_launch = algorithmic_bytes(top, n)
+    avg_ms = kms[top] / max(1, launches[top])
+    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    peak, peak_kind = measured_peak()
+    total_kms = sum(kms)
+    roof = {"bound": "hbm", "kernel": KERNEL_NAMES[top], "achieved": achieved, "peak": peak,
+            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+            "unit": "GB/s", "frac": achieved / peak,
+            "traffic": recorded_traffic(KERNEL_NAMES[top], n),
+            "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
+            "share_of_kernel_time": kms[top] / total_kms if total_kms > 0 else None}
+    kernels = {KERNEL_NAMES[i]: {"launches": launches[i], "ms": round(kms[i], 3),
+                                 "GBps": (algorithmic_bytes(i, n) * launches[i] / (kms[i] / 1e3) / 1e9)
+                                 if kms[i] > 0 else None}
+               for i in range(9) if launches[i]}
+    # end to end: a fresh job from host inputs to host outputs through the C ABI
+    e2e = None
+    if not a.no_e2e:
+        e2e = run_e2e(B, torch, dev, grid, model, contract, w, a.warmup + a.steps)
+    s.close()
+    if ws > 1:
+        torch.distributed.barrier()
+    if rank != 0:
+        return
+    cb = None
+    if not a.no_cpu_baseline and ws == 1:
+        cb = oracle_sample(steps=6, warmup=1)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": t_max / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "n": n, "padded_fft": 2 * n, "alpha": w.alpha, "kappa": w.kappa,
+                       "time_steps_total": w.steps, "tol": w.tol, "precision": "fp32-bulk (state double-float)",
+                       "sl_order": w.sl_order, "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "working set > L2 (inputs larger than the 129 MB L2, no flush)"},
+            "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": sum(launches),
+            "clocks": ck, "fp_iters_per_step": iters, "create_s": create_s, "kernels": kernels}
+    print(json.dumps(line), flush=True)
+
+
+def run_e2e(B, torch, dev, grid, model, contract, w, steps):
+    """pide2d_create from host structs, `steps` steps, then V copied to a
+    pinned host buffer; cell-iterations over wall time."""
+    import ctypes
+    n = grid.n
+    nbytes = B.pide2d_workspace_bytes(grid)
+    wsb = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+    base = (wsb.data_ptr() + 255) & ~255
+    host = torch.empty(((n + 1) * (n + 1),), dtype=torch.float64, pin_memory=True)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    opts = B.pide2d_options()
+    opts.kmax, opts.damping = 100, 1
+    h = B.pide2d_create(grid, model, contract, w.theta, w.maturity / w.steps, w.tol, opts, base, nbytes,
+                        stream.cuda_stream)
+    units = 0
+    iters = 0
+    for i in range(steps):
+        k, r, st = B.pide2d_step(h)
+        iters += k
+        units += n * n * (k + (4 if i == 0 else 1))
+    B.pide2d_get_values(h, host.data_ptr())
+    t1 = time.perf_counter()
+    B.pide2d_destroy(h)
+    h2d = 2 * (10 + 6 + 32 + 16) * 8 + 3 * 8 * 4  # quadrature nodes and scalar blocks
+    d2h = (n + 1) * (n + 1) * 8 + iters * 4 + 9 * 8
+    return {"value": units / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
+            "d2h_bytes_per_step": d2h / steps, "steps": steps, "wall_s": t1 - t0,
+            "includes": "create (device precompute) + steps + V^n to pinned host"}
+
+
+def main():
+    a = args_parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -484,24 +484,33 @@ class Scheme:
         Vn[1:-1, 1:-1] = Y
         return Vn, self.B(Y, tau), k, err
 
-    def solve(self) -> SolveResult:
+    def iterate(self):
+        """Algorithm 1 time loop as a generator: yields (step, iterations)
+        after every time step (the damped first step yields once, with the
+        iterations of its four substeps summed); the final state is left in
+        ``self.result``."""
         T = self.contract.maturity
         ht = T / self.n_steps
         n = self.grid.n
         V0 = self.g_nodes(0.0)
         V0[1:-1, 1:-1] = initial_values(self.contract, self.grid)[1:-1, 1:-1]
         res = SolveResult(V=None, price=float("nan"), pre=self.pre)
+        self.result = res
         hist = [V0]
         V = V0
         BV = self.B(V0[1:-1, 1:-1], 0.0)
         if self.damping:
             hq = ht / 4.0
+            ktot = 0
             for j in range(4):
                 V, BV, k, e = self.theta_step(V, BV, V[1:-1, 1:-1], j * hq, (j + 1) * hq, hq, 1.0)
                 res.iters.append(k)
                 res.resid.append(e)
+                ktot += k
             hist.append(V)
             first = 2
+            res.V = V
+            yield 1, ktot
         else:
             first = 1
         for step in range(first, self.n_steps + 1):
@@ -520,6 +529,11 @@ class Scheme:
             hist.append(V)
             if len(hist) > 4:
                 hist.pop(0)
-        res.V = V
+            res.V = V
+            yield step, k
         res.price = float(V[n // 2, n // 2])
-        return res
+
+    def solve(self) -> SolveResult:
+        for _ in self.iterate():
+            pass
+        return self.result

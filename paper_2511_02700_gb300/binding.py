@@ -46,6 +46,10 @@ class pide2d_stats(ctypes.Structure):
                 ("last_resid", c_double), ("cell_iters", c_double)]
 
 
+class pide2d_kernel_times(ctypes.Structure):
+    _fields_ = [("launches", c_int * 16), ("ms", c_double * 16)]
+
+
 class PideError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -74,10 +78,13 @@ def lib():
         L.pide2d_apply_jump.argtypes = [c_void_p, c_void_p, c_double, c_int, c_void_p]
         L.pide2d_last_error.argtypes = [c_void_p]
         L.pide2d_last_error.restype = ctypes.c_char_p
+        L.pide2d_profile.argtypes = [c_void_p, c_int]
+        L.pide2d_profile_read.argtypes = [c_void_p, POINTER(pide2d_kernel_times)]
         L.pide2d_destroy.argtypes = [c_void_p]
         L.pide2d_destroy.restype = None
         for name in ("pide2d_workspace_bytes", "pide2d_create", "pide2d_step", "pide2d_solve",
-                     "pide2d_get_values", "pide2d_get_weights", "pide2d_apply_jump"):
+                     "pide2d_get_values", "pide2d_get_weights", "pide2d_apply_jump", "pide2d_profile",
+                     "pide2d_profile_read"):
             getattr(L, name).restype = c_int
         _LIB = L
     return _LIB
@@ -130,6 +137,16 @@ def pide2d_get_weights(h, omega_ptr, rates_ptr):
 
 def pide2d_apply_jump(h, U_ptr, tau, far_field, out_ptr):
     _check(lib().pide2d_apply_jump(h, c_void_p(U_ptr), tau, int(far_field), c_void_p(out_ptr)), h)
+
+
+def pide2d_profile(h, enable):
+    _check(lib().pide2d_profile(h, int(enable)), h)
+
+
+def pide2d_profile_read(h) -> pide2d_kernel_times:
+    out = pide2d_kernel_times()
+    _check(lib().pide2d_profile_read(h, byref(out)), h)
+    return out
 
 
 def pide2d_last_error(h=None) -> str:
