@@ -195,6 +195,33 @@ pide2d_status pide2d_profile(pide2d_t* h, int enable);
  * into *out.  Errors: ERR_ARG (out NULL), ERR_CUDA. */
 pide2d_status pide2d_profile_read(pide2d_t* h, pide2d_kernel_times* out);
 
+/* B_w U (eq. 3.17 sweep) computed without any device allocation.  The paper
+ * has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory -- e.g. a plugin in a host process whose memory
+ * manager owns the whole device, or a service that must not call cudaMalloc
+ * (it can synchronise the device) after start-up.  Its scratch is a fixed
+ * 7.2 MB device array inside the library, present on every GPU where the
+ * library is loaded until the process exits; hence n <= 256.
+ *   n      power of two in [8, 256] (FP64 arithmetic, N_z = n/2)
+ *   omega  device, n x n doubles, the weights [l2 + n/2][l1 + n/2] (eq. 3.5),
+ *          e.g. from pide2d_get_weights
+ *   U      device, (n+1)^2 doubles [m2][m1]; its interior nodes are used and
+ *          every other node counts as 0
+ *   out    device, (n+1)^2 doubles; receives B_w U at the interior nodes, the
+ *          other entries are left unchanged
+ *   cuda_stream  the stream the work is queued on (NULL = legacy default)
+ * Returns after queuing; the result is ready when the stream gets there.
+ * The first call on a device looks up the scratch's device address
+ * (cudaGetSymbolAddress) and caches it: make that first call before any
+ * stream capture.  All calls share the one scratch array and nothing is
+ * cleared between calls (each call writes every scratch entry it reads), so
+ * calls whose GPU work overlaps -- on different streams or host threads --
+ * race and must be serialised by the caller.
+ * Errors: ERR_ARG (n out of range or not a power of two, NULL pointer),
+ * ERR_CUDA; message via pide2d_last_error(NULL). */
+pide2d_status pide2d_jump_static(int n, const double* omega, const double* U, double* out,
+                                 void* cuda_stream);
+
 /* Human-readable message for the last non-OK status on this handle (or of
  * the last failed pide2d_create when h is NULL).  Never NULL. */
 const char* pide2d_last_error(const pide2d_t* h);

@@ -80,11 +80,12 @@ def lib():
         L.pide2d_last_error.restype = ctypes.c_char_p
         L.pide2d_profile.argtypes = [c_void_p, c_int]
         L.pide2d_profile_read.argtypes = [c_void_p, POINTER(pide2d_kernel_times)]
+        L.pide2d_jump_static.argtypes = [c_int, c_void_p, c_void_p, c_void_p, c_void_p]
         L.pide2d_destroy.argtypes = [c_void_p]
         L.pide2d_destroy.restype = None
         for name in ("pide2d_workspace_bytes", "pide2d_create", "pide2d_step", "pide2d_solve",
                      "pide2d_get_values", "pide2d_get_weights", "pide2d_apply_jump", "pide2d_profile",
-                     "pide2d_profile_read"):
+                     "pide2d_profile_read", "pide2d_jump_static"):
             getattr(L, name).restype = c_int
         _LIB = L
     return _LIB
@@ -147,6 +148,12 @@ def pide2d_profile_read(h) -> pide2d_kernel_times:
     out = pide2d_kernel_times()
     _check(lib().pide2d_profile_read(h, byref(out)), h)
     return out
+
+
+def pide2d_jump_static(n, omega_ptr, U_ptr, out_ptr, stream=0):
+    """B_w U without device allocation (device pointers; n <= 256; async on stream)."""
+    _check(lib().pide2d_jump_static(int(n), c_void_p(omega_ptr), c_void_p(U_ptr), c_void_p(out_ptr),
+                                    c_void_p(stream)))
 
 
 def pide2d_last_error(h=None) -> str:

@@ -137,6 +137,11 @@ thread_local std::string g_create_error;
 
 }  // namespace
 
+namespace pide {
+// error channel of the handle-free entry points (read by pide2d_last_error(NULL))
+void set_global_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace pide
+
 struct pide2d {
     pide2d_grid grid;
     pide2d_model model;
