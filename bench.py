@@ -151,16 +151,16 @@ def measured_peak():
 
 def recorded_traffic(kernel, n):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel source (sha256 of sweep.cu), else None."""
+    the current kernel source (sha256 of sweep_impl.cuh), else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(path))
     except Exception:
         return None
-    src = os.path.join(ROOT, "paper_2511_02700_gb300", "csrc", "sweep.cu")
+    src = os.path.join(ROOT, "paper_2511_02700_gb300", "csrc", "sweep_impl.cuh")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
     e = d.get(kernel)
-    if not e or e.get("sweep_cu_sha256") != sha:
+    if not e or e.get("source_sha256") != sha:
         return None
     return float(e["dram_bytes_per_launch"]) * (n * n) / float(e["n"] ** 2)
 

@@ -17,8 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libpide2d.so")
-SOURCES = ["sweep.cu", "precompute.cu", "api.cu", "static_jump.cu"]
-HEADERS = ["common.cuh", "state.cuh", "internal.h"]
+SOURCES = ["sweep_f32.cu", "sweep_f64.cu", "precompute.cu", "api.cu", "static_jump.cu"]
+HEADERS = ["common.cuh", "state.cuh", "internal.h", "sweep_impl.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

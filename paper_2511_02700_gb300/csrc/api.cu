@@ -52,9 +52,9 @@ void gauss_legendre(int n, double* x, double* w) {
 }
 
 // quadrature orders of the device precompute
-constexpr int kGlNear = 10, kGlFar = 6, kGlEdge = 32, kGlPay = 16;
+constexpr int kGlNear = 10, kGlFar = 6, kGlEdge = 32, kGlPay = 16, kGlVfar = 4;
 constexpr double kTanhSinhStep = 0.125;
-constexpr int kGlTotal = 2 * (kGlNear + kGlFar + kGlEdge + kGlPay);
+constexpr int kGlTotal = 2 * (kGlNear + kGlFar + kGlEdge + kGlPay + kGlVfar);
 
 enum Region {
     R_V0, R_V1, R_V2, R_V3, R_V4, R_BV, R_BY, R_W, R_X, R_OUT,   // 10 state-sized fields
@@ -239,6 +239,7 @@ static pide2d_status theta_step(pide2d* H, const int* list, int cnt, double thet
     pa.BV = BV;
     pa.W = W;
     pa.Y = Y;
+    pa.cz = rres;            // the residual field is free until the first sweep of the step
     pa.htm = (R)htm;
     pa.rw = (R)rw;
     pa.d11 = d11;
@@ -445,6 +446,8 @@ static pide2d_status do_create(pide2d* H) {
     gauss_legendre(kGlFar, p + 2 * kGlNear, p + 2 * kGlNear + kGlFar);
     gauss_legendre(kGlEdge, p + 2 * (kGlNear + kGlFar), p + 2 * (kGlNear + kGlFar) + kGlEdge);
     gauss_legendre(kGlPay, p + 2 * (kGlNear + kGlFar + kGlEdge), p + 2 * (kGlNear + kGlFar + kGlEdge) + kGlPay);
+    double* pv = p + 2 * (kGlNear + kGlFar + kGlEdge + kGlPay);
+    gauss_legendre(kGlVfar, pv, pv + kGlVfar);
     double* dgl = H->at<double>(R_GL);
     PIDE_CUDA(cudaMemsetAsync(H->ws, 0, H->L.total, s));
     PIDE_CUDA(cudaMemcpyAsync(dgl, gl.data(), gl.size() * 8, cudaMemcpyHostToDevice, s));
@@ -483,6 +486,9 @@ static pide2d_status do_create(pide2d* H) {
     j.gl_far_x = dgl + 2 * kGlNear;
     j.gl_far_w = dgl + 2 * kGlNear + kGlFar;
     j.n_far = kGlFar;
+    j.gl_vfar_x = dgl + 2 * (kGlNear + kGlFar + kGlEdge + kGlPay);
+    j.gl_vfar_w = j.gl_vfar_x + kGlVfar;
+    j.n_vfar = kGlVfar;
     int nblocks = 0;
     PIDE_CUDA(launch_weights(L, j, H->at<double>(R_OMEGA), H->at<double>(R_PART), &nblocks, s));
     const double* edge = dgl + 2 * (kGlNear + kGlFar);

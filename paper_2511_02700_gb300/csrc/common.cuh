@@ -2,14 +2,17 @@
 // the in-register small DFTs and the shared-memory block FFT.
 //
 // Block FFT.  One "FFT unit" is P/16 threads that each hold 16 complex
-// values in registers; a length-P transform (P = 2^p, 16 <= P <= 8192) is a
-// Stockham autosort sequence of radix-16 stages and at most one radix-2/4/8
-// stage, exchanging through shared memory between stages.  Stage with
-// radix R and span Ns: butterfly j reads buf[j + r P/R], multiplies by
-// w_P^{(j mod Ns) r P/(Ns R)}, applies an R-point DFT and writes
-// buf[(j - j mod Ns) R + j mod Ns + r Ns] (the autosort Stockham formulation
-// of Govindaraju et al., SC'08).  Shared-memory addresses are padded with
-// one element per 16 to break the bank conflicts of the first stage.
+// values in registers; a length-P transform (P = 2^p, 16 <= P <= 8192, a
+// compile-time constant) is a Stockham autosort sequence of radix-16 stages
+// and at most one radix-2/4/8 stage, exchanging through shared memory
+// between stages.  Stage with radix R and span Ns: butterfly j reads
+// x[j + r P/R], multiplies by w_P^{(j mod Ns) r P/(Ns R)}, applies an R-point
+// DFT and writes x[(j - j mod Ns) R + j mod Ns + r Ns] (the autosort
+// Stockham formulation of Govindaraju et al., SC'08).  The first stage reads
+// through a caller functor and the last stage writes through one, so input
+// staging (midpoints, Hermitian or odd extensions) and output epilogues fuse
+// into the transform.  Shared-memory addresses are padded with one element
+// per 16 to break the bank conflicts of the first stage.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -113,29 +116,43 @@ __device__ __forceinline__ void dft_small(C* v) {
     dit_layers<DIR, RAD, 2>(v);
 }
 
-// One Stockham stage of radix RAD over the whole P-point sequence (see top).
-// t in [0, P/16): this thread's index within its FFT unit.
-template <typename R, int DIR, int RAD>
-__device__ __forceinline__ void fft_stage(cpx<R>* buf, int P, int Ns, int t, const cpx<R>* __restrict__ tw) {
+// Loader/storer of the shared-memory buffer (padded layout).
+template <typename R> struct SmemLoad {
+    cpx<R>* buf;
+    __device__ __forceinline__ cpx<R> operator()(int i) const { return buf[padi(i)]; }
+};
+template <typename R> struct SmemStore {
+    cpx<R>* buf;
+    __device__ __forceinline__ void operator()(int i, cpx<R> v) const { buf[padi(i)] = v; }
+};
+
+// One Stockham stage of radix RAD (compile-time P and span NS); t in [0, P/16)
+// is the thread's index in its FFT unit.  The stage reads its inputs through
+// `load` (position -> value), synchronises the block, and writes its outputs
+// through `store` (position, value), then synchronises again.  Intermediate
+// stages use the shared buffer; the first stage may read from anywhere (global
+// memory, a staged raw array) and the last stage may write anywhere.
+template <typename R, int DIR, int RAD, int P, int NS, class L, class S>
+__device__ __forceinline__ void fft_stage(int t, const cpx<R>* __restrict__ tw, const L& load, const S& store) {
     constexpr int NB = 16 / RAD;            // butterflies per thread
-    const int nt = P >> 4;
-    const int stride = P / RAD;
-    const int twstep = P / (Ns * RAD);
+    constexpr int NT = P / 16;
+    constexpr int STRIDE = P / RAD;
+    constexpr int TWS = P / (NS * RAD);
     cpx<R> v[16];
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-        const int j = t + b * nt;
+        const int j = t + b * NT;
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) v[b * RAD + r] = buf[padi(j + r * stride)];
+        for (int r = 0; r < RAD; ++r) v[b * RAD + r] = load(j + r * STRIDE);
     }
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-        const int j = t + b * nt;
-        const int k = j & (Ns - 1);
-        if (Ns > 1) {
+        const int j = t + b * NT;
+        if constexpr (NS > 1) {
+            const int k = j & (NS - 1);
 #pragma unroll
             for (int r = 1; r < RAD; ++r) {
-                cpx<R> w = __ldg(&tw[k * r * twstep]);
+                cpx<R> w = __ldg(&tw[k * (r * TWS)]);
                 if (DIR > 0) w.y = -w.y;
                 v[b * RAD + r] = cmul(v[b * RAD + r], w);
             }
@@ -145,30 +162,39 @@ __device__ __forceinline__ void fft_stage(cpx<R>* buf, int P, int Ns, int t, con
     __syncthreads();
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-        const int j = t + b * nt;
-        const int k = j & (Ns - 1);
+        const int j = t + b * NT;
+        const int k = j & (NS - 1);
         const int base = (j - k) * RAD + k;
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) buf[padi(base + r * Ns)] = v[b * RAD + r];
+        for (int r = 0; r < RAD; ++r) store(base + r * NS, v[b * RAD + r]);
     }
     __syncthreads();
 }
 
-// Unscaled length-P complex DFT of buf (padded layout) in place:
-// DIR = -1: X[k] = sum_j x[j] e^{-2 pi i jk/P}; DIR = +1: e^{+2 pi i jk/P}.
-// tw[k] = e^{-2 pi i k/P}.  Every thread of the block must call it (it
-// synchronises the block); buf must have been written and synchronised.
-template <typename R, int DIR>
-__device__ void block_fft(cpx<R>* buf, int P, int t, const cpx<R>* __restrict__ tw) {
-    int Ns = 1;
-    while (Ns * 16 <= P) {
-        fft_stage<R, DIR, 16>(buf, P, Ns, t, tw);
-        Ns *= 16;
+// Stages NS, 16 NS, ... of a length-P transform: radix 16 while it fits, one
+// radix-2/4/8 stage last.  `load` feeds the first of them, `store` takes the
+// last one's outputs (natural order); the others go through `buf`.
+template <typename R, int DIR, int P, int NS, class L, class S>
+__device__ __forceinline__ void fft_from(cpx<R>* buf, int t, const cpx<R>* __restrict__ tw, const L& load,
+                                         const S& store) {
+    constexpr int RAD = (NS * 16 <= P) ? 16 : P / NS;
+    if constexpr (NS * RAD == P) {
+        fft_stage<R, DIR, RAD, P, NS>(t, tw, load, store);
+    } else {
+        fft_stage<R, DIR, RAD, P, NS>(t, tw, load, SmemStore<R>{buf});
+        fft_from<R, DIR, P, NS * RAD>(buf, t, tw, SmemLoad<R>{buf}, store);
     }
-    const int rem = P / Ns;
-    if (rem == 2) fft_stage<R, DIR, 2>(buf, P, Ns, t, tw);
-    else if (rem == 4) fft_stage<R, DIR, 4>(buf, P, Ns, t, tw);
-    else if (rem == 8) fft_stage<R, DIR, 8>(buf, P, Ns, t, tw);
+}
+
+// Unscaled length-P complex DFT (DIR = -1: e^{-2 pi i jk/P}, DIR = +1: e^{+...})
+// with input x[j] = load(j) and output X[k] handed to store(k, X[k]);
+// tw[k] = e^{-2 pi i k/P}.  Every thread of the block must call it (it
+// synchronises the block); inputs read from `buf` must have been written and
+// synchronised before the call.
+template <typename R, int DIR, int P, class L, class S>
+__device__ __forceinline__ void block_fft(cpx<R>* buf, int t, const cpx<R>* __restrict__ tw, const L& load,
+                                          const S& store) {
+    fft_from<R, DIR, P, 1>(buf, t, tw, load, store);
 }
 
 // order-preserving bit pattern of a non-negative double (for atomicMax)

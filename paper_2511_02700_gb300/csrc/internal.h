@@ -97,6 +97,7 @@ template <typename R> struct PrepArgs {
     const St<R>* BV;
     St<R>* W;
     St<R>* Y;
+    R* cz;                   // Z - V at interior nodes (R field, pitch ldR)
     R htm;                   // h_t (1 - theta)
     R rw, d11, d22, d12;     // r_w and D coefficients
     int o1, o2, nt;          // SL: first tap offsets, taps per axis (2 or 4)
@@ -133,6 +134,7 @@ struct WeightJob {
     int M2;                  // z_II / h
     const double* gl_near_x; const double* gl_near_w; int n_near;
     const double* gl_far_x; const double* gl_far_w; int n_far;
+    const double* gl_vfar_x; const double* gl_vfar_w; int n_vfar;
 };
 cudaError_t launch_weights(const LevyParams& L, const WeightJob& j, double* omega, double* partials,
                            int* nblocks, cudaStream_t s);

@@ -67,10 +67,14 @@ __global__ void k_weights(LevyParams L, WeightJob j, double* omega, double* part
         if (inf <= 2.0) {
             w = 0.0;                                               // R_I
         } else if (inf <= (double)j.M2) {                          // R_II
+            // Gauss-Legendre order by distance from the singular origin (in
+            // cells): 10 up to 8 cells, 6 up to 24 cells (or on coarse grids),
+            // 4 beyond -- each within ~1e-14 relative of a 24-point rule
             const bool near = inf <= 8.0;
-            const int n = near ? j.n_near : j.n_far;
-            const double* gx = near ? j.gl_near_x : j.gl_far_x;
-            const double* gw = near ? j.gl_near_w : j.gl_far_w;
+            const bool far = inf > 24.0 && N >= 1024;
+            const int n = near ? j.n_near : (far ? j.n_vfar : j.n_far);
+            const double* gx = near ? j.gl_near_x : (far ? j.gl_vfar_x : j.gl_far_x);
+            const double* gw = near ? j.gl_near_w : (far ? j.gl_vfar_w : j.gl_far_w);
             double acc = 0.0;
             for (int a = 0; a < n; ++a) {
                 const double za = c1 + 0.5 * j.h * gx[a];
@@ -167,21 +171,36 @@ __global__ void k_moment(LevyParams L, double H, const double* glx, const double
     }
 }
 
-// params: [0] sum w, [1] r_w, [2] kappa1, [3] kappa2, [4] a11, [5] a12, [6] a22, [7] b1, [8] b2
+// params: [0] sum w, [1] r_w, [2] kappa1, [3] kappa2, [4] a11, [5] a12, [6] a22, [7] b1, [8] b2.
+// One block; each thread sums a fixed strided subset of the block partials,
+// then a fixed-order tree: the result does not depend on scheduling.
 __global__ void k_finalize(const double* partials, int nblocks, const double* moment, double r, double s11,
                            double s12, double s22, double* params) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ double a[1024], b[1024], c[1024];
     double sw = 0.0, e1 = 0.0, e2 = 0.0;
-    for (int i = 0; i < nblocks; ++i) {
+    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
         sw += partials[3 * i];
         e1 += partials[3 * i + 1];
         e2 += partials[3 * i + 2];
     }
+    a[threadIdx.x] = sw;
+    b[threadIdx.x] = e1;
+    c[threadIdx.x] = e2;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            a[threadIdx.x] += a[threadIdx.x + o];
+            b[threadIdx.x] += b[threadIdx.x + o];
+            c[threadIdx.x] += c[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
     const double a11 = s11 + moment[0], a12 = s12 + moment[1], a22 = s22 + moment[2];
-    params[0] = sw;
-    params[1] = r + sw;
-    params[2] = r - e1;
-    params[3] = r - e2;
+    params[0] = a[0];
+    params[1] = r + a[0];
+    params[2] = r - b[0];
+    params[3] = r - c[0];
     params[4] = a11;
     params[5] = a12;
     params[6] = a22;
@@ -312,7 +331,7 @@ cudaError_t launch_moment(const LevyParams& L, double H, const double* glx, cons
 }
 cudaError_t launch_finalize(const double* partials, int nblocks, const double* moment, double r,
                             const double* sigma_cov, double* params, cudaStream_t s) {
-    k_finalize<<<1, 1, 0, s>>>(partials, nblocks, moment, r, sigma_cov[0], sigma_cov[1], sigma_cov[2], params);
+    k_finalize<<<1, 1024, 0, s>>>(partials, nblocks, moment, r, sigma_cov[0], sigma_cov[1], sigma_cov[2], params);
     return cudaGetLastError();
 }
 cudaError_t launch_tables(int N, double s_lo1, double s_lo2, double h, double* E1d, double* E2d, float* E1f,

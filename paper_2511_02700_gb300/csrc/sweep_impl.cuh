@@ -1,0 +1,648 @@
+// Time-stepping kernels of pide2d (templates; instantiated per precision in
+// sweep_f32.cu and sweep_f64.cu): the jump sum B_w by zero-padded 2D FFT
+// cross-correlation (eqs. 3.10-3.17), the diffusion solve by DST-I, and the
+// semi-Lagrangian explicit part (Algorithm 1, steps 1-4).
+//
+// Data flow of one fixed-point iteration (all transforms length P = 2N):
+//   k_row_forward  rows of T_in U (midpoints along s1), packed two real rows
+//                  per complex FFT, R2C spectra -> S[group][row][c]
+//   k_col          per spectrum column: midpoints along s2, forward FFT,
+//                  product with conj(w^)/P^2, inverse FFT, keep rows 1..N
+//   k_row_inverse  per row pair: C2R, B_w at the interior nodes, state and
+//                  residual update, then the row DST-I of the residual -> E
+//   k_dst_col      per column pair: DST-I, divide by the eigenvalues of the
+//                  diffusion operator, DST-I back
+//   k_dst_row      per row pair: DST-I back to nodes = increment, state
+//                  update and the eq. 3.25 maximum
+// DST-I of length N-1 is the imaginary part of the length-2N DFT of the
+// odd extension, so every pass uses the same block FFT.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "internal.h"
+#include "state.cuh"
+
+namespace pide {
+
+namespace {
+
+// Launch shape of the FFT kernels for transform length P: FFT units of P/16
+// threads, at least 128 threads per block; the register target (64 in FP32,
+// 128 in FP64) fixes the minimum number of resident blocks per SM.
+template <typename R, int P> struct Cfg {
+    static constexpr int NT = P / 16;
+    static constexpr int UNITS = NT >= 128 ? 1 : 128 / NT;
+    static constexpr int THREADS = UNITS * NT;
+    static constexpr int ULEN = padded_len(P) + 4;
+    static constexpr int MINB = (sizeof(R) == 4 ? 1024 : 512) / THREADS;
+    static constexpr size_t SMEM = (size_t)UNITS * ULEN * sizeof(cpx<R>);
+};
+
+template <typename R>
+__device__ __forceinline__ R midpoint(const R* u, int i) {
+    // cubic Lagrange at the midpoint of nodes i+1, i+2 from nodes i..i+3
+    return R(-0.0625) * (u[i] + u[i + 3]) + R(0.5625) * (u[i + 1] + u[i + 2]);
+}
+
+template <typename R>
+__device__ __forceinline__ R node_value(const FwdArgs<R>& a, int m1, int m2) {
+    const int N = a.g.N;
+    const bool in = (m1 >= 1 && m1 <= N - 1 && m2 >= 1 && m2 <= N - 1);
+    if (a.mode == FWD_INCR) return in ? a.D[(size_t)m2 * a.g.ldR + m1] : R(0);
+    if (in) return st_r(a.Y[(size_t)m2 * a.g.ldS + m1]);
+    if (a.mode == FWD_FULL0) return R(0);
+    return far_value<R>(a.payoff, a.Kd, a.E1[m1 + a.g.eoff], a.E2[m2 + a.g.eoff]);
+}
+
+// D applied to a state field at interior index idx (pitch ld)
+template <typename S, typename R>
+__device__ __forceinline__ R diff_state(const S* Y, size_t idx, int ld, R d11, R d22, R d12) {
+    const S c = Y[idx];
+    const R dxx = st_diff(Y[idx + 1], c) + st_diff(Y[idx - 1], c);
+    const R dyy = st_diff(Y[idx + ld], c) + st_diff(Y[idx - ld], c);
+    const R dxy = st_diff(Y[idx + ld + 1], Y[idx - ld + 1]) - st_diff(Y[idx + ld - 1], Y[idx - ld - 1]);
+    return d11 * dxx + d22 * dyy + d12 * dxy;
+}
+template <typename R>
+__device__ __forceinline__ R diff_plain(const R* D, size_t idx, int ld, R d11, R d22, R d12) {
+    const R c = D[idx];
+    const R dxx = D[idx + 1] + D[idx - 1] - R(2) * c;
+    const R dyy = D[idx + ld] + D[idx - ld] - R(2) * c;
+    const R dxy = (D[idx + ld + 1] - D[idx - ld + 1]) - (D[idx + ld - 1] - D[idx - ld - 1]);
+    return d11 * dxx + d22 * dyy + d12 * dxy;
+}
+
+template <typename R> struct ResidAtomic;
+template <> struct ResidAtomic<float> {
+    static __device__ void max(void* p, float v) { atomicMax((unsigned int*)p, __float_as_uint(v)); }
+};
+template <> struct ResidAtomic<double> {
+    static __device__ void max(void* p, double v) {
+        atomicMax((unsigned long long*)p, (unsigned long long)__double_as_longlong(v));
+    }
+};
+
+template <typename K>
+void set_smem(K kernel, size_t bytes) {
+    if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+#define PIDE_FFT_KERNEL(R, P) __global__ void __launch_bounds__(Cfg<R, P>::THREADS, Cfg<R, P>::MINB)
+
+// ---------------------------------------------------------------------------
+// forward row pass: T_in along s1 (from staged nodes) + packed R2C
+// ---------------------------------------------------------------------------
+template <typename R, int P>
+PIDE_FFT_KERNEL(R, P) k_row_forward(FwdArgs<R> a) {
+    using C = cpx<R>;
+    using CF = Cfg<R, P>;
+    constexpr int NT = CF::NT, N = P / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int unit = threadIdx.x / NT, t = threadIdx.x - unit * NT;
+    C* buf = reinterpret_cast<C*>(smem_raw) + (size_t)unit * CF::ULEN;
+    R* nodes = reinterpret_cast<R*>(buf);
+    const int p = blockIdx.x * CF::UNITS + unit;
+    const bool valid = p < a.npairs;
+    const int rho = 2 * (a.pair0 + p);
+    const C* tw = (const C*)a.tw;
+    if (a.mode == FWD_WEIGHTS) {
+        auto load = [&](int i) -> C {
+            R wa = 0, wb = 0;
+            if (valid && i < N) {
+                if (rho < N) wa = (R)a.omega[(size_t)rho * N + i];
+                if (rho + 1 < N) wb = (R)a.omega[(size_t)(rho + 1) * N + i];
+            }
+            return mk<R>(wa, wb);
+        };
+        block_fft<R, -1, P>(buf, t, tw, load, SmemStore<R>{buf});
+    } else {
+        const int m2a = rho - N / 2 - 1;
+        for (int idx = t; idx < P + 2; idx += NT) {
+            const int m1 = idx - N / 2 - 1;
+            nodes[idx] = valid ? node_value(a, m1, m2a) : R(0);
+            nodes[P + 2 + idx] = valid ? node_value(a, m1, m2a + 1) : R(0);
+        }
+        __syncthreads();
+        auto load = [&](int i) -> C {
+            if (i > P - 2) return mk<R>(0, 0);
+            return mk<R>(midpoint(nodes, i), midpoint(nodes + P + 2, i));
+        };
+        block_fft<R, -1, P>(buf, t, tw, load, SmemStore<R>{buf});
+    }
+    constexpr int Gc = cgroup<R>();
+    C* S = (C*)a.S;
+    const int rows = a.g.rows;
+    for (int g = t; g < a.g.ng; g += NT) {
+#pragma unroll
+        for (int c = 0; c < Gc; ++c) {
+            const int k = g * Gc + c;
+            C xa = mk<R>(0, 0), xb = mk<R>(0, 0);
+            if (k <= P / 2) {
+                const C zk = buf[padi(k)];
+                const C zm = buf[padi((P - k) & (P - 1))];
+                xa = mk<R>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
+                xb = mk<R>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
+            }
+            if (valid) {
+                S[((size_t)g * rows + rho) * Gc + c] = xa;
+                S[((size_t)g * rows + rho + 1) * Gc + c] = xb;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// column pass: staged column, T_in along s2 in the first stage, product with
+// conj(w^)/P^2 in the last forward stage, inverse FFT writing rows 1..N
+// ---------------------------------------------------------------------------
+template <typename R, int P>
+PIDE_FFT_KERNEL(R, P) k_col(ColArgs<R> a) {
+    using C = cpx<R>;
+    using CF = Cfg<R, P>;
+    constexpr int NT = CF::NT, N = P / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int unit = threadIdx.x / NT, t = threadIdx.x - unit * NT;
+    C* buf = reinterpret_cast<C*>(smem_raw) + (size_t)unit * CF::ULEN;
+    const int k1 = blockIdx.x * CF::UNITS + unit;
+    const bool valid = k1 <= P / 2;
+    constexpr int Gc = cgroup<R>();
+    const int g = k1 / Gc, c = k1 - g * Gc;
+    C* col = (C*)a.S + (size_t)g * a.g.rows * Gc + c;
+    const C* tw = (const C*)a.tw;
+    for (int rho = t; rho < P + 2; rho += NT)
+        buf[padi(rho)] = (valid && rho >= a.rlo && rho < a.rhi) ? col[(size_t)rho * Gc] : mk<R>(0, 0);
+    __syncthreads();
+    auto load = [&](int i) -> C {
+        if (i > P - 2) return mk<R>(0, 0);
+        const C x0 = buf[padi(i)], x1 = buf[padi(i + 1)], x2 = buf[padi(i + 2)], x3 = buf[padi(i + 3)];
+        return mk<R>(R(-0.0625) * (x0.x + x3.x) + R(0.5625) * (x1.x + x2.x),
+                     R(-0.0625) * (x0.y + x3.y) + R(0.5625) * (x1.y + x2.y));
+    };
+    const C* wh = (const C*)a.Wh + (size_t)g * P * Gc + c;
+    auto store_mul = [&](int k2, C v) {
+        const C w = valid ? __ldg(&wh[(size_t)k2 * Gc]) : mk<R>(0, 0);
+        buf[padi(k2)] = cmul(v, w);
+    };
+    block_fft<R, -1, P>(buf, t, tw, load, store_mul);
+    auto store_out = [&](int m, C v) {
+        if (valid && m >= 1 && m <= N) col[(size_t)(m - 1) * Gc] = v;
+    };
+    block_fft<R, +1, P>(buf, t, tw, SmemLoad<R>{buf}, store_out);
+}
+
+// ---------------------------------------------------------------------------
+// inverse row pass: Hermitian-extended packed spectrum in the first stage,
+// B_w at the interior nodes + state/residual update in the last stage, which
+// also lays out the odd extension of the residual for the row DST
+// ---------------------------------------------------------------------------
+template <typename R, int P>
+PIDE_FFT_KERNEL(R, P) k_row_inverse(InvArgs<R> a) {
+    using C = cpx<R>;
+    using S_ = St<R>;
+    using CF = Cfg<R, P>;
+    constexpr int NT = CF::NT, N = P / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int unit = threadIdx.x / NT, t = threadIdx.x - unit * NT;
+    C* buf = reinterpret_cast<C*>(smem_raw) + (size_t)unit * CF::ULEN;
+    const int p = blockIdx.x * CF::UNITS + unit;
+    const int m2 = 2 * p + 1;
+    const bool valid = m2 <= N - 1;
+    const bool hasb = valid && (m2 + 1 <= N - 1);
+    constexpr int Gc = cgroup<R>();
+    const C* S = (const C*)a.S;
+    const int rows = a.g.rows;
+    const C* tw = (const C*)a.tw;
+    auto load = [&](int pos) -> C {
+        const bool hi = pos > P / 2;
+        const int k = hi ? P - pos : pos;
+        C xa = mk<R>(0, 0), xb = mk<R>(0, 0);
+        if (valid) {
+            const int g = k / Gc, c = k - g * Gc;
+            xa = S[((size_t)g * rows + (m2 - 1)) * Gc + c];
+            xb = S[((size_t)g * rows + m2) * Gc + c];
+        }
+        if (k == 0 || k == P / 2) { xa.y = 0; xb.y = 0; }
+        if (hi) { xa.y = -xa.y; xb.y = -xb.y; }
+        return mk<R>(xa.x - xb.y, xa.y + xb.x);
+    };
+    const int ld = a.g.ldS, ldR = a.g.ldR;
+    auto epilogue = [&](int m1, C zz) {
+        if (m1 == 0) {
+            if (a.do_resid) {
+                buf[padi(0)] = mk<R>(0, 0);
+                buf[padi(N)] = mk<R>(0, 0);
+            }
+            return;
+        }
+        if (m1 >= N) return;
+        R rr[2] = {R(0), R(0)};
+        if (valid) {
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                if (half == 1 && !hasb) break;
+                const int row = m2 + half;
+                const R zv = half == 0 ? zz.x : zz.y;
+                const size_t idx = (size_t)row * ld + m1;
+                const size_t idr = (size_t)row * ldR + m1;
+                if (a.mode == INV_OUT) {
+                    a.out[idx] = (double)zv;
+                } else if (a.mode == INV_FULL) {
+                    a.BY[idx] = st_from_r<S_, R>(zv);
+                    if (a.do_resid) {
+                        const S_ y = a.Y[idx];
+                        rr[half] = st_diff(a.W[idx], y) + a.htt * zv - a.htt * a.rw * st_r(y)
+                                   + a.htt * diff_state(a.Y, idx, ld, a.d11, a.d22, a.d12);
+                    }
+                } else {  // INV_INCR
+                    a.BY[idx] = st_add(a.BY[idx], zv);
+                    if (a.do_resid) {
+                        const R d = a.D[idr];
+                        rr[half] = a.r[idr] + a.htt * zv
+                                   - (a.cid * d - a.htt * diff_plain(a.D, idr, ldR, a.d11, a.d22, a.d12));
+                    }
+                }
+                if (a.do_resid) a.r[idr] = rr[half];
+            }
+        }
+        if (a.do_resid) {
+            buf[padi(m1)] = mk<R>(rr[0], rr[1]);
+            buf[padi(P - m1)] = mk<R>(-rr[0], -rr[1]);
+        }
+    };
+    block_fft<R, +1, P>(buf, t, tw, load, epilogue);
+    if (!a.do_resid) return;   // uniform across the block
+    constexpr int GE = rgroup<R>();
+    auto store_e = [&](int k, C zz) {
+        if (k >= N) return;
+        const int gE = k / GE, c = k - gE * GE;
+        const R va = k >= 1 ? R(-0.5) * zz.y : R(0);
+        const R vb = k >= 1 ? R(0.5) * zz.x : R(0);
+        if (valid) a.E[((size_t)gE * N + m2) * GE + c] = va;
+        if (hasb) a.E[((size_t)gE * N + m2 + 1) * GE + c] = vb;
+    };
+    block_fft<R, -1, P>(buf, t, tw, SmemLoad<R>{buf}, store_e);
+}
+
+// ---------------------------------------------------------------------------
+// column DST pass with the eigenvalue division between the two transforms
+// ---------------------------------------------------------------------------
+template <typename R, int P>
+PIDE_FFT_KERNEL(R, P) k_dst_col(DstColArgs<R> a) {
+    using C = cpx<R>;
+    using CF = Cfg<R, P>;
+    constexpr int NT = CF::NT, N = P / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int unit = threadIdx.x / NT, t = threadIdx.x - unit * NT;
+    C* buf = reinterpret_cast<C*>(smem_raw) + (size_t)unit * CF::ULEN;
+    const int u = blockIdx.x * CF::UNITS + unit;
+    const int ka = 2 * u, kb = ka + 1;
+    const bool valid = ka < N;
+    constexpr int GE = rgroup<R>();
+    const int gE = ka / GE, ca = ka - gE * GE, cb = ca + 1;
+    R* col = a.E + (size_t)gE * N * GE;
+    const C* tw = (const C*)a.tw;
+    auto load = [&](int i) -> C {
+        const int j = i <= N ? i : P - i;
+        const R sg = i <= N ? R(1) : R(-1);
+        R xa = 0, xb = 0;
+        if (valid && j >= 1 && j <= N - 1) {
+            xa = sg * col[(size_t)j * GE + ca];
+            xb = sg * col[(size_t)j * GE + cb];
+        }
+        return mk<R>(xa, xb);
+    };
+    const R c0 = (R)a.c0, c1 = (R)a.c1, c2 = (R)a.c2, sc = (R)a.scale;
+    const R sa = valid ? a.sin2[ka] : R(0);
+    const R sb = valid ? a.sin2[kb] : R(0);
+    auto divide = [&](int k2, C zz) {
+        if (k2 == 0) {
+            buf[padi(0)] = mk<R>(0, 0);
+            buf[padi(N)] = mk<R>(0, 0);
+            return;
+        }
+        if (k2 >= N) return;
+        const R s2 = a.sin2[k2];
+        const R ta = R(-0.5) * zz.y * sc / (c0 + c1 * sa + c2 * s2);
+        const R tb = R(0.5) * zz.x * sc / (c0 + c1 * sb + c2 * s2);
+        buf[padi(k2)] = mk<R>(ta, tb);
+        buf[padi(P - k2)] = mk<R>(-ta, -tb);
+    };
+    block_fft<R, -1, P>(buf, t, tw, load, divide);
+    auto store = [&](int m2, C zz) {
+        if (valid && m2 >= 1 && m2 <= N - 1) {
+            col[(size_t)m2 * GE + ca] = R(-0.5) * zz.y;
+            col[(size_t)m2 * GE + cb] = R(0.5) * zz.x;
+        }
+    };
+    block_fft<R, -1, P>(buf, t, tw, SmemLoad<R>{buf}, store);
+}
+
+// ---------------------------------------------------------------------------
+// row DST back to nodes: increment, state update, eq. 3.25 maximum
+// ---------------------------------------------------------------------------
+template <typename R, int P>
+PIDE_FFT_KERNEL(R, P) k_dst_row(DstRowArgs<R> a) {
+    using C = cpx<R>;
+    using CF = Cfg<R, P>;
+    constexpr int NT = CF::NT, N = P / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int unit = threadIdx.x / NT, t = threadIdx.x - unit * NT;
+    C* buf = reinterpret_cast<C*>(smem_raw) + (size_t)unit * CF::ULEN;
+    R* red = reinterpret_cast<R*>(reinterpret_cast<C*>(smem_raw) + (size_t)CF::UNITS * CF::ULEN);
+    const int p = blockIdx.x * CF::UNITS + unit;
+    const int m2 = 2 * p + 1;
+    const bool valid = m2 <= N - 1;
+    const bool hasb = valid && (m2 + 1 <= N - 1);
+    constexpr int GE = rgroup<R>();
+    const C* tw = (const C*)a.tw;
+    auto load = [&](int i) -> C {
+        const int j = i <= N ? i : P - i;
+        const R sg = i <= N ? R(1) : R(-1);
+        R ea = 0, eb = 0;
+        if (valid && j >= 1 && j <= N - 1) {
+            const int gE = j / GE, c = j - gE * GE;
+            ea = sg * a.E[((size_t)gE * N + m2) * GE + c];
+            if (hasb) eb = sg * a.E[((size_t)gE * N + m2 + 1) * GE + c];
+        }
+        return mk<R>(ea, eb);
+    };
+    R rmax = 0;
+    const int ld = a.g.ldS, ldR = a.g.ldR;
+    auto update = [&](int m1, C zz) {
+        if (!valid || m1 < 1 || m1 >= N) return;
+        const R da = R(-0.5) * zz.y, db = R(0.5) * zz.x;
+        {
+            const size_t idx = (size_t)m2 * ld + m1;
+            const St<R> y = st_add(a.Y[idx], da);
+            a.Y[idx] = y;
+            a.D[(size_t)m2 * ldR + m1] = da;
+            rmax = fmax(rmax, fabs(da) / fmax(R(1), fabs(st_r(y))));
+        }
+        if (hasb) {
+            const size_t idx = (size_t)(m2 + 1) * ld + m1;
+            const St<R> y = st_add(a.Y[idx], db);
+            a.Y[idx] = y;
+            a.D[(size_t)(m2 + 1) * ldR + m1] = db;
+            rmax = fmax(rmax, fabs(db) / fmax(R(1), fabs(st_r(y))));
+        }
+    };
+    block_fft<R, -1, P>(buf, t, tw, load, update);
+    // block maximum, one atomic per block
+    for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
+    if (lane == 0) red[warp] = rmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        R m = 0;
+        for (int w = 0; w < nwarp; ++w) m = fmax(m, red[w]);
+        ResidAtomic<R>::max(a.resid, m);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// per-step preparation: W = T_SL[Z] (Algorithm 1 step 2), Y^{n,0} (eq. 3.26),
+// far field on the boundary ring of Y.  Z - V at interior nodes comes from
+// k_explicit (one pass), so the SL taps read it instead of recomputing the
+// stencil per tap.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ double far_dbl(const PrepArgs<R>& a, int q1, int q2, double Kd) {
+    return (double)far_value<double>(a.payoff, Kd, a.E1d[q1 + a.g.eoff], a.E2d[q2 + a.g.eoff]);
+}
+
+// cz = h_t (1-theta) (D V - r_w V + B V) at interior nodes (Z - V of Algorithm 1 step 2)
+template <typename R>
+__global__ void k_explicit(PrepArgs<R> a) {
+    const int N = a.g.N;
+    const int m1 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int m2 = blockIdx.y * blockDim.y + threadIdx.y;
+    if (m1 < 1 || m2 < 1 || m1 > N - 1 || m2 > N - 1) return;
+    const int ld = a.g.ldS;
+    const size_t idx = (size_t)m2 * ld + m1;
+    const St<R>* V = a.V[0];
+    a.cz[(size_t)m2 * a.g.ldR + m1] =
+        a.htm * (diff_state(V, idx, ld, a.d11, a.d22, a.d12) - a.rw * st_r(V[idx]) + st_r(a.BV[idx]));
+}
+
+template <typename R, int NTAP>
+__global__ void __launch_bounds__(256) k_prep(PrepArgs<R> a) {
+    const int N = a.g.N;
+    const int m1 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int m2 = blockIdx.y * blockDim.y + threadIdx.y;
+    if (m1 > N || m2 > N) return;
+    const int ld = a.g.ldS, ldR = a.g.ldR;
+    const size_t idx = (size_t)m2 * ld + m1;
+    using S_ = St<R>;
+    if (m1 == 0 || m2 == 0 || m1 == N || m2 == N) {
+        a.Y[idx] = st_make<S_>(far_dbl(a, m1, m2, a.Kd_now));
+        return;
+    }
+    const S_* V = a.V[0];
+    const S_ v = V[idx];
+    const bool expl = a.htm != R(0);
+    const R czm = expl ? a.cz[(size_t)m2 * ldR + m1] : R(0);
+    // all taps inside the interior: the common case, branch-free and unrolled
+    const bool inner = m1 + a.o1 >= 1 && m1 + a.o1 + NTAP - 1 <= N - 1 && m2 + a.o2 >= 1 &&
+                       m2 + a.o2 + NTAP - 1 <= N - 1;
+    R w1[NTAP], w2[NTAP];
+#pragma unroll
+    for (int c = 0; c < NTAP; ++c) {
+        w1[c] = a.w1[c];
+        w2[c] = a.w2[c];
+    }
+    R corr = czm;
+    if (inner) {
+        const S_* Vb = V + (size_t)(m2 + a.o2) * ld + (m1 + a.o1);
+        const R* Cb = a.cz + (size_t)(m2 + a.o2) * ldR + (m1 + a.o1);
+        S_ vv[NTAP][NTAP];
+        R cc[NTAP][NTAP];
+#pragma unroll
+        for (int b = 0; b < NTAP; ++b)
+#pragma unroll
+            for (int c = 0; c < NTAP; ++c) {
+                vv[b][c] = Vb[(size_t)b * ld + c];
+                cc[b][c] = expl ? Cb[(size_t)b * ldR + c] : R(0);
+            }
+#pragma unroll
+        for (int b = 0; b < NTAP; ++b) {
+            R row = 0;
+#pragma unroll
+            for (int c = 0; c < NTAP; ++c) row += w1[c] * (st_diff(vv[b][c], v) + cc[b][c] - czm);
+            corr += w2[b] * row;
+        }
+    } else {
+#pragma unroll
+        for (int b = 0; b < NTAP; ++b) {
+            const int q2 = m2 + a.o2 + b;
+            R row = 0;
+#pragma unroll
+            for (int c = 0; c < NTAP; ++c) {
+                const int q1 = m1 + a.o1 + c;
+                R dz;
+                if (q1 >= 1 && q1 <= N - 1 && q2 >= 1 && q2 <= N - 1) {
+                    dz = st_diff(V[(size_t)q2 * ld + q1], v) - czm;
+                    if (expl) dz += a.cz[(size_t)q2 * ldR + q1];
+                } else {
+                    dz = (R)(far_dbl(a, q1, q2, a.Kd_prev) - st_dbl(v)) - czm;
+                }
+                row += w1[c] * dz;
+            }
+            corr += w2[b] * row;
+        }
+    }
+    a.W[idx] = st_add(v, corr);
+    R e = 0;
+    if (a.hcount == 2) {
+        e = -st_diff(a.V[1][idx], v);
+    } else if (a.hcount == 3) {
+        e = R(-3) * st_diff(a.V[1][idx], v) + st_diff(a.V[2][idx], v);
+    } else if (a.hcount >= 4) {
+        e = R(-6) * st_diff(a.V[1][idx], v) + R(4) * st_diff(a.V[2][idx], v) - st_diff(a.V[3][idx], v);
+    }
+    a.Y[idx] = st_add(v, e);
+}
+
+// ---------------------------------------------------------------------------
+// omega-hat: FP64 forward column FFT of the FP64 row spectra of Omega
+// ---------------------------------------------------------------------------
+template <typename RO, int P>
+PIDE_FFT_KERNEL(double, P) k_weights_col(Geometry g, const double2* Sd, cpx<RO>* Wh, const double2* twd) {
+    using CF = Cfg<double, P>;
+    constexpr int NT = CF::NT, N = P / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int unit = threadIdx.x / NT, t = threadIdx.x - unit * NT;
+    double2* buf = reinterpret_cast<double2*>(smem_raw) + (size_t)unit * CF::ULEN;
+    const int k1 = blockIdx.x * CF::UNITS + unit;
+    const bool valid = k1 <= P / 2;
+    auto load = [&](int i) -> double2 {
+        // rows >= N of the zero-padded Omega are zero
+        return (valid && i < N) ? Sd[(size_t)k1 * P + i] : mk<double>(0, 0);
+    };
+    constexpr int Go = cgroup<RO>();
+    const int go = k1 / Go, co = k1 - go * Go;
+    const double inv = 1.0 / ((double)P * (double)P);
+    auto store = [&](int k2, double2 w) {
+        if (valid) Wh[((size_t)go * P + k2) * Go + co] = mk<RO>((RO)(w.x * inv), (RO)(-w.y * inv));
+    };
+    block_fft<double, -1, P>(buf, t, twd, load, store);
+}
+
+template <typename R>
+__global__ void k_state_from_double(Geometry g, const double* src, int lds, St<R>* dst) {
+    const int m1 = blockIdx.x * blockDim.x + threadIdx.x, m2 = blockIdx.y * blockDim.y + threadIdx.y;
+    if (m1 > g.N || m2 > g.N) return;
+    dst[(size_t)m2 * g.ldS + m1] = st_make<St<R>>(src[(size_t)m2 * lds + m1]);
+}
+template <typename R>
+__global__ void k_state_to_double(Geometry g, const St<R>* src, double* dst, int ldd) {
+    const int m1 = blockIdx.x * blockDim.x + threadIdx.x, m2 = blockIdx.y * blockDim.y + threadIdx.y;
+    if (m1 > g.N || m2 > g.N) return;
+    dst[(size_t)m2 * ldd + m1] = st_dbl(src[(size_t)m2 * g.ldS + m1]);
+}
+
+// ---------------------------------------------------------------------------
+// launchers: dispatch the compile-time transform length
+// ---------------------------------------------------------------------------
+#define PIDE_SWITCH_P(P, CASE)                                                              \
+    switch (P) {                                                                            \
+        case 16: CASE(16); case 32: CASE(32); case 64: CASE(64); case 128: CASE(128);       \
+        case 256: CASE(256); case 512: CASE(512); case 1024: CASE(1024);                    \
+        case 2048: CASE(2048); case 4096: CASE(4096); case 8192: CASE(8192);                \
+        default: return cudaErrorInvalidValue;                                              \
+    }
+
+// FP64 time-loop kernels exist up to P = 4096 (FP64 mode is limited to N <= 2048)
+template <typename R, int P> struct LoopSize { static constexpr bool ok = sizeof(R) == 4 || P <= 4096; };
+
+template <typename R, int P, class K, class A>
+cudaError_t launch_fft_kernel(K kernel, const A& a, int work_units, size_t extra_smem, cudaStream_t s) {
+    using CF = Cfg<R, P>;
+    const size_t smem = CF::SMEM + extra_smem;
+    set_smem(kernel, smem);
+    const int blocks = (work_units + CF::UNITS - 1) / CF::UNITS;
+    kernel<<<blocks, CF::THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_row_forward(const FwdArgs<R>& a, cudaStream_t s) {
+#define CASE(PP) return launch_fft_kernel<R, PP>(k_row_forward<R, PP>, a, a.npairs, 0, s);
+    PIDE_SWITCH_P(a.g.P, CASE)
+#undef CASE
+}
+template <typename R>
+cudaError_t launch_col(const ColArgs<R>& a, cudaStream_t s) {
+#define CASE(PP)                                                                       \
+    if constexpr (LoopSize<R, PP>::ok) return launch_fft_kernel<R, PP>(k_col<R, PP>, a, PP / 2 + 1, 0, s); \
+    else return cudaErrorInvalidValue;
+    PIDE_SWITCH_P(a.g.P, CASE)
+#undef CASE
+}
+template <typename R>
+cudaError_t launch_row_inverse(const InvArgs<R>& a, cudaStream_t s) {
+#define CASE(PP)                                                                       \
+    if constexpr (LoopSize<R, PP>::ok) return launch_fft_kernel<R, PP>(k_row_inverse<R, PP>, a, PP / 4, 0, s); \
+    else return cudaErrorInvalidValue;
+    PIDE_SWITCH_P(a.g.P, CASE)
+#undef CASE
+}
+template <typename R>
+cudaError_t launch_dst_col(const DstColArgs<R>& a, cudaStream_t s) {
+#define CASE(PP)                                                                       \
+    if constexpr (LoopSize<R, PP>::ok) return launch_fft_kernel<R, PP>(k_dst_col<R, PP>, a, PP / 4, 0, s); \
+    else return cudaErrorInvalidValue;
+    PIDE_SWITCH_P(a.g.P, CASE)
+#undef CASE
+}
+template <typename R>
+cudaError_t launch_dst_row(const DstRowArgs<R>& a, cudaStream_t s) {
+#define CASE(PP)                                                                       \
+    if constexpr (LoopSize<R, PP>::ok) return launch_fft_kernel<R, PP>(k_dst_row<R, PP>, a, PP / 4, 32 * sizeof(R), s); \
+    else return cudaErrorInvalidValue;
+    PIDE_SWITCH_P(a.g.P, CASE)
+#undef CASE
+}
+template <typename R>
+cudaError_t launch_prep(const PrepArgs<R>& a, cudaStream_t s) {
+    const dim3 blk(32, 8);
+    const dim3 grd((a.g.N + 1 + 31) / 32, (a.g.N + 1 + 7) / 8);
+    if (a.htm != R(0)) {
+        k_explicit<R><<<grd, blk, 0, s>>>(a);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (a.nt == 2) k_prep<R, 2><<<grd, blk, 0, s>>>(a);
+    else k_prep<R, 4><<<grd, blk, 0, s>>>(a);
+    return cudaGetLastError();
+}
+template <typename RO>
+cudaError_t launch_weights_col(const Geometry& g, const void* Sd, void* Wh, const void* twd, cudaStream_t s) {
+#define CASE(PP)                                                                                   \
+    {                                                                                              \
+        using CF = Cfg<double, PP>;                                                                \
+        set_smem(k_weights_col<RO, PP>, CF::SMEM);                                                 \
+        k_weights_col<RO, PP><<<(PP / 2 + 1 + CF::UNITS - 1) / CF::UNITS, CF::THREADS, CF::SMEM, s>>>( \
+            g, (const double2*)Sd, (cpx<RO>*)Wh, (const double2*)twd);                             \
+        return cudaGetLastError();                                                                 \
+    }
+    PIDE_SWITCH_P(g.P, CASE)
+#undef CASE
+}
+template <typename R>
+cudaError_t launch_state_from_double(const Geometry& g, const double* src, int lds, St<R>* dst, cudaStream_t s) {
+    const dim3 blk(32, 8), grd((g.N + 1 + 31) / 32, (g.N + 1 + 7) / 8);
+    k_state_from_double<R><<<grd, blk, 0, s>>>(g, src, lds, dst);
+    return cudaGetLastError();
+}
+template <typename R>
+cudaError_t launch_state_to_double(const Geometry& g, const St<R>* src, double* dst, int ldd, cudaStream_t s) {
+    const dim3 blk(32, 8), grd((g.N + 1 + 31) / 32, (g.N + 1 + 7) / 8);
+    k_state_to_double<R><<<grd, blk, 0, s>>>(g, src, dst, ldd);
+    return cudaGetLastError();
+}
+
+}  // namespace pide

@@ -34,7 +34,7 @@ def roi_mask(n, half_width=2.5):
     return M
 
 
-@pytest.mark.parametrize("n,alpha", [(16, 0.25), (64, 0.5), (128, 0.25), (128, 0.75)])
+@pytest.mark.parametrize("n,alpha", [(16, 0.25), (64, 0.5), (128, 0.25), (128, 0.75), (1024, 0.75)])
 def test_weights_and_rates_match_oracle(n, alpha):
     w = Workload("w", n=n, steps=n // 4, alpha=alpha)
     s = gpu_solver(w)
