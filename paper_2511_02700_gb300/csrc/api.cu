@@ -59,7 +59,7 @@ constexpr int kGlTotal = 2 * (kGlNear + kGlFar + kGlEdge + kGlPay + kGlVfar);
 enum Region {
     R_V0, R_V1, R_V2, R_V3, R_V4, R_BV, R_BY, R_W, R_X, R_OUT,   // 10 state-sized fields
     R_RES, R_DLT,                                                 // R fields
-    R_S, R_WH, R_E, R_TWR, R_TWD,
+    R_S, R_WH, R_WHI, R_E, R_TWR, R_TWD,
     R_E1D, R_E2D, R_E1F, R_E2F, R_SIN2D, R_SIN2R,
     R_OMEGA, R_PART, R_PARAMS, R_MOMENT, R_GL, R_RESID,
     R_COUNT
@@ -89,7 +89,7 @@ void fill_layout(int N, Layout& L) {
     for (int i = R_V0; i <= R_OUT; ++i) L.size[i] = fieldS;
     L.size[R_RES] = L.size[R_DLT] = fieldR;
     L.size[R_S] = (size_t)g.ng * g.rows * 16;
-    L.size[R_WH] = (size_t)g.ng * g.P * 16;
+    L.size[R_WH] = L.size[R_WHI] = (size_t)g.ng * g.P * 16;
     L.size[R_E] = (size_t)g.nge * N * 16;
     L.size[R_TWR] = (size_t)g.P * 2 * sizeof(R);
     L.size[R_TWD] = (size_t)g.P * 16;
@@ -348,6 +348,7 @@ static pide2d_status theta_step(pide2d* H, const int* list, int cnt, double thet
     fa.pair0 = (N / 2 + 2) / 2;
     fa.npairs = N / 2;
     ca.mode = COL_INCR;
+    ca.Wh = H->at<void>(R_WHI);
     ca.rlo = N / 2 + 2;
     ca.rhi = N / 2 + N + 2;
     ia.mode = INV_INCR;
@@ -510,7 +511,7 @@ static pide2d_status do_create(pide2d* H) {
     wa.npairs = N / 2;
     wa.tw = H->at<void>(R_TWD);
     PIDE_CUDA(launch_row_forward<double>(wa, s));
-    PIDE_CUDA(launch_weights_col<R>(gd, H->field(0), H->at<void>(R_WH), H->at<void>(R_TWD), s));
+    PIDE_CUDA(launch_weights_col<R>(gd, H->field(0), H->at<void>(R_WH), H->at<void>(R_WHI), H->at<void>(R_TWD), s));
     PIDE_CUDA(cudaMemsetAsync(H->field(0), 0, H->L.off[R_RES] - H->L.off[R_V0], s));
 
     PIDE_CUDA(cudaMemcpyAsync(H->par, H->at<double>(R_PARAMS), 9 * 8, cudaMemcpyDeviceToHost, s));

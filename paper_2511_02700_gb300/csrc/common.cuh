@@ -150,11 +150,32 @@ __device__ __forceinline__ void fft_stage(int t, const cpx<R>* __restrict__ tw, 
         const int j = t + b * NT;
         if constexpr (NS > 1) {
             const int k = j & (NS - 1);
+            if constexpr (RAD == 16) {
+                // w^r = w^{4a} w^b (r = 4a + b): six table loads, nine products,
+                // each twiddle at most one rounding away from the table
+                cpx<R> wb[4], wa[4];
 #pragma unroll
-            for (int r = 1; r < RAD; ++r) {
-                cpx<R> w = __ldg(&tw[k * (r * TWS)]);
-                if (DIR > 0) w.y = -w.y;
-                v[b * RAD + r] = cmul(v[b * RAD + r], w);
+                for (int q = 1; q < 4; ++q) {
+                    wb[q] = __ldg(&tw[k * (q * TWS)]);
+                    wa[q] = __ldg(&tw[k * (4 * q * TWS)]);
+                    if (DIR > 0) { wb[q].y = -wb[q].y; wa[q].y = -wa[q].y; }
+                }
+#pragma unroll
+                for (int r = 1; r < 16; ++r) {
+                    const int qa = r >> 2, qb = r & 3;
+                    cpx<R> w;
+                    if (qa == 0) w = wb[qb];
+                    else if (qb == 0) w = wa[qa];
+                    else w = cmul(wa[qa], wb[qb]);
+                    v[b * RAD + r] = cmul(v[b * RAD + r], w);
+                }
+            } else {
+#pragma unroll
+                for (int r = 1; r < RAD; ++r) {
+                    cpx<R> w = __ldg(&tw[k * (r * TWS)]);
+                    if (DIR > 0) w.y = -w.y;
+                    v[b * RAD + r] = cmul(v[b * RAD + r], w);
+                }
             }
         }
         dft_small<DIR, RAD>(&v[b * RAD]);

@@ -52,7 +52,7 @@ template <typename R> struct ColArgs {
     Geometry g;
     int mode;
     void* S;                 // cpx<R> spectrum, in place
-    const void* Wh;          // cpx<R> conj(w^)/P^2, layout [group][k2][c]
+    const void* Wh;          // cpx<R> conj(w^)/P^2 (FULL) or with the midpoint factors (INCR), [group][k2][c]
     int rlo, rhi;            // spectrum rows holding data
     const void* tw;
 };
@@ -115,7 +115,7 @@ template <typename R> cudaError_t launch_dst_col(const DstColArgs<R>& a, cudaStr
 template <typename R> cudaError_t launch_dst_row(const DstRowArgs<R>& a, cudaStream_t s);
 template <typename R> cudaError_t launch_prep(const PrepArgs<R>& a, cudaStream_t s);
 // omega-hat: forward column FFT of the FP64 row spectra, written as cpx<RO>
-template <typename RO> cudaError_t launch_weights_col(const Geometry& g, const void* Sd, void* Wh,
+template <typename RO> cudaError_t launch_weights_col(const Geometry& g, const void* Sd, void* Wh, void* Whi,
                                                        const void* twd, cudaStream_t s);
 template <typename R> cudaError_t launch_state_from_double(const Geometry& g, const double* src, int ld_src,
                                                           St<R>* dst, cudaStream_t s);

@@ -130,7 +130,7 @@ extern "C" pide2d_status pide2d_jump_static(int n, const double* omega, const do
     wa.npairs = n / 2;
     wa.tw = tw;
     PIDE_STATIC_CUDA(launch_row_forward<double>(wa, s));
-    PIDE_STATIC_CUDA(launch_weights_col<double>(gd, Wt, Wh, tw, s));
+    PIDE_STATIC_CUDA(launch_weights_col<double>(gd, Wt, Wh, nullptr, tw, s));
 
     // U -> state field, then one zero-padded correlation sweep
     PIDE_STATIC_CUDA(cudaMemcpy2DAsync(OUT, (size_t)g.ldS * 8, U, (size_t)(n + 1) * 8, (size_t)(n + 1) * 8, n + 1,

@@ -11,7 +11,7 @@ namespace pide {
     template cudaError_t launch_dst_col<R>(const DstColArgs<R>&, cudaStream_t);                     \
     template cudaError_t launch_dst_row<R>(const DstRowArgs<R>&, cudaStream_t);                     \
     template cudaError_t launch_prep<R>(const PrepArgs<R>&, cudaStream_t);                          \
-    template cudaError_t launch_weights_col<R>(const Geometry&, const void*, void*, const void*,    \
+    template cudaError_t launch_weights_col<R>(const Geometry&, const void*, void*, void*, const void*, \
                                                cudaStream_t);                                       \
     template cudaError_t launch_state_from_double<R>(const Geometry&, const double*, int, St<R>*,  \
                                                      cudaStream_t);                                 \

@@ -119,6 +119,19 @@ PIDE_FFT_KERNEL(R, P) k_row_forward(FwdArgs<R> a) {
             return mk<R>(wa, wb);
         };
         block_fft<R, -1, P>(buf, t, tw, load, SmemStore<R>{buf});
+    } else if (a.mode == FWD_INCR) {
+        // raw increment rows at positions p = m1 + N/2 + 1; the cubic midpoint
+        // interpolation along s1 is a factor of the increment weight spectrum
+        const int m2a = rho - N / 2 - 1;
+        const R* ra = a.D + (size_t)m2a * a.g.ldR;
+        const bool va = valid && m2a >= 1 && m2a <= N - 1;
+        const bool vb = valid && m2a + 1 >= 1 && m2a + 1 <= N - 1;
+        auto load = [&](int i) -> C {
+            const int m1 = i - N / 2 - 1;
+            if (m1 < 1 || m1 > N - 1) return mk<R>(0, 0);
+            return mk<R>(va ? ra[m1] : R(0), vb ? ra[a.g.ldR + m1] : R(0));
+        };
+        block_fft<R, -1, P>(buf, t, tw, load, SmemStore<R>{buf});
     } else {
         const int m2a = rho - N / 2 - 1;
         for (int idx = t; idx < P + 2; idx += NT) {
@@ -173,21 +186,29 @@ PIDE_FFT_KERNEL(R, P) k_col(ColArgs<R> a) {
     const int g = k1 / Gc, c = k1 - g * Gc;
     C* col = (C*)a.S + (size_t)g * a.g.rows * Gc + c;
     const C* tw = (const C*)a.tw;
-    for (int rho = t; rho < P + 2; rho += NT)
-        buf[padi(rho)] = (valid && rho >= a.rlo && rho < a.rhi) ? col[(size_t)rho * Gc] : mk<R>(0, 0);
-    __syncthreads();
-    auto load = [&](int i) -> C {
-        if (i > P - 2) return mk<R>(0, 0);
-        const C x0 = buf[padi(i)], x1 = buf[padi(i + 1)], x2 = buf[padi(i + 2)], x3 = buf[padi(i + 3)];
-        return mk<R>(R(-0.0625) * (x0.x + x3.x) + R(0.5625) * (x1.x + x2.x),
-                     R(-0.0625) * (x0.y + x3.y) + R(0.5625) * (x1.y + x2.y));
-    };
     const C* wh = (const C*)a.Wh + (size_t)g * P * Gc + c;
     auto store_mul = [&](int k2, C v) {
         const C w = valid ? __ldg(&wh[(size_t)k2 * Gc]) : mk<R>(0, 0);
         buf[padi(k2)] = cmul(v, w);
     };
-    block_fft<R, -1, P>(buf, t, tw, load, store_mul);
+    if (a.mode == COL_INCR) {
+        // raw rows; the midpoint interpolation along s2 is in the weight spectrum
+        auto load = [&](int rho) -> C {
+            return (valid && rho >= a.rlo && rho < a.rhi) ? col[(size_t)rho * Gc] : mk<R>(0, 0);
+        };
+        block_fft<R, -1, P>(buf, t, tw, load, store_mul);
+    } else {
+        for (int rho = t; rho < P + 2; rho += NT)
+            buf[padi(rho)] = (valid && rho >= a.rlo && rho < a.rhi) ? col[(size_t)rho * Gc] : mk<R>(0, 0);
+        __syncthreads();
+        auto load = [&](int i) -> C {
+            if (i > P - 2) return mk<R>(0, 0);
+            const C x0 = buf[padi(i)], x1 = buf[padi(i + 1)], x2 = buf[padi(i + 2)], x3 = buf[padi(i + 3)];
+            return mk<R>(R(-0.0625) * (x0.x + x3.x) + R(0.5625) * (x1.x + x2.x),
+                         R(-0.0625) * (x0.y + x3.y) + R(0.5625) * (x1.y + x2.y));
+        };
+        block_fft<R, -1, P>(buf, t, tw, load, store_mul);
+    }
     auto store_out = [&](int m, C v) {
         if (valid && m >= 1 && m <= N) col[(size_t)(m - 1) * Gc] = v;
     };
@@ -509,8 +530,14 @@ __global__ void __launch_bounds__(256) k_prep(PrepArgs<R> a) {
 // ---------------------------------------------------------------------------
 // omega-hat: FP64 forward column FFT of the FP64 row spectra of Omega
 // ---------------------------------------------------------------------------
+// Wh  = conj(w^)/P^2                      (full sweeps: midpoints taken in space)
+// Whi = conj(w^ c^[k1] c^[k2])/P^2         (increment sweeps; skipped if NULL): c^[k] = sum_e c_e
+// e^{-2 pi i e k/P} with the cubic midpoint weights c = (-1, 9, 9, -1)/16, so the
+// midpoint interpolation of a field that vanishes outside the interior is a
+// spectral factor (its support never wraps around at P = 2N).
 template <typename RO, int P>
-PIDE_FFT_KERNEL(double, P) k_weights_col(Geometry g, const double2* Sd, cpx<RO>* Wh, const double2* twd) {
+PIDE_FFT_KERNEL(double, P) k_weights_col(Geometry g, const double2* Sd, cpx<RO>* Wh, cpx<RO>* Whi,
+                                         const double2* twd) {
     using CF = Cfg<double, P>;
     constexpr int NT = CF::NT, N = P / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -525,8 +552,20 @@ PIDE_FFT_KERNEL(double, P) k_weights_col(Geometry g, const double2* Sd, cpx<RO>*
     constexpr int Go = cgroup<RO>();
     const int go = k1 / Go, co = k1 - go * Go;
     const double inv = 1.0 / ((double)P * (double)P);
+    auto chat = [&](int k) -> double2 {
+        const double2 a1 = twd[k], a2 = twd[(2 * k) & (P - 1)], a3 = twd[(3 * k) & (P - 1)];
+        return mk<double>(-0.0625 + 0.5625 * a1.x + 0.5625 * a2.x - 0.0625 * a3.x,
+                          0.5625 * a1.y + 0.5625 * a2.y - 0.0625 * a3.y);
+    };
+    const double2 c1 = valid ? chat(k1) : mk<double>(0, 0);
     auto store = [&](int k2, double2 w) {
-        if (valid) Wh[((size_t)go * P + k2) * Go + co] = mk<RO>((RO)(w.x * inv), (RO)(-w.y * inv));
+        if (!valid) return;
+        const size_t o = ((size_t)go * P + k2) * Go + co;
+        Wh[o] = mk<RO>((RO)(w.x * inv), (RO)(-w.y * inv));
+        if (Whi) {
+            const double2 wc = cmul(cmul(w, c1), chat(k2));
+            Whi[o] = mk<RO>((RO)(wc.x * inv), (RO)(-wc.y * inv));
+        }
     };
     block_fft<double, -1, P>(buf, t, twd, load, store);
 }
@@ -620,13 +659,14 @@ cudaError_t launch_prep(const PrepArgs<R>& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 template <typename RO>
-cudaError_t launch_weights_col(const Geometry& g, const void* Sd, void* Wh, const void* twd, cudaStream_t s) {
+cudaError_t launch_weights_col(const Geometry& g, const void* Sd, void* Wh, void* Whi, const void* twd,
+                               cudaStream_t s) {
 #define CASE(PP)                                                                                   \
     {                                                                                              \
         using CF = Cfg<double, PP>;                                                                \
         set_smem(k_weights_col<RO, PP>, CF::SMEM);                                                 \
         k_weights_col<RO, PP><<<(PP / 2 + 1 + CF::UNITS - 1) / CF::UNITS, CF::THREADS, CF::SMEM, s>>>( \
-            g, (const double2*)Sd, (cpx<RO>*)Wh, (const double2*)twd);                             \
+            g, (const double2*)Sd, (cpx<RO>*)Wh, (cpx<RO>*)Whi, (const double2*)twd);               \
         return cudaGetLastError();                                                                 \
     }
     PIDE_SWITCH_P(g.P, CASE)
