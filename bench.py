@@ -132,12 +132,12 @@ def algorithmic_bytes(cls, n, hcount=4):
         5: spec_n + 8 * cells + 16 * cells + 4 * cells + 4 * cells,   # inverse full: S, BY, W+Y, r, E
         6: spec_n + 16 * cells + 8 * cells + 4 * cells + 4 * cells,   # inverse incr: S, BY, r, D, E
         7: 8 * cells,                                          # column DST
-        8: 4 * cells + 16 * cells + 4 * cells,                 # row DST back: E, Y, D
+        8: 4 * cells + 16 * cells + 4 * cells + spec_n,        # row DST back (E, Y, D) + increment R2C rows
     }[cls]
 
 
 KERNEL_NAMES = ["k_prep", "k_row_forward(full)", "k_row_forward(incr)", "k_col(full)", "k_col(incr)",
-                "k_row_inverse(full)", "k_row_inverse(incr)", "k_dst_col", "k_dst_row"]
+                "k_row_inverse(full)", "k_row_inverse(incr)", "k_dst_col", "k_dst_row+fwd"]
 
 
 def measured_peak():

@@ -170,13 +170,14 @@ pide2d_status pide2d_apply_jump(pide2d_t* h, const double* U, double tau, int fa
 enum {
     PIDE2D_KERNEL_PREP = 0,            /* W = T_SL[...] and Y^{n,0} (Algorithm 1 steps 2-3)   */
     PIDE2D_KERNEL_ROW_FORWARD_FULL,    /* row pass of B_w Y^{n,0} (with far field)            */
-    PIDE2D_KERNEL_ROW_FORWARD_INCR,    /* row pass of B_w of a fixed-point increment           */
+    PIDE2D_KERNEL_ROW_FORWARD_INCR,    /* (unused: the increment row pass runs in DST_ROW)     */
     PIDE2D_KERNEL_COL_FULL,            /* column pass (FFT, product, inverse FFT), full rows   */
     PIDE2D_KERNEL_COL_INCR,            /* column pass of an increment                          */
     PIDE2D_KERNEL_ROW_INVERSE_FULL,    /* inverse row pass + first residual + row DST          */
     PIDE2D_KERNEL_ROW_INVERSE_INCR,    /* inverse row pass + residual update + row DST         */
     PIDE2D_KERNEL_DST_COL,             /* column DST, eigenvalue division, column DST          */
-    PIDE2D_KERNEL_DST_ROW,             /* row DST back, state update, eq. 3.25 maximum         */
+    PIDE2D_KERNEL_DST_ROW,             /* row DST back, state update, eq. 3.25 maximum, and   */
+                                       /* the row pass of the increment's B_w sweep         */
     PIDE2D_KERNEL_CLASSES = 9
 };
 

@@ -342,6 +342,7 @@ static pide2d_status theta_step(pide2d* H, const int* list, int cnt, double thet
     ra.Y = Y;
     ra.D = dlt;
     ra.resid = H->at<void>(R_RESID);
+    ra.S = H->at<void>(R_S);
     ra.tw = tw;
 
     fa.mode = FWD_INCR;
@@ -365,8 +366,8 @@ static pide2d_status theta_step(pide2d* H, const int* list, int cnt, double thet
         PIDE_CUDA(cudaStreamSynchronize(H->stream));
         resid = (double)rhost;
         conv = resid < H->tol;
-        // B_w of the increment keeps B_w Y^{n,k} current (needed for the next W)
-        PIDE_LAUNCH(PIDE2D_KERNEL_ROW_FORWARD_INCR, launch_row_forward<R>(fa, H->stream));
+        // B_w of the increment keeps B_w Y^{n,k} current (needed for the next W);
+        // its row pass ran inside k_dst_row
         PIDE_LAUNCH(PIDE2D_KERNEL_COL_INCR, launch_col<R>(ca, H->stream));
         ia.do_resid = conv ? 0 : 1;
         PIDE_LAUNCH(PIDE2D_KERNEL_ROW_INVERSE_INCR, launch_row_inverse<R>(ia, H->stream));

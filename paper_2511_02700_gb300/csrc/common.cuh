@@ -116,15 +116,25 @@ __device__ __forceinline__ void dft_small(C* v) {
     dit_layers<DIR, RAD, 2>(v);
 }
 
-// Loader/storer of the shared-memory buffer (padded layout).
+// Loader/storer of the shared-memory buffer (padded layout).  The stage
+// calls them with positions base + r * step; when both base and step are
+// multiples of 16 (or step < 16 with base a multiple of 16 and r*step < 16)
+// the padding distributes, padi(base + r*step) = padi(base) + r*padi(step),
+// and the stage uses the *_at forms with one padded base per thread.
 template <typename R> struct SmemLoad {
     cpx<R>* buf;
     __device__ __forceinline__ cpx<R> operator()(int i) const { return buf[padi(i)]; }
+    __device__ __forceinline__ cpx<R> at(int pbase, int poff) const { return buf[pbase + poff]; }
+    static constexpr bool smem = true;
 };
 template <typename R> struct SmemStore {
     cpx<R>* buf;
     __device__ __forceinline__ void operator()(int i, cpx<R> v) const { buf[padi(i)] = v; }
+    __device__ __forceinline__ void at(int pbase, int poff, cpx<R> v) const { buf[pbase + poff] = v; }
+    static constexpr bool smem = true;
 };
+template <class T, class = void> struct is_smem_io { static constexpr bool value = false; };
+template <class T> struct is_smem_io<T, decltype((void)T::smem, void())> { static constexpr bool value = T::smem; };
 
 // One Stockham stage of radix RAD (compile-time P and span NS); t in [0, P/16)
 // is the thread's index in its FFT unit.  The stage reads its inputs through
@@ -142,8 +152,14 @@ __device__ __forceinline__ void fft_stage(int t, const cpx<R>* __restrict__ tw, 
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
         const int j = t + b * NT;
+        if constexpr (is_smem_io<L>::value && STRIDE % 16 == 0) {
+            const int pj = padi(j);
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) v[b * RAD + r] = load(j + r * STRIDE);
+            for (int r = 0; r < RAD; ++r) v[b * RAD + r] = load.at(pj, r * (STRIDE + STRIDE / 16));
+        } else {
+#pragma unroll
+            for (int r = 0; r < RAD; ++r) v[b * RAD + r] = load(j + r * STRIDE);
+        }
     }
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
@@ -186,8 +202,15 @@ __device__ __forceinline__ void fft_stage(int t, const cpx<R>* __restrict__ tw, 
         const int j = t + b * NT;
         const int k = j & (NS - 1);
         const int base = (j - k) * RAD + k;
+        if constexpr (is_smem_io<S>::value && (NS % 16 == 0 || (NS == 1 && RAD == 16))) {
+            // NS = 1: base is a multiple of 16 and r < 16; NS % 16 == 0: r*NS is
+            const int pb = padi(base);
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) store(base + r * NS, v[b * RAD + r]);
+            for (int r = 0; r < RAD; ++r) store.at(pb, r * (NS + NS / 16), v[b * RAD + r]);
+        } else {
+#pragma unroll
+            for (int r = 0; r < RAD; ++r) store(base + r * NS, v[b * RAD + r]);
+        }
     }
     __syncthreads();
 }

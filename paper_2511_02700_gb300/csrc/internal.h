@@ -87,6 +87,7 @@ template <typename R> struct DstRowArgs {
     St<R>* Y;
     R* D;                    // increment out (interior)
     void* resid;             // R-typed max |D| / max(1, |Y|) as unsigned bits
+    void* S;                 // spectrum rows of the increment (R2C), cpx<R>
     const void* tw;
 };
 

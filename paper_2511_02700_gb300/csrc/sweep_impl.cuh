@@ -363,7 +363,8 @@ PIDE_FFT_KERNEL(R, P) k_dst_col(DstColArgs<R> a) {
 }
 
 // ---------------------------------------------------------------------------
-// row DST back to nodes: increment, state update, eq. 3.25 maximum
+// row DST back to nodes: increment, state update, eq. 3.25 maximum, and the
+// row pass of the increment's B_w sweep (packed R2C) in the same block
 // ---------------------------------------------------------------------------
 template <typename R, int P>
 PIDE_FFT_KERNEL(R, P) k_dst_row(DstRowArgs<R> a) {
@@ -393,25 +394,57 @@ PIDE_FFT_KERNEL(R, P) k_dst_row(DstRowArgs<R> a) {
     };
     R rmax = 0;
     const int ld = a.g.ldS, ldR = a.g.ldR;
+    // the increment also enters the next B_w sweep: it is laid out at its
+    // R2C position p = m1 + N/2 + 1 (zero elsewhere) for the second transform
     auto update = [&](int m1, C zz) {
-        if (!valid || m1 < 1 || m1 >= N) return;
-        const R da = R(-0.5) * zz.y, db = R(0.5) * zz.x;
-        {
-            const size_t idx = (size_t)m2 * ld + m1;
-            const St<R> y = st_add(a.Y[idx], da);
-            a.Y[idx] = y;
-            a.D[(size_t)m2 * ldR + m1] = da;
-            rmax = fmax(rmax, fabs(da) / fmax(R(1), fabs(st_r(y))));
+        R da = 0, db = 0;
+        if (valid && m1 >= 1 && m1 < N) {
+            da = R(-0.5) * zz.y;
+            {
+                const size_t idx = (size_t)m2 * ld + m1;
+                const St<R> y = st_add(a.Y[idx], da);
+                a.Y[idx] = y;
+                a.D[(size_t)m2 * ldR + m1] = da;
+                rmax = fmax(rmax, fabs(da) / fmax(R(1), fabs(st_r(y))));
+            }
+            if (hasb) {
+                db = R(0.5) * zz.x;
+                const size_t idx = (size_t)(m2 + 1) * ld + m1;
+                const St<R> y = st_add(a.Y[idx], db);
+                a.Y[idx] = y;
+                a.D[(size_t)(m2 + 1) * ldR + m1] = db;
+                rmax = fmax(rmax, fabs(db) / fmax(R(1), fabs(st_r(y))));
+            }
         }
-        if (hasb) {
-            const size_t idx = (size_t)(m2 + 1) * ld + m1;
-            const St<R> y = st_add(a.Y[idx], db);
-            a.Y[idx] = y;
-            a.D[(size_t)(m2 + 1) * ldR + m1] = db;
-            rmax = fmax(rmax, fabs(db) / fmax(R(1), fabs(st_r(y))));
-        }
+        buf[padi((m1 + N / 2 + 1) & (P - 1))] = mk<R>(da, db);
     };
     block_fft<R, -1, P>(buf, t, tw, load, update);
+    // packed R2C of the two increment rows -> spectrum rows rho = m2 + N/2 + 1, +1
+    // (the midpoint interpolation is a factor of the increment weight spectrum)
+    block_fft<R, -1, P>(buf, t, tw, SmemLoad<R>{buf}, SmemStore<R>{buf});
+    {
+        constexpr int Gc = cgroup<R>();
+        C* S = (C*)a.S;
+        const int rows = a.g.rows;
+        const int rho = m2 + N / 2 + 1;
+        for (int g = t; g < a.g.ng; g += NT) {
+#pragma unroll
+            for (int c = 0; c < Gc; ++c) {
+                const int k = g * Gc + c;
+                C xa = mk<R>(0, 0), xb = mk<R>(0, 0);
+                if (k <= P / 2) {
+                    const C zk = buf[padi(k)];
+                    const C zm = buf[padi((P - k) & (P - 1))];
+                    xa = mk<R>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
+                    xb = mk<R>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
+                }
+                if (valid) {
+                    S[((size_t)g * rows + rho) * Gc + c] = xa;
+                    S[((size_t)g * rows + rho + 1) * Gc + c] = xb;
+                }
+            }
+        }
+    }
     // block maximum, one atomic per block
     for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;

@@ -138,3 +138,44 @@ def test_step_api_and_state_errors():
     with pytest.raises(B.PideError) as e:
         s.step()
     assert "ERR_STATE" in str(e.value)
+
+
+@pytest.mark.parametrize("n,alpha", [(512, 0.5), (1024, 0.25), (1024, 0.75)])
+def test_fp32_bulk_matches_fp64_on_large_grids(n, alpha):
+    """Convergence-sweep sizes (tol 1e-8, N/4 steps): the FP32-bulk solve
+    agrees with the FP64 solve (itself oracle-pinned on smaller grids) to
+    1e-5 relative at S0 and in max-norm over the region of interest."""
+    w64 = Workload("big", n=n, steps=n // 4, alpha=alpha, tol=1e-8, precision="fp64")
+    p64, V64, _, _ = gpu_solver(w64).solve(values=True)
+    p32, V32, _, _ = gpu_solver(with_(w64, precision="fp32")).solve(values=True)
+    V64, V32 = V64.cpu().numpy(), V32.cpu().numpy()
+    roi = roi_mask(n)
+    assert abs(p32 - p64) <= 1e-5 * abs(p64), (p32, p64)
+    assert np.abs(V32 - V64)[roi].max() <= 1e-5 * np.abs(V64[roi]).max()
+
+
+@pytest.mark.slow
+def test_jump_operator_full_size_sampled():
+    """4096^2 grid, 8192^2 transforms, FP32-bulk -- the launch configuration of
+    the benchmark: B_w U at 16 sampled interior nodes against the oracle's
+    direct sums (eq. 3.10) with the oracle's weights (8-point cell rule)."""
+    n = 4096
+    w = Workload("full", n=n, steps=1024, alpha=0.5, precision="fp32")
+    s = gpu_solver(w)
+    U = random_field(n, seed=4096)
+    tau = 0.25
+    B_gpu = s.apply_jump(torch.from_numpy(U), tau, far_field=True).cpu().numpy()
+    m, g, c = oracle_inputs(w)
+    pre = O.precompute(m, g, r2_order=8)
+    Ue = O.extend(g, c, m.r, U[1:-1, 1:-1], tau)          # nodes -N/2-1 .. N+N/2
+    rng = np.random.default_rng(11)
+    nodes = [(int(a), int(b)) for a, b in rng.integers(1, n, size=(16, 2))] + [(1, 1), (n - 1, n - 1), (n // 2, n // 2)]
+    wsum = pre.sum_w
+    for (m1, m2) in nodes:
+        # midpoints j = m + l, l in [-N/2, N/2): nodes j-1..j+2 -> ext index j - 1 + N/2 + 1 ..
+        o = n // 2 + 1
+        lo1, lo2 = m1 - n // 2, m2 - n // 2
+        blk = Ue[lo2 - 1 + o: lo2 + n + 2 + o, lo1 - 1 + o: lo1 + n + 2 + o]
+        mid = O.midpoints(blk)                               # (n) x (n) midpoints m + l
+        ref = float(np.sum(pre.omega * mid))
+        assert abs(B_gpu[m2, m1] - ref) <= 2e-6 * wsum * np.abs(Ue).max(), (m1, m2, B_gpu[m2, m1], ref)
