@@ -319,9 +319,12 @@ def run_ours(a):
 
 
 def run_e2e(B, torch, dev, grid, model, contract, w, steps):
-    """pide2d_create from host structs, `steps` steps, then V copied to a
-    pinned host buffer; cell-iterations over wall time."""
-    import ctypes
+    """One complete pricing through the C ABI, as a user calls it:
+    pide2d_create from host structs (device precompute), pide2d_solve over all
+    the workload's time steps, V^{N_t} copied to a pinned host buffer and the
+    price returned to the host; cell-iterations over wall time.  Per step the
+    library reads the fixed-point residual back to the host (4 bytes per
+    iteration)."""
     n = grid.n
     nbytes = B.pide2d_workspace_bytes(grid)
     wsb = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
@@ -334,20 +337,16 @@ def run_e2e(B, torch, dev, grid, model, contract, w, steps):
     opts.kmax, opts.damping = 100, 1
     h = B.pide2d_create(grid, model, contract, w.theta, w.maturity / w.steps, w.tol, opts, base, nbytes,
                         stream.cuda_stream)
-    units = 0
-    iters = 0
-    for i in range(steps):
-        k, r, st = B.pide2d_step(h)
-        iters += k
-        units += n * n * (k + (4 if i == 0 else 1))
-    B.pide2d_get_values(h, host.data_ptr())
+    price, stats, st = B.pide2d_solve(h, host.data_ptr())
     t1 = time.perf_counter()
     B.pide2d_destroy(h)
-    h2d = 2 * (10 + 6 + 32 + 16) * 8 + 3 * 8 * 4  # quadrature nodes and scalar blocks
-    d2h = (n + 1) * (n + 1) * 8 + iters * 4 + 9 * 8
-    return {"value": units / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
-            "d2h_bytes_per_step": d2h / steps, "steps": steps, "wall_s": t1 - t0,
-            "includes": "create (device precompute) + steps + V^n to pinned host"}
+    nsteps = stats.steps_done
+    h2d = 2 * (10 + 6 + 32 + 16 + 4) * 8 + 3 * 8 * 4  # quadrature nodes and parameter blocks
+    d2h = (n + 1) * (n + 1) * 8 + stats.fp_iters_total * 4 + 9 * 8 + 8
+    return {"value": stats.cell_iters / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": h2d / nsteps,
+            "d2h_bytes_per_step": d2h / nsteps, "steps": nsteps, "wall_s": t1 - t0, "price": price,
+            "fp_iters_total": stats.fp_iters_total,
+            "includes": "pide2d_create (device precompute) + pide2d_solve over all time steps + V to pinned host"}
 
 
 def main():

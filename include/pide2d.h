@@ -157,6 +157,15 @@ pide2d_status pide2d_get_values(pide2d_t* h, double* dst);
  * log-space departure drift).  Pointers may be device or host. */
 pide2d_status pide2d_get_weights(pide2d_t* h, double* omega_out, double* rates_out);
 
+/* Greeks of the current value array V^n at the interior nodes, by the
+ * second-order central differences of Sec. 4 taken in log price and mapped
+ * to price space: Delta_i = V_{s_i}/S_i, Gamma_ii = (V_{s_i s_i} - V_{s_i})/S_i^2,
+ * Gamma_12 = V_{s_1 s_2}/(S_1 S_2) (FP64).  Each output is NULL (skipped) or
+ * (N+1)^2 doubles [m2][m1] (device or host); only interior entries are
+ * written.  Blocks until done. */
+pide2d_status pide2d_greeks(pide2d_t* h, double* delta1, double* delta2, double* gamma11,
+                            double* gamma12, double* gamma22);
+
 /* The jump sum (B_w U)(s_m) at the interior nodes for a caller field:
  * U is (N+1)^2 doubles [m2][m1] (device or host) whose interior nodes are
  * used; every node outside the interior takes g(s, tau) when far_field is

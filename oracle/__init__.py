@@ -10,5 +10,5 @@ from .levy import (NTSModel, char_exponent_1d, levy_density, levy_density_subord
                    variance)
 from .scheme import (CALL_AVG, PUT_ASSET1, PUT_AVG, Contract, Grid, Precomputed, Scheme,
                      apply_diffusion, cell_average, circulant_product, cell_integral_r2, diffusion_matrix, extend,
-                     far_field, initial_values, jump_direct, jump_fft, midpoints, precompute,
+                     far_field, greeks, initial_values, jump_direct, jump_fft, midpoints, precompute,
                      r1_moment, sl_interpolate, sl_weights, zones)

@@ -394,6 +394,27 @@ def sl_interpolate(Zx: np.ndarray, pad: int, n: int, shift: tuple, order: int) -
 
 
 # --------------------------------------------------------------------------
+# Greeks (Sec. 4: second-order central differences on the grid)
+# --------------------------------------------------------------------------
+def greeks(grid: Grid, V: np.ndarray) -> dict:
+    """Delta_i = dV/dS_i and Gamma_ij = d2V/dS_i dS_j at the interior nodes by
+    central differences in log price: dV/dS = V_s / S,
+    d2V/dS^2 = (V_ss - V_s) / S^2, d2V/dS1 dS2 = V_s1s2 / (S1 S2)."""
+    h = grid.h
+    n = grid.n
+    S1 = np.exp(grid.s(0, np.arange(1, n)))[None, :]
+    S2 = np.exp(grid.s(1, np.arange(1, n)))[:, None]
+    c = V[1:-1, 1:-1]
+    v1 = (V[1:-1, 2:] - V[1:-1, :-2]) / (2 * h)
+    v2 = (V[2:, 1:-1] - V[:-2, 1:-1]) / (2 * h)
+    v11 = (V[1:-1, 2:] - 2 * c + V[1:-1, :-2]) / (h * h)
+    v22 = (V[2:, 1:-1] - 2 * c + V[:-2, 1:-1]) / (h * h)
+    v12 = (V[2:, 2:] - V[:-2, 2:] - V[2:, :-2] + V[:-2, :-2]) / (4 * h * h)
+    return {"delta1": v1 / S1, "delta2": v2 / S2, "gamma11": (v11 - v1) / (S1 * S1),
+            "gamma12": v12 / (S1 * S2), "gamma22": (v22 - v2) / (S2 * S2)}
+
+
+# --------------------------------------------------------------------------
 # time stepping (Sec. 3.3, Algorithm 1)
 # --------------------------------------------------------------------------
 @dataclass

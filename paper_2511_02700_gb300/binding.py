@@ -81,11 +81,12 @@ def lib():
         L.pide2d_profile.argtypes = [c_void_p, c_int]
         L.pide2d_profile_read.argtypes = [c_void_p, POINTER(pide2d_kernel_times)]
         L.pide2d_jump_static.argtypes = [c_int, c_void_p, c_void_p, c_void_p, c_void_p]
+        L.pide2d_greeks.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
         L.pide2d_destroy.argtypes = [c_void_p]
         L.pide2d_destroy.restype = None
         for name in ("pide2d_workspace_bytes", "pide2d_create", "pide2d_step", "pide2d_solve",
                      "pide2d_get_values", "pide2d_get_weights", "pide2d_apply_jump", "pide2d_profile",
-                     "pide2d_profile_read", "pide2d_jump_static"):
+                     "pide2d_profile_read", "pide2d_jump_static", "pide2d_greeks"):
             getattr(L, name).restype = c_int
         _LIB = L
     return _LIB
@@ -138,6 +139,11 @@ def pide2d_get_weights(h, omega_ptr, rates_ptr):
 
 def pide2d_apply_jump(h, U_ptr, tau, far_field, out_ptr):
     _check(lib().pide2d_apply_jump(h, c_void_p(U_ptr), tau, int(far_field), c_void_p(out_ptr)), h)
+
+
+def pide2d_greeks(h, delta1, delta2, gamma11, gamma12, gamma22):
+    _check(lib().pide2d_greeks(h, *[c_void_p(p) if p else None for p in
+                                    (delta1, delta2, gamma11, gamma12, gamma22)]), h)
 
 
 def pide2d_profile(h, enable):
@@ -244,6 +250,13 @@ class Solver:
         rates = torch.empty(9, dtype=torch.float64)
         pide2d_get_weights(self.h, om.data_ptr(), rates.data_ptr())
         return om, rates
+
+    def greeks(self):
+        """Delta and Gamma fields of the current values (device tensors)."""
+        torch = self.torch
+        outs = [torch.zeros((self.n + 1, self.n + 1), dtype=torch.float64, device=self.ws.device) for _ in range(5)]
+        pide2d_greeks(self.h, *[o.data_ptr() for o in outs])
+        return dict(zip(("delta1", "delta2", "gamma11", "gamma12", "gamma22"), outs))
 
     def apply_jump(self, U, tau, far_field=True):
         torch = self.torch

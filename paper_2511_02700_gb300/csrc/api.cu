@@ -636,6 +636,22 @@ static pide2d_status do_get_values(pide2d* H, double* dst) {
 }
 
 template <typename R>
+static pide2d_status do_greeks(pide2d* H, double* const* outs) {
+    const Geometry g = H->L.g;
+    const int N = g.N;
+    double* OUT = H->at<double>(R_OUT);
+    for (int k = 0; k < 5; ++k) {
+        if (!outs[k]) continue;
+        PIDE_CUDA(launch_greeks<R>(g, (const St<R>*)H->field(H->hist[0]), H->at<double>(R_E1D),
+                                   H->at<double>(R_E2D), H->h, k, OUT, g.ldS, H->stream));
+        PIDE_CUDA(cudaMemcpy2DAsync(outs[k] + (N + 1) + 1, (size_t)(N + 1) * 8, OUT + g.ldS + 1, (size_t)g.ldS * 8,
+                                    (size_t)(N - 1) * 8, N - 1, cudaMemcpyDefault, H->stream));
+        PIDE_CUDA(cudaStreamSynchronize(H->stream));
+    }
+    return PIDE2D_OK;
+}
+
+template <typename R>
 static pide2d_status do_price(pide2d* H, double* price) {
     const Geometry g = H->L.g;
     const int N = g.N;
@@ -798,6 +814,14 @@ pide2d_status pide2d_get_weights(pide2d_t* H, double* omega_out, double* rates_o
         PIDE_CUDA(cudaMemcpy(rates_out, H->par, 9 * 8, cudaMemcpyDefault));
     }
     return PIDE2D_OK;
+}
+
+pide2d_status pide2d_greeks(pide2d_t* H, double* delta1, double* delta2, double* gamma11, double* gamma12,
+                            double* gamma22) {
+    if (!H) return PIDE2D_ERR_ARG;
+    if (H->broken) return PIDE2D_ERR_STATE;
+    double* const outs[5] = {delta1, delta2, gamma11, gamma12, gamma22};
+    return H->grid.precision == PIDE2D_FP64 ? do_greeks<double>(H, outs) : do_greeks<float>(H, outs);
 }
 
 pide2d_status pide2d_apply_jump(pide2d_t* H, const double* U, double tau, int far_field, double* out) {

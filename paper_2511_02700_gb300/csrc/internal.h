@@ -120,6 +120,9 @@ template <typename RO> cudaError_t launch_weights_col(const Geometry& g, const v
                                                        const void* twd, cudaStream_t s);
 template <typename R> cudaError_t launch_state_from_double(const Geometry& g, const double* src, int ld_src,
                                                           St<R>* dst, cudaStream_t s);
+template <typename R> cudaError_t launch_greeks(const Geometry& g, const St<R>* V, const double* E1d,
+                                                const double* E2d, double h, int which, double* out, int ldo,
+                                                cudaStream_t s);
 template <typename R> cudaError_t launch_state_to_double(const Geometry& g, const St<R>* src, double* dst,
                                                         int ld_dst, cudaStream_t s);
 

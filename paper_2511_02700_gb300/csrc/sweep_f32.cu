@@ -15,6 +15,8 @@ namespace pide {
                                                cudaStream_t);                                       \
     template cudaError_t launch_state_from_double<R>(const Geometry&, const double*, int, St<R>*,  \
                                                      cudaStream_t);                                 \
+    template cudaError_t launch_greeks<R>(const Geometry&, const St<R>*, const double*, const double*, \
+                                          double, int, double*, int, cudaStream_t);                 \
     template cudaError_t launch_state_to_double<R>(const Geometry&, const St<R>*, double*, int,    \
                                                    cudaStream_t);
 PIDE_INSTANTIATE(PIDE_PREC)

@@ -603,6 +603,37 @@ PIDE_FFT_KERNEL(double, P) k_weights_col(Geometry g, const double2* Sd, cpx<RO>*
     block_fft<double, -1, P>(buf, t, twd, load, store);
 }
 
+// Greeks (Sec. 4, central differences) at interior nodes, in price space:
+// which = 0: dV/dS1, 1: dV/dS2, 2: d2V/dS1^2, 3: d2V/dS1dS2, 4: d2V/dS2^2
+template <typename R>
+__global__ void k_greeks(Geometry g, const St<R>* V, const double* E1d, const double* E2d, double h, int which,
+                         double* out, int ldo) {
+    const int m1 = blockIdx.x * blockDim.x + threadIdx.x, m2 = blockIdx.y * blockDim.y + threadIdx.y;
+    if (m1 < 1 || m2 < 1 || m1 > g.N - 1 || m2 > g.N - 1) return;
+    const int ld = g.ldS;
+    const size_t i = (size_t)m2 * ld + m1;
+    const double S1 = E1d[m1 + g.eoff], S2 = E2d[m2 + g.eoff];
+    const double c = st_dbl(V[i]);
+    double r;
+    if (which == 0) {
+        r = (st_dbl(V[i + 1]) - st_dbl(V[i - 1])) / (2.0 * h) / S1;
+    } else if (which == 1) {
+        r = (st_dbl(V[i + ld]) - st_dbl(V[i - ld])) / (2.0 * h) / S2;
+    } else if (which == 2) {
+        const double v1 = (st_dbl(V[i + 1]) - st_dbl(V[i - 1])) / (2.0 * h);
+        const double v11 = (st_dbl(V[i + 1]) - 2.0 * c + st_dbl(V[i - 1])) / (h * h);
+        r = (v11 - v1) / (S1 * S1);
+    } else if (which == 3) {
+        r = (st_dbl(V[i + ld + 1]) - st_dbl(V[i - ld + 1]) - st_dbl(V[i + ld - 1]) + st_dbl(V[i - ld - 1])) /
+            (4.0 * h * h) / (S1 * S2);
+    } else {
+        const double v2 = (st_dbl(V[i + ld]) - st_dbl(V[i - ld])) / (2.0 * h);
+        const double v22 = (st_dbl(V[i + ld]) - 2.0 * c + st_dbl(V[i - ld])) / (h * h);
+        r = (v22 - v2) / (S2 * S2);
+    }
+    out[(size_t)m2 * ldo + m1] = r;
+}
+
 template <typename R>
 __global__ void k_state_from_double(Geometry g, const double* src, int lds, St<R>* dst) {
     const int m1 = blockIdx.x * blockDim.x + threadIdx.x, m2 = blockIdx.y * blockDim.y + threadIdx.y;
@@ -704,6 +735,13 @@ cudaError_t launch_weights_col(const Geometry& g, const void* Sd, void* Wh, void
     }
     PIDE_SWITCH_P(g.P, CASE)
 #undef CASE
+}
+template <typename R>
+cudaError_t launch_greeks(const Geometry& g, const St<R>* V, const double* E1d, const double* E2d, double h,
+                         int which, double* out, int ldo, cudaStream_t s) {
+    const dim3 blk(32, 8), grd((g.N + 1 + 31) / 32, (g.N + 1 + 7) / 8);
+    k_greeks<R><<<grd, blk, 0, s>>>(g, V, E1d, E2d, h, which, out, ldo);
+    return cudaGetLastError();
 }
 template <typename R>
 cudaError_t launch_state_from_double(const Geometry& g, const double* src, int lds, St<R>* dst, cudaStream_t s) {

@@ -179,3 +179,61 @@ def test_jump_operator_full_size_sampled():
         mid = O.midpoints(blk)                               # (n) x (n) midpoints m + l
         ref = float(np.sum(pre.omega * mid))
         assert abs(B_gpu[m2, m1] - ref) <= 2e-6 * wsum * np.abs(Ue).max(), (m1, m2, B_gpu[m2, m1], ref)
+
+
+def test_greeks_match_oracle():
+    """Delta/Gamma fields (Sec. 4 central differences) of the FP64 solve."""
+    w = Workload("g", n=64, steps=16, alpha=0.5, tol=1e-13)
+    s = gpu_solver(w)
+    s.solve()
+    G = {k: v.cpu().numpy()[1:-1, 1:-1] for k, v in s.greeks().items()}
+    m, g, c = oracle_inputs(w)
+    ref = O.Scheme(m, g, c, w.steps, tol=w.tol, sl_order=w.sl_order).solve()
+    R = O.greeks(g, ref.V)
+    for k in R:
+        assert np.abs(G[k] - R[k]).max() <= 1e-9 * (np.abs(R[k]).max() + 1e-12), k
+
+
+def test_vg0_wide_domain_fp64_matches_oracle():
+    """VG0 (alpha = 0, z_max^III = 11.5): half-width 11.5 log units."""
+    from conftest import paper_sets
+    from paper_2511_02700_gb300 import binding as B
+    mo, co = paper_sets()["VG0"]
+    n = 64
+    grid = B.make_grid(n, B.PIDE2D_FP64, 3, half_width=11.5)
+    model = B.make_model(mo.alpha, mo.delta, mo.lam, mo.eta, mo.rho, mo.r)
+    s = B.Solver(grid, model, B.make_contract(0, co.strike, co.maturity), n // 4, tol=1e-13)
+    price, V, _, _ = s.solve(values=True)
+    ref = O.Scheme(mo, O.Grid(n, half_width=11.5), co, n // 4, tol=1e-13, sl_order=3).solve()
+    assert np.abs(V.cpu().numpy() - ref.V).max() <= 1e-10 * np.abs(ref.V).max()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name,col,half_width", [("VG0", 0, 11.5), ("VG1", 1, 2.5), ("NIG0", 2, 2.5),
+                                                 ("NIG1", 3, 2.5)])
+def test_table4_prices_on_fine_grids(name, col, half_width):
+    """Table 4 (nine points near (K, K)) through the CUDA path: 2048^2 log
+    grid, FP32-bulk, N/2 time steps (the paper's N_t = N_x/2), cubic SL, values
+    off the grid by bicubic interpolation of the log-grid solution.  Bands: 4e-3
+    (8e-3 for NIG0) -- the printed values carry the paper's own grid error."""
+    from conftest import paper_sets, read_table
+    from paper_2511_02700_gb300 import binding as B
+    from scipy.interpolate import RectBivariateSpline
+    mo, co = paper_sets()[name]
+    n = 2048
+    grid = B.make_grid(n, B.PIDE2D_FP32_BULK, 3, half_width=half_width)
+    model = B.make_model(mo.alpha, mo.delta, mo.lam, mo.eta, mo.rho, mo.r)
+    s = B.Solver(grid, model, B.make_contract(0, co.strike, co.maturity), n // 2, tol=1e-8)
+    price, V, _, _ = s.solve(values=True)
+    V = V.cpu().numpy()
+    sg = math.log(100.0) - half_width + np.arange(n + 1) * (2 * half_width / n)
+    spl = RectBivariateSpline(sg, sg, V.T, kx=3, ky=3)     # V is [m2, m1]
+    # the paper prints NIG0 from a 400-point grid (the others from 800 points,
+    # Sec. 4), so its own discretisation error allows a wider band there
+    tol = 8e-3 if name == "NIG0" else 4e-3
+    dev = []
+    for row in read_table("table4_prices.txt"):
+        x1, x2 = float(row[0]), float(row[1])
+        got = float(spl.ev(math.log(x1), math.log(x2)))
+        dev.append((x1, x2, round(got, 5), float(row[2 + col]), round(got - float(row[2 + col]), 5)))
+    assert max(abs(d[-1]) for d in dev) < tol, (name, dev)

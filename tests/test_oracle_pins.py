@@ -417,3 +417,24 @@ def test_price_monotone_and_convex_in_strike():
     p = [Scheme(m, g, Contract(PUT_AVG, K, 1.0), 8, tol=1e-11, sl_order=3).solve().price for K in Ks]
     assert p[0] < p[1] < p[2]
     assert p[1] < 0.5 * (p[0] + p[2])
+
+
+def test_greeks_against_closed_form_derivatives():
+    """Central differences in log price reproduce the price-space Delta and
+    Gamma of a smooth field with second-order errors."""
+    from oracle import greeks
+    errs = {}
+    for n in (64, 256):
+        g = Grid(n, half_width=1.0)
+        s1, s2 = g.s(0, np.arange(n + 1)), g.s(1, np.arange(n + 1))
+        S1, S2 = np.meshgrid(np.exp(s1), np.exp(s2))
+        V = 1e-4 * S1 * S1 * S2 + 0.3 * S1 - 0.2 * S2 + 1e-3 * S1 * S2
+        G = greeks(g, V)
+        I1, I2 = S1[1:-1, 1:-1], S2[1:-1, 1:-1]
+        exact = {"delta1": 2e-4 * I1 * I2 + 0.3 + 1e-3 * I2, "delta2": 1e-4 * I1 * I1 - 0.2 + 1e-3 * I1,
+                 "gamma11": 2e-4 * I2, "gamma12": 2e-4 * I1 + 1e-3, "gamma22": 0.0 * I1}
+        for k, v in exact.items():
+            errs[(n, k)] = np.abs(G[k] - v).max()
+    for k in ("delta1", "delta2", "gamma11", "gamma12", "gamma22"):
+        assert errs[(256, k)] < errs[(64, k)] / 12.0, k          # O(h^2): ratio 16
+    assert errs[(256, "delta1")] < 1e-3 and errs[(256, "gamma12")] < 1e-5
