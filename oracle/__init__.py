@@ -12,3 +12,4 @@ from .scheme import (CALL_AVG, PUT_ASSET1, PUT_AVG, Contract, Grid, Precomputed,
                      apply_diffusion, cell_average, circulant_product, cell_integral_r2, diffusion_matrix, extend,
                      far_field, greeks, initial_values, jump_direct, jump_fft, midpoints, precompute,
                      r1_moment, sl_interpolate, sl_weights, zones)
+from .sensitivities import PARAMS as SENSITIVITY_PARAMS, price_gradient_fd

@@ -438,3 +438,27 @@ def test_greeks_against_closed_form_derivatives():
     for k in ("delta1", "delta2", "gamma11", "gamma12", "gamma22"):
         assert errs[(256, k)] < errs[(64, k)] / 12.0, k          # O(h^2): ratio 16
     assert errs[(256, "delta1")] < 1e-3 and errs[(256, "gamma12")] < 1e-5
+
+
+def test_price_gradient_single_asset_matches_fourier_derivatives():
+    """Payoff max(K - S1, 0): the scheme's price depends on asset 1 alone, so
+    its gradient in (sigma1, beta1) approaches the derivatives of the 1D
+    Fourier price (Table A6 exponent, Lewis formula) and the parameters of
+    asset 2 and the correlation drop out (up to the s2-edge far field)."""
+    from oracle import price_gradient_fd
+    alpha, kappa, beta, sigma, corr, r = 0.25, 0.5, (-0.10, -0.05), (0.20, 0.25), 0.3, 0.03
+    n = 64
+    gr = price_gradient_fd(alpha, kappa, beta, sigma, corr, r, Grid(n), Contract(PUT_ASSET1, 100.0, 1.0), n // 4,
+                           tol=1e-12, eps=1e-4)
+
+    def p1(s1, b1):
+        m = model_from_subordinated_bm(alpha, kappa, (b1, beta[1]), (s1, sigma[1]), corr, r)
+        return put_price_1d(m, 0, 100.0, 100.0, 1.0)
+
+    e = 1e-4
+    d_sigma1 = (p1(sigma[0] + e, beta[0]) - p1(sigma[0] - e, beta[0])) / (2 * e)
+    d_beta1 = (p1(sigma[0], beta[0] + e) - p1(sigma[0], beta[0] - e)) / (2 * e)
+    assert abs(gr["sigma1"] - d_sigma1) < 0.01 * abs(d_sigma1), (gr, d_sigma1)
+    assert abs(gr["beta1"] - d_beta1) < 0.1 * abs(d_beta1), (gr, d_beta1)
+    for p in ("sigma2", "corr", "beta2"):
+        assert abs(gr[p]) < 0.01 * abs(gr["sigma1"]), (p, gr)
