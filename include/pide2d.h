@@ -96,6 +96,13 @@ typedef struct {
 typedef struct {
     int kmax;             /* fixed-point iteration cap per time step [100]        */
     int damping;          /* 1: first step = four theta = 1 steps of dt/4 [1]     */
+    int host_loop;        /* 0: the fixed-point loop of each theta step runs on   */
+                          /*    the device, as a CUDA graph whose while-node     */
+                          /*    evaluates eq. 3.25 itself -- no host round trip  */
+                          /*    per iteration [0];                               */
+                          /* 1: the host reads the eq. 3.25 quantity after each  */
+                          /*    iteration and launches the next one.  Tracing    */
+                          /*    (pide2d_profile) always uses the host loop.      */
 } pide2d_options;
 
 typedef struct {
@@ -133,15 +140,17 @@ pide2d_status pide2d_create(const pide2d_grid* grid, const pide2d_model* model,
                             pide2d_t** out);
 
 /* One time step of Algorithm 1 (the first call performs the four damped
- * steps when damping is on).  Synchronises with the stream once per
- * fixed-point iteration to read the eq. 3.25 quantity.
+ * steps when damping is on).  With the device loop it synchronises with the
+ * stream once, at the end of the step, to read the iteration count; with
+ * host_loop = 1 once per fixed-point iteration.
  * fp_iters / fp_resid: optional outputs (NULL allowed).
  * Errors: ERR_STATE after the last step, ERR_NOT_CONVERGED (state advanced
  * with the last iterate), ERR_CUDA. */
 pide2d_status pide2d_step(pide2d_t* h, int* fp_iters, double* fp_resid);
 
 /* Runs the remaining time steps, then writes the value at the valuation
- * node (N/2, N/2) = S0 to *price (FP64).  values_out: NULL or a pointer
+ * node (N/2, N/2) = S0 to *price (FP64).  With the device loop the steps are
+ * queued without any host synchronisation in between.  values_out: NULL or a pointer
  * (device or host) to (N+1)^2 doubles receiving V^{N_t} [m2][m1].
  * stats: optional.  Blocks until done. */
 pide2d_status pide2d_solve(pide2d_t* h, double* price, double* values_out, pide2d_stats* stats);
@@ -204,6 +213,81 @@ pide2d_status pide2d_profile(pide2d_t* h, int enable);
 /* Waits for the stream, then sums the recorded event pairs per kernel class
  * into *out.  Errors: ERR_ARG (out NULL), ERR_CUDA. */
 pide2d_status pide2d_profile_read(pide2d_t* h, pide2d_kernel_times* out);
+
+/* ------------------------------------------------------------------------
+ * Discrete adjoint: the gradient of the price V^{N_t}(S0) with respect to
+ * model parameters, exact for the discrete scheme of Algorithm 1 (up to
+ * the fixed-point tolerance).  Going backwards through the theta steps, each
+ * step solves the transposed system of eq. 3.23 with the same fixed-point
+ * machinery (the transposed jump sum is the correlation with the weights
+ * flipped in both axes; the DST diffusion solve is symmetric), applies the
+ * transposed departure interpolation (the mirrored stencil of eq. 3.22) and
+ * contracts the adjoint fields with the derivatives of the weights (eq. 3.5),
+ * of sigma_w sigma_w^T, r_w and kappa_w (eqs. 3.3, 3.6) and of the departure
+ * shift.  The derivatives of the precomputed quantities along each
+ * direction are central differences of the FP64 precompute (relative step
+ * 1e-5).  The time loop is replayed from checkpoints taken every
+ * `interval` time steps.
+ * ------------------------------------------------------------------------ */
+
+/* Bytes of device tape for pide2d_record with this interval (>= 1) and up to
+ * ndirs (<= 16) directions. */
+pide2d_status pide2d_tape_bytes(pide2d_t* h, int interval, int ndirs, size_t* bytes);
+
+/* Records checkpoints of the time loop into `tape` (device memory, 256-byte
+ * aligned, >= pide2d_tape_bytes, caller-owned, untouched by anything else
+ * until destroy).  Must be called before the first step.
+ * Errors: ERR_STATE (steps already taken), ERR_ARG, ERR_WORKSPACE. */
+pide2d_status pide2d_record(pide2d_t* h, void* tape, size_t bytes, int interval, int ndirs);
+
+/* After pide2d_solve: grad[k] = d V^{N_t}(S0) / d eps of the model
+ * model + eps * dirs[k] (only delta, lambda, eta and rho of dirs[k] are
+ * used; alpha, r and sigma_cov are held fixed), k < ndirs (host arrays).
+ * Replays the time loop segment by segment (one more forward solve) and
+ * leaves the final values V^{N_t} in place.  Blocks until done.
+ * Errors: ERR_STATE (no tape or the solve is not finished), ERR_ARG,
+ * ERR_NOT_CONVERGED (an adjoint solve hit kmax; grad still written), ERR_CUDA. */
+pide2d_status pide2d_adjoint(pide2d_t* h, const pide2d_model* dirs, int ndirs, double* grad);
+
+/* ------------------------------------------------------------------------
+ * Batches: many independent pricings on one GPU (one time loop each, as in
+ * Algorithm 1).  Jobs are taken from a queue (largest first) by `lanes` host
+ * threads, each with its own CUDA stream and workspace lane, so small grids
+ * overlap on the device.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    pide2d_grid grid;
+    pide2d_model model;
+    pide2d_contract contract;
+    double theta;         /* as for pide2d_create                                  */
+    double dt;
+    double fp_tol;
+} pide2d_job;
+
+typedef struct {
+    int jobs_done;        /* jobs that produced a price (including NOT_CONVERGED)  */
+    int failures;         /* jobs whose status was not OK                          */
+    int fp_iters_total;   /* fixed-point iterations over all jobs                  */
+    double cell_iters;    /* cell-applications of B_w over all jobs                */
+} pide2d_batch_stats;
+
+/* Workspace for pide2d_batch_solve: min(lanes, count) lanes of the largest
+ * job's pide2d_workspace_bytes (256-byte rounded).  1 <= lanes <= 256.
+ * Errors: ERR_ARG. */
+pide2d_status pide2d_batch_workspace_bytes(const pide2d_job* jobs, int count, int lanes, size_t* bytes);
+
+/* Prices `count` jobs: prices[j] (host, count doubles) receives job j's value
+ * at S0; statuses (host, count ints, optional) each job's status; stats
+ * optional.  opts->host_loop is ignored: every job runs the host-driven
+ * fixed-point loop (with several lanes that overlaps better on GB300).
+ * workspace: device, >= pide2d_batch_workspace_bytes(), 256-byte aligned,
+ * caller-owned.  Uses the calling thread's current device; creates
+ * and destroys `lanes` non-blocking streams (no device allocation).  Blocks
+ * until every job is done.  Returns OK if every job succeeded, else the
+ * status of a failed job (ERR_CUDA first); message via pide2d_last_error(NULL). */
+pide2d_status pide2d_batch_solve(const pide2d_job* jobs, int count, const pide2d_options* opts, int lanes,
+                                 void* workspace, size_t workspace_bytes, double* prices, int* statuses,
+                                 pide2d_batch_stats* stats);
 
 /* B_w U (eq. 3.17 sweep) computed without any device allocation.  The paper
  * has no counterpart: this entry point exists for callers that cannot

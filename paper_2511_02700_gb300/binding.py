@@ -38,7 +38,7 @@ class pide2d_contract(ctypes.Structure):
 
 
 class pide2d_options(ctypes.Structure):
-    _fields_ = [("kmax", c_int), ("damping", c_int)]
+    _fields_ = [("kmax", c_int), ("damping", c_int), ("host_loop", c_int)]
 
 
 class pide2d_stats(ctypes.Structure):
@@ -48,6 +48,15 @@ class pide2d_stats(ctypes.Structure):
 
 class pide2d_kernel_times(ctypes.Structure):
     _fields_ = [("launches", c_int * 16), ("ms", c_double * 16)]
+
+
+class pide2d_job(ctypes.Structure):
+    _fields_ = [("grid", pide2d_grid), ("model", pide2d_model), ("contract", pide2d_contract),
+                ("theta", c_double), ("dt", c_double), ("fp_tol", c_double)]
+
+
+class pide2d_batch_stats(ctypes.Structure):
+    _fields_ = [("jobs_done", c_int), ("failures", c_int), ("fp_iters_total", c_int), ("cell_iters", c_double)]
 
 
 class PideError(RuntimeError):
@@ -82,11 +91,18 @@ def lib():
         L.pide2d_profile_read.argtypes = [c_void_p, POINTER(pide2d_kernel_times)]
         L.pide2d_jump_static.argtypes = [c_int, c_void_p, c_void_p, c_void_p, c_void_p]
         L.pide2d_greeks.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+        L.pide2d_tape_bytes.argtypes = [c_void_p, c_int, c_int, POINTER(c_size_t)]
+        L.pide2d_record.argtypes = [c_void_p, c_void_p, c_size_t, c_int, c_int]
+        L.pide2d_adjoint.argtypes = [c_void_p, POINTER(pide2d_model), c_int, POINTER(c_double)]
+        L.pide2d_batch_workspace_bytes.argtypes = [POINTER(pide2d_job), c_int, c_int, POINTER(c_size_t)]
+        L.pide2d_batch_solve.argtypes = [POINTER(pide2d_job), c_int, POINTER(pide2d_options), c_int, c_void_p,
+                                         c_size_t, POINTER(c_double), POINTER(c_int), POINTER(pide2d_batch_stats)]
         L.pide2d_destroy.argtypes = [c_void_p]
         L.pide2d_destroy.restype = None
         for name in ("pide2d_workspace_bytes", "pide2d_create", "pide2d_step", "pide2d_solve",
                      "pide2d_get_values", "pide2d_get_weights", "pide2d_apply_jump", "pide2d_profile",
-                     "pide2d_profile_read", "pide2d_jump_static", "pide2d_greeks"):
+                     "pide2d_profile_read", "pide2d_jump_static", "pide2d_greeks", "pide2d_batch_workspace_bytes",
+                     "pide2d_batch_solve", "pide2d_tape_bytes", "pide2d_record", "pide2d_adjoint"):
             getattr(L, name).restype = c_int
         _LIB = L
     return _LIB
@@ -162,6 +178,53 @@ def pide2d_jump_static(n, omega_ptr, U_ptr, out_ptr, stream=0):
                                     c_void_p(stream)))
 
 
+def pide2d_tape_bytes(h, interval, ndirs) -> int:
+    n = c_size_t(0)
+    _check(lib().pide2d_tape_bytes(h, interval, ndirs, byref(n)), h)
+    return n.value
+
+
+def pide2d_record(h, tape_ptr, nbytes, interval, ndirs):
+    _check(lib().pide2d_record(h, c_void_p(tape_ptr), nbytes, interval, ndirs), h)
+
+
+def pide2d_adjoint(h, dirs):
+    """Returns (gradient list, status)."""
+    k = len(dirs)
+    arr = (pide2d_model * k)(*dirs)
+    g = (c_double * k)()
+    st = _check(lib().pide2d_adjoint(h, arr, k, g), h)
+    return list(g), st
+
+
+def pide2d_batch_workspace_bytes(jobs, lanes) -> int:
+    arr = (pide2d_job * len(jobs))(*jobs)
+    n = c_size_t(0)
+    _check(lib().pide2d_batch_workspace_bytes(arr, len(jobs), lanes, byref(n)))
+    return n.value
+
+
+def pide2d_batch_solve(jobs, opts, lanes, workspace, workspace_bytes):
+    """Returns (prices list, statuses list, stats, status)."""
+    count = len(jobs)
+    arr = (pide2d_job * count)(*jobs)
+    prices = (c_double * count)()
+    sts = (c_int * count)()
+    stats = pide2d_batch_stats()
+    st = lib().pide2d_batch_solve(arr, count, byref(opts) if opts is not None else None, lanes,
+                                  c_void_p(workspace), workspace_bytes, prices, sts, byref(stats))
+    if st not in (PIDE2D_OK, 4):
+        raise PideError(st, lib().pide2d_last_error(None).decode())
+    return list(prices), list(sts), stats, st
+
+
+def make_job(grid, model, contract, n_steps, theta=0.5, tol=1e-10):
+    j = pide2d_job()
+    j.grid, j.model, j.contract = grid, model, contract
+    j.theta, j.dt, j.fp_tol = theta, contract.maturity / n_steps, tol
+    return j
+
+
 def pide2d_last_error(h=None) -> str:
     return lib().pide2d_last_error(h).decode()
 
@@ -203,6 +266,27 @@ def model_from_subordinated_bm(alpha, kappa, beta, sigma, corr, r):
     return make_model(alpha, delta, lam, beta, (s1 * s1, corr * s1 * s2, s2 * s2), r)
 
 
+SUBORDINATED_BM_PARAMS = ("sigma1", "sigma2", "corr", "kappa", "beta1", "beta2")
+
+
+def subordinated_bm_directions(alpha, kappa, beta, sigma, corr):
+    """Tangents d(model)/dp of model_from_subordinated_bm for p in
+    SUBORDINATED_BM_PARAMS, as pide2d_model directions for pide2d_adjoint."""
+    lam = (1.0 - alpha) / kappa
+    delta = lam ** (1.0 - alpha) / math.gamma(1.0 - alpha)
+    s1, s2 = sigma
+    z = (0.0, 0.0)
+    dirs = [
+        make_model(0.0, 0.0, 0.0, z, (2.0 * s1, corr * s2, 0.0), 0.0),           # sigma1
+        make_model(0.0, 0.0, 0.0, z, (0.0, corr * s1, 2.0 * s2), 0.0),           # sigma2
+        make_model(0.0, 0.0, 0.0, z, (0.0, s1 * s2, 0.0), 0.0),                  # corr
+        make_model(0.0, -(1.0 - alpha) * delta / kappa, -lam / kappa, z, (0.0, 0.0, 0.0), 0.0),  # kappa
+        make_model(0.0, 0.0, 0.0, (1.0, 0.0), (0.0, 0.0, 0.0), 0.0),             # beta1
+        make_model(0.0, 0.0, 0.0, (0.0, 1.0), (0.0, 0.0, 0.0), 0.0),             # beta2
+    ]
+    return dirs
+
+
 def make_contract(payoff=PIDE2D_PUT_AVG, strike=100.0, maturity=1.0):
     c = pide2d_contract()
     c.payoff, c.strike, c.maturity = payoff, strike, maturity
@@ -213,7 +297,7 @@ class Solver:
     """One pricing: device workspace from PyTorch, kernels on a PyTorch stream."""
 
     def __init__(self, grid, model, contract, n_steps, theta=0.5, tol=1e-10, kmax=100, damping=True,
-                 device="cuda", stream=None):
+                 device="cuda", stream=None, host_loop=False):
         import torch
         self.torch = torch
         self.grid = grid
@@ -224,6 +308,7 @@ class Solver:
         self.stream = stream if stream is not None else torch.cuda.current_stream(device)
         opts = pide2d_options()
         opts.kmax, opts.damping = kmax, 1 if damping else 0
+        opts.host_loop = 1 if host_loop else 0
         self.h = pide2d_create(grid, model, contract, theta, contract.maturity / n_steps, tol, opts, base,
                                nbytes, self.stream.cuda_stream)
         self.workspace_bytes = nbytes
@@ -265,6 +350,18 @@ class Solver:
         pide2d_apply_jump(self.h, U.data_ptr(), tau, far_field, out.data_ptr())
         return out
 
+    def record(self, interval=16, ndirs=6):
+        """Checkpoint the time loop for pide2d_adjoint (before the first step)."""
+        torch = self.torch
+        nbytes = pide2d_tape_bytes(self.h, interval, ndirs)
+        self.tape = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.ws.device)
+        base = (self.tape.data_ptr() + 255) & ~255
+        pide2d_record(self.h, base, nbytes, interval, ndirs)
+        self.tape_bytes = nbytes
+
+    def adjoint(self, dirs):
+        return pide2d_adjoint(self.h, dirs)
+
     def close(self):
         if self.h:
             pide2d_destroy(self.h)
@@ -275,3 +372,50 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def solve_batch(jobs, lanes=16, kmax=100, damping=True, device="cuda", host_loop=False):
+    """Prices a list of pide2d_job through pide2d_batch_solve (workspace from
+    PyTorch).  Returns (prices, statuses, stats)."""
+    import torch
+    lanes = max(1, min(lanes, len(jobs)))
+    nbytes = pide2d_batch_workspace_bytes(jobs, lanes)
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+    base = (ws.data_ptr() + 255) & ~255
+    opts = pide2d_options()
+    opts.kmax, opts.damping = kmax, 1 if damping else 0
+    opts.host_loop = 1 if host_loop else 0
+    torch.cuda.synchronize(device)
+    prices, sts, stats, _ = pide2d_batch_solve(jobs, opts, lanes, base, nbytes)
+    del ws
+    return prices, sts, stats
+
+
+def price_function():
+    """torch.autograd.Function: price(params) with params = (sigma1, sigma2,
+    corr, kappa, beta1, beta2) as a float64 tensor; the backward pass is the
+    discrete adjoint (pide2d_adjoint).  Extra arguments of apply: alpha, r,
+    grid, contract, n_steps, theta, tol, interval."""
+    import torch
+
+    class _Price(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, params, alpha, r, grid, contract, n_steps, theta=0.5, tol=1e-10, interval=16):
+            p = [float(x) for x in params.detach().cpu().tolist()]
+            sig, corr, kap, beta = (p[0], p[1]), p[2], p[3], (p[4], p[5])
+            model = model_from_subordinated_bm(alpha, kap, beta, sig, corr, r)
+            s = Solver(grid, model, contract, n_steps, theta=theta, tol=tol)
+            s.record(interval=interval, ndirs=6)
+            price, _, _, _ = s.solve()
+            g, _ = s.adjoint(subordinated_bm_directions(alpha, kap, beta, sig, corr))
+            s.close()
+            ctx.save_for_backward(torch.tensor(g, dtype=torch.float64))
+            return torch.tensor(price, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (g,) = ctx.saved_tensors
+            return (grad_out * g, None, None, None, None, None, None, None, None)
+
+    return _Price
+

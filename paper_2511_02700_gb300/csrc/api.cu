@@ -61,7 +61,7 @@ enum Region {
     R_RES, R_DLT,                                                 // R fields
     R_S, R_WH, R_WHI, R_E, R_TWR, R_TWD,
     R_E1D, R_E2D, R_E1F, R_E2F, R_SIN2D, R_SIN2R,
-    R_OMEGA, R_PART, R_PARAMS, R_MOMENT, R_GL, R_RESID,
+    R_OMEGA, R_PART, R_PARAMS, R_MOMENT, R_GL, R_RESID, R_CTL,
     R_COUNT
 };
 
@@ -104,6 +104,7 @@ void fill_layout(int N, Layout& L) {
     L.size[R_MOMENT] = 4 * 8;
     L.size[R_GL] = (size_t)kGlTotal * 8;
     L.size[R_RESID] = 16;
+    L.size[R_CTL] = sizeof(FpCtl);
     size_t o = 0;
     for (int i = 0; i < R_COUNT; ++i) {
         L.off[i] = o;
@@ -147,7 +148,7 @@ struct pide2d {
     pide2d_model model;
     pide2d_contract contract;
     double theta, dt, tol;
-    int kmax, damping, n_steps, sl_order;
+    int kmax, damping, n_steps, sl_order, host_loop;
     Layout L;
     cudaStream_t stream;
     char* ws;
@@ -159,6 +160,28 @@ struct pide2d {
     pide2d_stats stats;
     std::string err;
     bool broken;
+    // device-side fixed-point loop: instantiated loop graphs keyed by their kernel arguments
+    struct LoopGraph { std::string key; cudaGraph_t graph; cudaGraphExec_t exec; };
+    std::vector<LoopGraph> graphs;
+    cudaStream_t cap = nullptr;    // private stream used only to record graphs
+    int graph_builds = 0;
+    bool ctl_dirty = false;        // device loop ran since the last read of FpCtl
+    bool last_step_device = false;
+    FpCtl ctl{};                   // host copy of the device statistics
+    int nonconv_seen = 0;
+    // adjoint tape (pide2d_record / pide2d_adjoint)
+    struct Tape {
+        char* base = nullptr;
+        size_t bytes = 0;
+        int interval = 0, ndirs = 0, nckpt = 0, seg_slots = 0;
+        size_t off_ckpt = 0, off_seg = 0, off_final = 0, off_adj = 0, off_spec = 0, off_scr = 0, off_acc = 0;
+        std::vector<int> ckpt_cnt;
+    } tape;
+    bool seg_record = false;       // replay of a tape segment: keep every theta step's V and B_w V
+    bool force_host_loop = false;
+    int seg_slot = 0;
+    struct StepMeta { double theta, ht, tau_prev, tau; };
+    std::vector<StepMeta> seg_meta;
     // tracing
     bool prof = false;
     struct Rec { int cls; cudaEvent_t a, b; };
@@ -209,112 +232,347 @@ cudaError_t prof_event(pide2d* H, cudaEvent_t* e) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// one theta step (eq. 3.23) by the fixed-point iteration (3.24)-(3.26)
+// adjoint tape: checkpoints of the time loop every `interval` time steps
+// (history fields and B_w V), a segment buffer for the replay of one
+// interval (V and B_w V after every theta step), the adjoint fields, the
+// weight spectra of the adjoint and of the parameter directions, scratch
+// for the finite differences of the precompute, and the FP64 accumulators.
 // ---------------------------------------------------------------------------
+namespace {
+enum AdjField { A_LAM, A_MU, A_BMU, A_NU, A_XI, A_PEND, A_COUNT };
+constexpr int kAdjAcc = 6;        // <xi,V>, <xi,dxx V>, <xi,dxy V>, <xi,dyy V>, shift 1, shift 2
+
+struct TapeLayout {
+    size_t ckpt, seg, fin, adj, spec, scr, acc, total;
+    size_t field, spec1, omega, part, rows, nparts;
+    int nckpt, seg_slots;
+};
+
+TapeLayout tape_layout(const Layout& L, int n_steps, int interval, int ndirs) {
+    TapeLayout t{};
+    const int N = L.g.N;
+    t.field = align256(L.size[R_V0]);
+    t.spec1 = align256(L.size[R_WH]);
+    t.omega = align256((size_t)N * N * 8);
+    t.part = align256(L.size[R_PART]);
+    t.rows = align256((size_t)(L.g.P / 2 + 1) * L.g.P * 16);
+    t.nparts = align256((size_t)adjoint_dot_blocks(N) * 4 * 8);
+    t.nckpt = (n_steps + interval - 1) / interval;
+    t.seg_slots = interval + 3;                       // the damped first step has four theta steps
+    size_t o = 0;
+    t.ckpt = o;  o += (size_t)t.nckpt * 5 * t.field;  // hist (up to 4) + B_w V per checkpoint
+    t.seg = o;   o += (size_t)t.seg_slots * 2 * t.field;
+    t.fin = o;   o += 5 * t.field;                    // the final state, put back after the adjoint
+    t.adj = o;   o += (size_t)A_COUNT * t.field;
+    t.spec = o;  o += (size_t)(2 + ndirs) * t.spec1;  // flipped Wh, Whi; one Wh per direction
+    t.scr = o;   o += 3 * t.omega + t.part + 256 + 2 * 256 + t.rows + t.nparts;
+    t.acc = o;   o += align256((size_t)(kAdjAcc + ndirs) * 8);
+    t.total = o;
+    return t;
+}
+}  // namespace
+
+static void* tape_ckpt(pide2d* H, const TapeLayout& t, int k, int slot) {
+    return H->tape.base + t.ckpt + ((size_t)k * 5 + slot) * t.field;
+}
+static void* tape_seg(pide2d* H, const TapeLayout& t, int slot, int which) {
+    return H->tape.base + t.seg + ((size_t)slot * 2 + which) * t.field;
+}
+
+static pide2d_status save_checkpoint(pide2d* H, int k) {
+    const TapeLayout t = tape_layout(H->L, H->n_steps, H->tape.interval, H->tape.ndirs);
+    const size_t fb = H->L.size[R_V0];
+    for (size_t i = 0; i < H->hist.size(); ++i)
+        PIDE_CUDA(cudaMemcpyAsync(tape_ckpt(H, t, k, (int)i), H->field(H->hist[i]), fb, cudaMemcpyDeviceToDevice,
+                                  H->stream));
+    PIDE_CUDA(cudaMemcpyAsync(tape_ckpt(H, t, k, 4), H->field(H->bv), fb, cudaMemcpyDeviceToDevice, H->stream));
+    H->tape.ckpt_cnt[k] = (int)H->hist.size();
+    return PIDE2D_OK;
+}
+
+// the time-loop state at the start of time step k * interval + 1
+static pide2d_status restore_checkpoint(pide2d* H, int k) {
+    const TapeLayout t = tape_layout(H->L, H->n_steps, H->tape.interval, H->tape.ndirs);
+    const size_t fb = H->L.size[R_V0];
+    const int cnt = H->tape.ckpt_cnt[k];
+    for (int i = 0; i < cnt; ++i)
+        PIDE_CUDA(cudaMemcpyAsync(H->field(i), tape_ckpt(H, t, k, i), fb, cudaMemcpyDeviceToDevice, H->stream));
+    PIDE_CUDA(cudaMemcpyAsync(H->field(5), tape_ckpt(H, t, k, 4), fb, cudaMemcpyDeviceToDevice, H->stream));
+    H->hist.clear();
+    for (int i = 0; i < cnt; ++i) H->hist.push_back(i);
+    H->freel.clear();
+    for (int i = 4; i >= cnt; --i) H->freel.push_back(i);
+    H->bv = 5;
+    H->by = 6;
+    H->steps_done = k * H->tape.interval;
+    return PIDE2D_OK;
+}
+
+// during a segment replay: V^s (field `res`) and B_w V^s (now in field bv)
 template <typename R>
-static pide2d_status theta_step(pide2d* H, const int* list, int cnt, double theta, double ht, double tau_prev,
-                                double tau, int res, int* iters_out, double* resid_out) {
+static pide2d_status record_theta_step(pide2d* H, int res, double theta, double ht, double tau_prev, double tau) {
+    const TapeLayout t = tape_layout(H->L, H->n_steps, H->tape.interval, H->tape.ndirs);
+    if (H->seg_slot >= t.seg_slots) {
+        H->err = "tape segment overflow";
+        return PIDE2D_ERR_STATE;
+    }
+    const size_t fb = H->L.size[R_V0];
+    PIDE_CUDA(cudaMemcpyAsync(tape_seg(H, t, H->seg_slot, 0), H->field(res), fb, cudaMemcpyDeviceToDevice, H->stream));
+    PIDE_CUDA(cudaMemcpyAsync(tape_seg(H, t, H->seg_slot, 1), H->field(H->bv), fb, cudaMemcpyDeviceToDevice,
+                              H->stream));
+    H->seg_meta.push_back({theta, ht, tau_prev, tau});
+    H->seg_slot++;
+    return PIDE2D_OK;
+}
+
+// ---------------------------------------------------------------------------
+// the fixed-point loop of one theta step as a CUDA graph:
+//   reset(FpCtl.k, FpCtl.conv) -> while(cond) { dst_col, dst_row, check, col, inv } -> tally
+// k_fp_check clears the condition at convergence, at kmax or on a non-finite
+// residual, so every launch of the graph ends.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t kMaxLoopGraphs = 24;
+
+template <typename R>
+cudaError_t record_loop_graph(pide2d* H, cudaGraph_t g, const DstColArgs<R>& da, const DstRowArgs<R>& ra,
+                              const ColArgs<R>& ca, const InvArgs<R>& ia, const char** where) {
+    cudaStream_t cs = H->cap;
+    FpCtl* ctl = H->at<FpCtl>(R_CTL);
+    cudaError_t e = cudaSuccess;
+#define PIDE_GTRY(call)              \
+    do {                             \
+        e = (call);                  \
+        if (e != cudaSuccess) {      \
+            *where = #call;          \
+            return e;                \
+        }                            \
+    } while (0)
+    cudaGraphConditionalHandle hnd;
+    PIDE_GTRY(cudaGraphConditionalHandleCreate(&hnd, g, 1, cudaGraphCondAssignDefault));
+    cudaMemsetParams mp{};
+    mp.dst = ctl;                  // FpCtl.k and FpCtl.conv
+    mp.value = 0;
+    mp.elementSize = 4;
+    mp.width = 2;
+    mp.height = 1;
+    cudaGraphNode_t reset = nullptr, loop = nullptr;
+    PIDE_GTRY(cudaGraphAddMemsetNode(&reset, g, nullptr, 0, &mp));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hnd;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    PIDE_GTRY(cudaGraphAddNode(&loop, g, &reset, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+
+    // body: one iteration of the increment form of eq. 3.24
+    PIDE_GTRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    auto iteration = [&]() -> cudaError_t {
+        cudaError_t x;
+        if ((x = launch_dst_col<R>(da, cs)) != cudaSuccess) return x;
+        if ((x = cudaMemsetAsync(H->at<void>(R_RESID), 0, 16, cs)) != cudaSuccess) return x;
+        if ((x = launch_dst_row<R>(ra, cs)) != cudaSuccess) return x;
+        if ((x = launch_fp_check<R>(H->at<void>(R_RESID), ctl, H->tol, H->kmax, (unsigned long long)hnd, cs)) !=
+            cudaSuccess)
+            return x;
+        if ((x = launch_col<R>(ca, cs)) != cudaSuccess) return x;
+        return launch_row_inverse<R>(ia, cs);
+    };
+    e = iteration();
+    cudaGraph_t got = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &got);
+    if (e != cudaSuccess) { *where = "loop body launches"; return e; }
+    if (e2 != cudaSuccess) { *where = "cudaStreamEndCapture(body)"; return e2; }
+
+    // after the loop: fold the step's count into the statistics
+    PIDE_GTRY(cudaStreamBeginCaptureToGraph(cs, g, &loop, nullptr, 1, cudaStreamCaptureModeRelaxed));
+    e = launch_fp_tally(ctl, cs);
+    const cudaError_t e3 = cudaStreamEndCapture(cs, &got);
+    if (e != cudaSuccess) { *where = "launch_fp_tally"; return e; }
+    if (e3 != cudaSuccess) { *where = "cudaStreamEndCapture"; return e3; }
+#undef PIDE_GTRY
+    return cudaSuccess;
+}
+
+}  // namespace
+
+template <typename R>
+static pide2d_status loop_graph(pide2d* H, const DstColArgs<R>& da, const DstRowArgs<R>& ra, const ColArgs<R>& ca,
+                                const InvArgs<R>& ia, cudaGraphExec_t* exec) {
+    std::string key;
+    key.append(reinterpret_cast<const char*>(&da), sizeof da);
+    key.append(reinterpret_cast<const char*>(&ra), sizeof ra);
+    key.append(reinterpret_cast<const char*>(&ca), sizeof ca);
+    key.append(reinterpret_cast<const char*>(&ia), sizeof ia);
+    for (const auto& e : H->graphs)
+        if (e.key == key) {
+            *exec = e.exec;
+            return PIDE2D_OK;
+        }
+    if (!H->cap) PIDE_CUDA(cudaStreamCreateWithFlags(&H->cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    PIDE_CUDA(cudaGraphCreate(&g, 0));
+    const char* where = "";
+    cudaError_t e = record_loop_graph<R>(H, g, da, ra, ca, ia, &where);
+    cudaGraphExec_t ex = nullptr;
+    if (e == cudaSuccess) {
+        e = cudaGraphInstantiate(&ex, g, 0);
+        where = "cudaGraphInstantiate";
+    }
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        H->err = std::string("fixed-point loop graph: ") + where + ": " + cudaGetErrorString(e);
+        H->broken = true;
+        return PIDE2D_ERR_CUDA;
+    }
+    if (H->graphs.size() >= kMaxLoopGraphs) {
+        // the oldest entry may still be queued on the stream: wait before freeing it
+        PIDE_CUDA(cudaStreamSynchronize(H->stream));
+        cudaGraphExecDestroy(H->graphs.front().exec);
+        cudaGraphDestroy(H->graphs.front().graph);
+        H->graphs.erase(H->graphs.begin());
+    }
+    H->graphs.push_back({std::move(key), g, ex});
+    H->graph_builds++;
+    *exec = ex;
+    return PIDE2D_OK;
+}
+
+// read the device loop statistics (synchronises the stream)
+static pide2d_status read_ctl(pide2d* H) {
+    if (!H->ctl_dirty) return PIDE2D_OK;
+    PIDE_CUDA(cudaMemcpyAsync(&H->ctl, H->at<FpCtl>(R_CTL), sizeof(FpCtl), cudaMemcpyDeviceToHost, H->stream));
+    PIDE_CUDA(cudaStreamSynchronize(H->stream));
+    H->ctl_dirty = false;
+    return PIDE2D_OK;
+}
+
+// host-loop statistics combined with those of the device loop
+static pide2d_stats combined_stats(const pide2d* H) {
+    pide2d_stats s = H->stats;
+    const double nn = (double)H->grid.n * H->grid.n;
+    s.steps_done = H->steps_done;
+    s.fp_iters_total += H->ctl.total;
+    if (H->ctl.max_step > s.fp_iters_max) s.fp_iters_max = H->ctl.max_step;
+    s.cell_iters += nn * (double)(H->ctl.total + H->ctl.substeps);
+    if (H->last_step_device) s.last_resid = H->ctl.step_resid;
+    return s;
+}
+
+// NOT_CONVERGED if a device-loop theta step stopped without meeting eq. 3.25 since the last check
+static pide2d_status check_device_convergence(pide2d* H) {
+    if (H->ctl.nonconv > H->nonconv_seen) {
+        char buf[200];
+        std::snprintf(buf, sizeof buf,
+                      "fixed-point iteration not converged in %d theta step(s) (kmax %d, last resid %.3e, tol %.3e)",
+                      H->ctl.nonconv - H->nonconv_seen, H->kmax, H->ctl.last_resid, H->tol);
+        H->err = buf;
+        H->nonconv_seen = H->ctl.nonconv;
+        return PIDE2D_ERR_NOT_CONVERGED;
+    }
+    return PIDE2D_OK;
+}
+
+// Lagrange weights of the departure stencil for a shift of q cells (eq. 3.22):
+// first tap offset o, weights w and their derivatives dw/dq.
+static void sl_stencil(int order, double q, int* o, double w[4], double dw[4]) {
+    const int fl = (int)std::floor(q);
+    const double f = q - fl;
+    if (order == 1) {
+        *o = fl;
+        w[0] = 1.0 - f;
+        w[1] = f;
+        w[2] = w[3] = 0.0;
+        dw[0] = -1.0;
+        dw[1] = 1.0;
+        dw[2] = dw[3] = 0.0;
+    } else {
+        *o = fl - 1;
+        w[0] = -f * (f - 1.0) * (f - 2.0) / 6.0;
+        w[1] = (f + 1.0) * (f - 1.0) * (f - 2.0) / 2.0;
+        w[2] = -(f + 1.0) * f * (f - 2.0) / 2.0;
+        w[3] = (f + 1.0) * f * (f - 1.0) / 6.0;
+        dw[0] = -(3.0 * f * f - 6.0 * f + 2.0) / 6.0;
+        dw[1] = (3.0 * f * f - 4.0 * f - 1.0) / 2.0;
+        dw[2] = -(3.0 * f * f - 2.0 * f - 2.0) / 2.0;
+        dw[3] = (3.0 * f * f - 1.0) / 6.0;
+    }
+}
+
+// one implicit solve of eq. 3.24 by the fixed-point iteration (3.24)-(3.25),
+// in increment form with the DST-I preconditioner:
+//   (1 + h_t theta r_w) Y - h_t theta D Y - h_t theta B Y = W  (+ the far-field terms)
+// Y holds the start Y^{0} (its boundary ring is part of the input); on return
+// Y holds the solution and BY = B Y.  far = 0 solves with a zero far field
+// (halo and ring) and takes the weight spectra Wh/Whi as given, which is how
+// the transposed system of the adjoint is solved.
+template <typename R>
+struct SolveSpec {
+    St<R>* Y;
+    St<R>* BY;
+    const St<R>* W;
+    int far;
+    double Kd;
+    const void* Wh;
+    const void* Whi;
+    double theta, ht;
+    int step_end;
+    bool device_loop;
+};
+
+template <typename R>
+static pide2d_status fixed_point_solve(pide2d* H, const SolveSpec<R>& sp, int* iters_out, double* resid_out,
+                                       bool* conv_out) {
     const Geometry g = H->L.g;
     const int N = g.N;
     const double hg = H->h;
-    const double htt = ht * theta, htm = ht * (1.0 - theta);
+    const double htt = sp.ht * sp.theta;
     const double rw = H->par[1], a11 = H->par[4], a12 = H->par[5], a22 = H->par[6];
     const R d11 = (R)(0.5 * a11 / (hg * hg)), d22 = (R)(0.5 * a22 / (hg * hg)), d12 = (R)(0.25 * a12 / (hg * hg));
-    const double Kd_prev = H->contract.strike * std::exp(-H->model.r * tau_prev);
-    const double Kd_now = H->contract.strike * std::exp(-H->model.r * tau);
-    St<R>* Y = (St<R>*)H->field(res);
-    St<R>* W = H->at<St<R>>(R_W);
-    St<R>* BV = (St<R>*)H->field(H->bv);
-    St<R>* BY = (St<R>*)H->field(H->by);
+    St<R>* Y = sp.Y;
+    St<R>* BY = sp.BY;
     R* rres = H->at<R>(R_RES);
     R* dlt = H->at<R>(R_DLT);
     R* E = H->at<R>(R_E);
     const void* tw = H->at<void>(R_TWR);
+    *conv_out = false;
 
-    // Algorithm 1 steps 2-3: W and Y^{n,0}
-    PrepArgs<R> pa{};
-    pa.g = g;
-    for (int i = 0; i < 4; ++i) pa.V[i] = (const St<R>*)H->field(list[i < cnt ? i : 0]);
-    pa.hcount = cnt;
-    pa.BV = BV;
-    pa.W = W;
-    pa.Y = Y;
-    pa.cz = rres;            // the residual field is free until the first sweep of the step
-    pa.htm = (R)htm;
-    pa.rw = (R)rw;
-    pa.d11 = d11;
-    pa.d22 = d22;
-    pa.d12 = d12;
-    const double q[2] = {H->par[7] * ht / hg, H->par[8] * ht / hg};
-    // the departure stencil and the far-field tables reach N/4 cells at most
-    if (!(std::fabs(q[0]) <= N / 4) || !(std::fabs(q[1]) <= N / 4)) {
-        H->err = "semi-Lagrangian shift exceeds N/4 cells: time step too large";
-        return PIDE2D_ERR_ARG;
-    }
-    int o[2];
-    double w[2][4];
-    for (int ax = 0; ax < 2; ++ax) {
-        const int fl = (int)std::floor(q[ax]);
-        const double f = q[ax] - fl;
-        if (H->sl_order == 1) {
-            o[ax] = fl;
-            w[ax][0] = 1.0 - f;
-            w[ax][1] = f;
-            w[ax][2] = w[ax][3] = 0.0;
-        } else {
-            o[ax] = fl - 1;
-            w[ax][0] = -f * (f - 1.0) * (f - 2.0) / 6.0;
-            w[ax][1] = (f + 1.0) * (f - 1.0) * (f - 2.0) / 2.0;
-            w[ax][2] = -(f + 1.0) * f * (f - 2.0) / 2.0;
-            w[ax][3] = (f + 1.0) * f * (f - 1.0) / 6.0;
-        }
-    }
-    pa.o1 = o[0];
-    pa.o2 = o[1];
-    pa.nt = H->sl_order == 1 ? 2 : 4;
-    for (int i = 0; i < 4; ++i) {
-        pa.w1[i] = (R)w[0][i];
-        pa.w2[i] = (R)w[1][i];
-    }
-    pa.E1d = H->at<double>(R_E1D);
-    pa.E2d = H->at<double>(R_E2D);
-    pa.Kd_prev = Kd_prev;
-    pa.Kd_now = Kd_now;
-    pa.payoff = H->contract.payoff;
-    PIDE_LAUNCH(PIDE2D_KERNEL_PREP, launch_prep<R>(pa, H->stream));
-
-    // B_w Y^{n,0} by a full sweep (with far field) and the first residual
+    // B_w Y^{0} by a full sweep and the first residual
     FwdArgs<R> fa{};
     fa.g = g;
-    fa.mode = FWD_FULL;
+    fa.mode = sp.far ? FWD_FULL : FWD_FULL0;
     fa.Y = Y;
     fa.D = dlt;
     fa.E1 = (const R*)(sizeof(R) == 4 ? (const void*)H->at<float>(R_E1F) : (const void*)H->at<double>(R_E1D));
     fa.E2 = (const R*)(sizeof(R) == 4 ? (const void*)H->at<float>(R_E2F) : (const void*)H->at<double>(R_E2D));
-    fa.Kd = (R)Kd_now;
+    fa.Kd = (R)sp.Kd;
     fa.payoff = H->contract.payoff;
     fa.S = H->at<void>(R_S);
     fa.pair0 = 0;
     fa.npairs = N + 1;
     fa.tw = tw;
     PIDE_LAUNCH(PIDE2D_KERNEL_ROW_FORWARD_FULL, launch_row_forward<R>(fa, H->stream));
-    ColArgs<R> ca{};
+    // argument blocks of the iteration body are zeroed bytewise: their bytes key the loop graphs
+    ColArgs<R> ca;
+    std::memset(&ca, 0, sizeof ca);
     ca.g = g;
     ca.mode = COL_FULL;
     ca.S = H->at<void>(R_S);
-    ca.Wh = H->at<void>(R_WH);
+    ca.Wh = sp.Wh;
     ca.rlo = 0;
     ca.rhi = g.P + 2;
     ca.tw = tw;
     PIDE_LAUNCH(PIDE2D_KERNEL_COL_FULL, launch_col<R>(ca, H->stream));
-    InvArgs<R> ia{};
+    InvArgs<R> ia;
+    std::memset(&ia, 0, sizeof ia);
     ia.g = g;
     ia.mode = INV_FULL;
     ia.do_resid = 1;
     ia.S = H->at<void>(R_S);
     ia.BY = BY;
     ia.Y = Y;
-    ia.W = W;
+    ia.W = sp.W;
     ia.r = rres;
     ia.D = dlt;
     ia.htt = (R)htt;
@@ -327,7 +585,8 @@ static pide2d_status theta_step(pide2d* H, const int* list, int cnt, double thet
     ia.tw = tw;
     PIDE_LAUNCH(PIDE2D_KERNEL_ROW_INVERSE_FULL, launch_row_inverse<R>(ia, H->stream));
 
-    DstColArgs<R> da{};
+    DstColArgs<R> da;
+    std::memset(&da, 0, sizeof da);
     da.g = g;
     da.E = E;
     da.sin2 = H->at<R>(R_SIN2R);
@@ -336,7 +595,8 @@ static pide2d_status theta_step(pide2d* H, const int* list, int cnt, double thet
     da.c2 = 2.0 * htt * a22 / (hg * hg);
     da.scale = (2.0 / N) * (2.0 / N);
     da.tw = tw;
-    DstRowArgs<R> ra{};
+    DstRowArgs<R> ra;
+    std::memset(&ra, 0, sizeof ra);
     ra.g = g;
     ra.E = E;
     ra.Y = Y;
@@ -345,14 +605,34 @@ static pide2d_status theta_step(pide2d* H, const int* list, int cnt, double thet
     ra.S = H->at<void>(R_S);
     ra.tw = tw;
 
-    fa.mode = FWD_INCR;
-    fa.pair0 = (N / 2 + 2) / 2;
-    fa.npairs = N / 2;
     ca.mode = COL_INCR;
-    ca.Wh = H->at<void>(R_WHI);
+    ca.Wh = sp.Whi;
     ca.rlo = N / 2 + 2;
     ca.rhi = N / 2 + N + 2;
     ia.mode = INV_INCR;
+
+    if (sp.device_loop) {
+        // the iteration loop runs on the device (graph while-node); the step's
+        // fields Y and B_w Y are passed through FpCtl, so the graph depends on
+        // h_t and theta only; statistics are kept in FpCtl
+        FpCtl* ctl = H->at<FpCtl>(R_CTL);
+        ia.do_resid = 1;
+        ia.conv_flag = &ctl->conv;
+        ia.BY = nullptr;
+        ia.BYind = reinterpret_cast<St<R>* const*>(&ctl->BY);
+        ra.Y = nullptr;
+        ra.Yind = reinterpret_cast<St<R>* const*>(&ctl->Y);
+        cudaGraphExec_t ex = nullptr;
+        const pide2d_status gs = loop_graph<R>(H, da, ra, ca, ia, &ex);
+        if (gs != PIDE2D_OK) return gs;
+        PIDE_CUDA(launch_fp_setup(ctl, Y, BY, sp.step_end, H->stream));
+        PIDE_CUDA(cudaGraphLaunch(ex, H->stream));
+        H->ctl_dirty = true;
+        *iters_out = 0;
+        *resid_out = 0.0;
+        *conv_out = true;      // reported through FpCtl
+        return PIDE2D_OK;
+    }
 
     int k = 0;
     double resid = 0.0;
@@ -366,7 +646,8 @@ static pide2d_status theta_step(pide2d* H, const int* list, int cnt, double thet
         PIDE_CUDA(cudaStreamSynchronize(H->stream));
         resid = (double)rhost;
         conv = resid < H->tol;
-        // B_w of the increment keeps B_w Y^{n,k} current (needed for the next W);
+        if (!std::isfinite(resid)) break;
+        // B_w of the increment keeps B_w Y^{k} current (needed for the next W);
         // its row pass ran inside k_dst_row
         PIDE_LAUNCH(PIDE2D_KERNEL_COL_INCR, launch_col<R>(ca, H->stream));
         ia.do_resid = conv ? 0 : 1;
@@ -374,9 +655,91 @@ static pide2d_status theta_step(pide2d* H, const int* list, int cnt, double thet
         if (conv) break;
     }
     if (!conv) k = H->kmax;
-    std::swap(H->bv, H->by);
     *iters_out = k;
     *resid_out = resid;
+    *conv_out = conv;
+    return PIDE2D_OK;
+}
+
+// ---------------------------------------------------------------------------
+// one theta step (eq. 3.23): W and Y^{n,0} (Algorithm 1 steps 2-3), then the
+// implicit solve
+// ---------------------------------------------------------------------------
+template <typename R>
+static pide2d_status theta_step(pide2d* H, const int* list, int cnt, double theta, double ht, double tau_prev,
+                                double tau, int res, int step_end, int* iters_out, double* resid_out) {
+    const Geometry g = H->L.g;
+    const int N = g.N;
+    const double hg = H->h;
+    const double htm = ht * (1.0 - theta);
+    const double rw = H->par[1], a11 = H->par[4], a12 = H->par[5], a22 = H->par[6];
+    const R d11 = (R)(0.5 * a11 / (hg * hg)), d22 = (R)(0.5 * a22 / (hg * hg)), d12 = (R)(0.25 * a12 / (hg * hg));
+    const double Kd_prev = H->contract.strike * std::exp(-H->model.r * tau_prev);
+    const double Kd_now = H->contract.strike * std::exp(-H->model.r * tau);
+    St<R>* Y = (St<R>*)H->field(res);
+    St<R>* W = H->at<St<R>>(R_W);
+    St<R>* BV = (St<R>*)H->field(H->bv);
+    St<R>* BY = (St<R>*)H->field(H->by);
+
+    PrepArgs<R> pa{};
+    pa.g = g;
+    for (int i = 0; i < 4; ++i) pa.V[i] = (const St<R>*)H->field(list[i < cnt ? i : 0]);
+    pa.hcount = cnt;
+    pa.BV = BV;
+    pa.W = W;
+    pa.Y = Y;
+    pa.cz = H->at<R>(R_RES);   // the residual field is free until the first sweep of the step
+    pa.htm = (R)htm;
+    pa.rw = (R)rw;
+    pa.d11 = d11;
+    pa.d22 = d22;
+    pa.d12 = d12;
+    const double q[2] = {H->par[7] * ht / hg, H->par[8] * ht / hg};
+    // the departure stencil and the far-field tables reach N/4 cells at most
+    if (!(std::fabs(q[0]) <= N / 4) || !(std::fabs(q[1]) <= N / 4)) {
+        H->err = "semi-Lagrangian shift exceeds N/4 cells: time step too large";
+        return PIDE2D_ERR_ARG;
+    }
+    double w[2][4], dw[2][4];
+    sl_stencil(H->sl_order, q[0], &pa.o1, w[0], dw[0]);
+    sl_stencil(H->sl_order, q[1], &pa.o2, w[1], dw[1]);
+    pa.nt = H->sl_order == 1 ? 2 : 4;
+    for (int i = 0; i < 4; ++i) {
+        pa.w1[i] = (R)w[0][i];
+        pa.w2[i] = (R)w[1][i];
+    }
+    pa.E1d = H->at<double>(R_E1D);
+    pa.E2d = H->at<double>(R_E2D);
+    pa.Kd_prev = Kd_prev;
+    pa.Kd_now = Kd_now;
+    pa.payoff = H->contract.payoff;
+    PIDE_LAUNCH(PIDE2D_KERNEL_PREP, launch_prep<R>(pa, H->stream));
+
+    SolveSpec<R> sp{};
+    sp.Y = Y;
+    sp.BY = BY;
+    sp.W = W;
+    sp.far = 1;
+    sp.Kd = Kd_now;
+    sp.Wh = H->at<void>(R_WH);
+    sp.Whi = H->at<void>(R_WHI);
+    sp.theta = theta;
+    sp.ht = ht;
+    sp.step_end = step_end;
+    sp.device_loop = !H->host_loop && !H->prof && !H->force_host_loop;
+    int k = 0;
+    double resid = 0.0;
+    bool conv = false;
+    const pide2d_status s = fixed_point_solve<R>(H, sp, &k, &resid, &conv);
+    if (s != PIDE2D_OK) return s;
+    std::swap(H->bv, H->by);
+    if (H->seg_record) {
+        const pide2d_status rs = record_theta_step<R>(H, res, theta, ht, tau_prev, tau);
+        if (rs != PIDE2D_OK) return rs;
+    }
+    *iters_out = k;
+    *resid_out = resid;
+    if (sp.device_loop) return PIDE2D_OK;
     H->stats.cell_iters += (double)N * N * (k + 1);
     if (!conv) {
         char buf[160];
@@ -391,6 +754,10 @@ static pide2d_status theta_step(pide2d* H, const int* list, int cnt, double thet
 template <typename R>
 static pide2d_status do_step(pide2d* H, int* iters, double* resid) {
     pide2d_status st = PIDE2D_OK;
+    if (H->tape.base && !H->seg_record && H->steps_done % H->tape.interval == 0) {
+        const pide2d_status cs = save_checkpoint(H, H->steps_done / H->tape.interval);
+        if (cs != PIDE2D_OK) return cs;
+    }
     int k = 0;
     double r = 0.0;
     int ktot = 0;
@@ -403,7 +770,7 @@ static pide2d_status do_step(pide2d* H, int* iters, double* resid) {
             H->freel.pop_back();
             const int list[1] = {cur};
             const pide2d_status s = theta_step<R>(H, list, 1, 1.0, dt / 4.0, j * (dt / 4.0), (j + 1) * (dt / 4.0),
-                                                  res, &k, &r);
+                                                  res, j == 3 ? 1 : 0, &k, &r);
             if (s == PIDE2D_ERR_CUDA || s == PIDE2D_ERR_ARG) return s;
             if (s != PIDE2D_OK) st = s;
             if (cur != v0) H->freel.push_back(cur);
@@ -416,7 +783,8 @@ static pide2d_status do_step(pide2d* H, int* iters, double* resid) {
         H->freel.pop_back();
         const int cnt = (int)H->hist.size() < 4 ? (int)H->hist.size() : 4;
         const int n = H->steps_done + 1;
-        const pide2d_status s = theta_step<R>(H, H->hist.data(), cnt, H->theta, dt, (n - 1) * dt, n * dt, res, &k, &r);
+        const pide2d_status s = theta_step<R>(H, H->hist.data(), cnt, H->theta, dt, (n - 1) * dt, n * dt, res, 1,
+                                              &k, &r);
         if (s == PIDE2D_ERR_CUDA || s == PIDE2D_ERR_ARG) return s;
         if (s != PIDE2D_OK) st = s;
         H->hist.insert(H->hist.begin(), res);
@@ -428,6 +796,8 @@ static pide2d_status do_step(pide2d* H, int* iters, double* resid) {
     }
     H->steps_done++;
     H->stats.steps_done = H->steps_done;
+    H->last_step_device = !H->host_loop && !H->prof && !H->force_host_loop;
+    if (H->last_step_device) return st;   // counts are on the device (FpCtl)
     H->stats.fp_iters_total += ktot;
     if (ktot > H->stats.fp_iters_max) H->stats.fp_iters_max = ktot;
     H->stats.last_resid = r;
@@ -436,32 +806,14 @@ static pide2d_status do_step(pide2d* H, int* iters, double* resid) {
     return st;
 }
 
-template <typename R>
-static pide2d_status do_create(pide2d* H) {
-    const Geometry g = H->L.g;
-    const int N = g.N;
+// weights w (eq. 3.5), the R_I moment (eq. 3.3) and the rates (eq. 3.6) of a
+// model, into the given device buffers (params: the 9 values of pide2d_get_weights)
+static pide2d_status run_precompute(pide2d* H, const pide2d_model& m, double* omega, double* part, double* moment,
+                                    double* params) {
+    const int N = H->L.g.N;
     cudaStream_t s = H->stream;
-    // quadrature nodes
-    std::vector<double> gl(kGlTotal);
-    double* p = gl.data();
-    gauss_legendre(kGlNear, p, p + kGlNear);
-    gauss_legendre(kGlFar, p + 2 * kGlNear, p + 2 * kGlNear + kGlFar);
-    gauss_legendre(kGlEdge, p + 2 * (kGlNear + kGlFar), p + 2 * (kGlNear + kGlFar) + kGlEdge);
-    gauss_legendre(kGlPay, p + 2 * (kGlNear + kGlFar + kGlEdge), p + 2 * (kGlNear + kGlFar + kGlEdge) + kGlPay);
-    double* pv = p + 2 * (kGlNear + kGlFar + kGlEdge + kGlPay);
-    gauss_legendre(kGlVfar, pv, pv + kGlVfar);
-    double* dgl = H->at<double>(R_GL);
-    PIDE_CUDA(cudaMemsetAsync(H->ws, 0, H->L.total, s));
-    PIDE_CUDA(cudaMemcpyAsync(dgl, gl.data(), gl.size() * 8, cudaMemcpyHostToDevice, s));
-
-    // tables
-    PIDE_CUDA(launch_tables(N, H->s_lo1, H->s_lo2, H->h, H->at<double>(R_E1D), H->at<double>(R_E2D),
-                            H->at<float>(R_E1F), H->at<float>(R_E2F), H->at<double>(R_SIN2D), s));
-    PIDE_CUDA(launch_twiddles<R>(g.P, H->at<void>(R_TWR), s));
-    PIDE_CUDA(launch_twiddles<double>(g.P, H->at<void>(R_TWD), s));
-
+    const double* dgl = H->at<double>(R_GL);
     // Levy density constants (Sec. 4)
-    const pide2d_model& m = H->model;
     const double r11 = m.rho[0], r12 = m.rho[1], r22 = m.rho[2];
     const double det = r11 * r22 - r12 * r12;
     LevyParams L{};
@@ -492,28 +844,74 @@ static pide2d_status do_create(pide2d* H) {
     j.gl_vfar_w = j.gl_vfar_x + kGlVfar;
     j.n_vfar = kGlVfar;
     int nblocks = 0;
-    PIDE_CUDA(launch_weights(L, j, H->at<double>(R_OMEGA), H->at<double>(R_PART), &nblocks, s));
+    PIDE_CUDA(launch_weights(L, j, omega, part, &nblocks, s));
     const double* edge = dgl + 2 * (kGlNear + kGlFar);
-    PIDE_CUDA(launch_moment(L, 2.0 * H->h, edge, edge + kGlEdge, kGlEdge, kTanhSinhStep, H->at<double>(R_MOMENT), s));
-    PIDE_CUDA(launch_finalize(H->at<double>(R_PART), nblocks, H->at<double>(R_MOMENT), m.r, m.sigma_cov,
-                              H->at<double>(R_PARAMS), s));
+    PIDE_CUDA(launch_moment(L, 2.0 * H->h, edge, edge + kGlEdge, kGlEdge, kTanhSinhStep, moment, s));
+    PIDE_CUDA(launch_finalize(part, nblocks, moment, m.r, m.sigma_cov, params, s));
+    return PIDE2D_OK;
+}
 
-    // omega-hat = conj(fft2(Omega padded))/P^2 (eq. 3.13): FP64 row spectra in
-    // the (not yet used) state-field region, then FP64 column FFTs
+// conj(fft2(Omega zero-padded))/P^2 (eq. 3.13) of an N x N weight array: FP64
+// row spectra in `rows` ((P/2+1) x P x 16 bytes of scratch), then the FP64
+// column FFTs write Wh (and Whi, the increment-sweep variant, unless NULL)
+template <typename R>
+static pide2d_status weight_spectrum(pide2d* H, const double* omega, void* Wh, void* Whi, void* rows) {
+    const Geometry g = H->L.g;
     Geometry gd = g;
     gd.rows = g.P;
     gd.ng = g.P / 2 + 1;
     FwdArgs<double> wa{};
     wa.g = gd;
     wa.mode = FWD_WEIGHTS;
-    wa.omega = H->at<double>(R_OMEGA);
-    wa.S = H->field(0);
+    wa.omega = omega;
+    wa.S = rows;
     wa.pair0 = 0;
-    wa.npairs = N / 2;
+    wa.npairs = g.N / 2;
     wa.tw = H->at<void>(R_TWD);
-    PIDE_CUDA(launch_row_forward<double>(wa, s));
-    PIDE_CUDA(launch_weights_col<R>(gd, H->field(0), H->at<void>(R_WH), H->at<void>(R_WHI), H->at<void>(R_TWD), s));
+    PIDE_CUDA(launch_row_forward<double>(wa, H->stream));
+    PIDE_CUDA(launch_weights_col<R>(gd, rows, Wh, Whi, H->at<void>(R_TWD), H->stream));
+    return PIDE2D_OK;
+}
+
+template <typename R>
+static pide2d_status do_create(pide2d* H) {
+    const Geometry g = H->L.g;
+    const int N = g.N;
+    cudaStream_t s = H->stream;
+    // quadrature nodes
+    std::vector<double> gl(kGlTotal);
+    double* p = gl.data();
+    gauss_legendre(kGlNear, p, p + kGlNear);
+    gauss_legendre(kGlFar, p + 2 * kGlNear, p + 2 * kGlNear + kGlFar);
+    gauss_legendre(kGlEdge, p + 2 * (kGlNear + kGlFar), p + 2 * (kGlNear + kGlFar) + kGlEdge);
+    gauss_legendre(kGlPay, p + 2 * (kGlNear + kGlFar + kGlEdge), p + 2 * (kGlNear + kGlFar + kGlEdge) + kGlPay);
+    double* pv = p + 2 * (kGlNear + kGlFar + kGlEdge + kGlPay);
+    gauss_legendre(kGlVfar, pv, pv + kGlVfar);
+    double* dgl = H->at<double>(R_GL);
+    PIDE_CUDA(cudaMemsetAsync(H->ws, 0, H->L.total, s));
+    PIDE_CUDA(cudaMemcpyAsync(dgl, gl.data(), gl.size() * 8, cudaMemcpyHostToDevice, s));
+
+    // tables
+    PIDE_CUDA(launch_tables(N, H->s_lo1, H->s_lo2, H->h, H->at<double>(R_E1D), H->at<double>(R_E2D),
+                            H->at<float>(R_E1F), H->at<float>(R_E2F), H->at<double>(R_SIN2D), s));
+    PIDE_CUDA(launch_twiddles<R>(g.P, H->at<void>(R_TWR), s));
+    PIDE_CUDA(launch_twiddles<double>(g.P, H->at<void>(R_TWD), s));
+
+    // weights, R_I moment and rates (eqs. 3.3, 3.5, 3.6), then
+    // omega-hat = conj(fft2(Omega padded))/P^2 (eq. 3.13) with the FP64 row
+    // spectra in the (not yet used) state-field region
+    {
+        const pide2d_status ps = run_precompute(H, H->model, H->at<double>(R_OMEGA), H->at<double>(R_PART),
+                                                H->at<double>(R_MOMENT), H->at<double>(R_PARAMS));
+        if (ps != PIDE2D_OK) return ps;
+    }
+    {
+        const pide2d_status ws = weight_spectrum<R>(H, H->at<double>(R_OMEGA), H->at<void>(R_WH),
+                                                    H->at<void>(R_WHI), H->field(0));
+        if (ws != PIDE2D_OK) return ws;
+    }
     PIDE_CUDA(cudaMemsetAsync(H->field(0), 0, H->L.off[R_RES] - H->L.off[R_V0], s));
+    PIDE_CUDA(cudaMemsetAsync(H->at<void>(R_CTL), 0, sizeof(FpCtl), s));
 
     PIDE_CUDA(cudaMemcpyAsync(H->par, H->at<double>(R_PARAMS), 9 * 8, cudaMemcpyDeviceToHost, s));
     // sin^2 table in the transform precision
@@ -521,9 +919,11 @@ static pide2d_status do_create(pide2d* H) {
     {
         std::vector<R> s2(N + 1);
         std::vector<double> s2d(N + 1);
-        PIDE_CUDA(cudaMemcpy(s2d.data(), H->at<double>(R_SIN2D), (N + 1) * 8, cudaMemcpyDeviceToHost));
+        PIDE_CUDA(cudaMemcpyAsync(s2d.data(), H->at<double>(R_SIN2D), (N + 1) * 8, cudaMemcpyDeviceToHost, s));
+        PIDE_CUDA(cudaStreamSynchronize(s));
         for (int i = 0; i <= N; ++i) s2[i] = (R)s2d[i];
-        PIDE_CUDA(cudaMemcpy(H->at<R>(R_SIN2R), s2.data(), (N + 1) * sizeof(R), cudaMemcpyHostToDevice));
+        PIDE_CUDA(cudaMemcpyAsync(H->at<R>(R_SIN2R), s2.data(), (N + 1) * sizeof(R), cudaMemcpyHostToDevice, s));
+        PIDE_CUDA(cudaStreamSynchronize(s));
     }
     for (int i = 0; i < 9; ++i) {
         if (!std::isfinite(H->par[i])) {
@@ -664,6 +1064,299 @@ static pide2d_status do_price(pide2d* H, double* price) {
     return PIDE2D_OK;
 }
 
+template <typename R> St<R> st_host_one();
+template <> float2 st_host_one<float>() { return make_float2(1.f, 0.f); }
+template <> double st_host_one<double>() { return 1.0; }
+
+// ---------------------------------------------------------------------------
+// discrete adjoint of the time loop (see adjoint.cu for the recursion)
+// ---------------------------------------------------------------------------
+// B_w with the weight spectrum Wh applied to a full node field V (far field
+// g(s, tau) with discounted strike Kd in the halo when far = 1, zero when
+// far = 0), interior result written to the FP64 field `out` (pitch ldS)
+template <typename R>
+static pide2d_status jump_apply(pide2d* H, const St<R>* V, int far, double Kd, const void* Wh, double* out) {
+    const Geometry g = H->L.g;
+    const int N = g.N;
+    FwdArgs<R> fa{};
+    fa.g = g;
+    fa.mode = far ? FWD_FULL : FWD_FULL0;
+    fa.Y = V;
+    fa.E1 = (const R*)(sizeof(R) == 4 ? (const void*)H->at<float>(R_E1F) : (const void*)H->at<double>(R_E1D));
+    fa.E2 = (const R*)(sizeof(R) == 4 ? (const void*)H->at<float>(R_E2F) : (const void*)H->at<double>(R_E2D));
+    fa.Kd = (R)Kd;
+    fa.payoff = H->contract.payoff;
+    fa.S = H->at<void>(R_S);
+    fa.pair0 = 0;
+    fa.npairs = N + 1;
+    fa.tw = H->at<void>(R_TWR);
+    PIDE_CUDA(launch_row_forward<R>(fa, H->stream));
+    ColArgs<R> ca{};
+    ca.g = g;
+    ca.mode = COL_FULL;
+    ca.S = H->at<void>(R_S);
+    ca.Wh = Wh;
+    ca.rlo = 0;
+    ca.rhi = g.P + 2;
+    ca.tw = H->at<void>(R_TWR);
+    PIDE_CUDA(launch_col<R>(ca, H->stream));
+    InvArgs<R> ia{};
+    ia.g = g;
+    ia.mode = INV_OUT;
+    ia.do_resid = 0;
+    ia.S = H->at<void>(R_S);
+    ia.out = out;
+    ia.tw = H->at<void>(R_TWR);
+    PIDE_CUDA(launch_row_inverse<R>(ia, H->stream));
+    return PIDE2D_OK;
+}
+
+namespace {
+struct SavedState {
+    std::vector<int> hist, freel;
+    int bv, by, steps_done;
+    pide2d_stats stats;
+    bool last_step_device;
+};
+}  // namespace
+
+// the contributions of one stored state V^j (far field at tau_j) with the
+// coefficient field xi: <xi, V>, <xi, D-parts V> and <xi, B_{dw_k} V>
+template <typename R>
+static pide2d_status state_dots(pide2d* H, const TapeLayout& t, const St<R>* V, double tau, int ndirs) {
+    const Geometry g = H->L.g;
+    char* scr = H->tape.base + t.scr;
+    double* part = reinterpret_cast<double*>(scr + 3 * t.omega + t.part + 3 * 256 + t.rows);
+    double* acc = reinterpret_cast<double*>(H->tape.base + t.acc);
+    const double* xi = reinterpret_cast<const double*>(H->tape.base + t.adj + A_XI * t.field);
+    PIDE_CUDA(launch_dots_state<R>(g, xi, V, part, acc, 1.0, H->stream));
+    const double Kd = H->contract.strike * std::exp(-H->model.r * tau);
+    double* out = H->at<double>(R_OUT);
+    for (int k = 0; k < ndirs; ++k) {
+        const void* Whk = H->tape.base + t.spec + (size_t)(2 + k) * t.spec1;
+        const pide2d_status js = jump_apply<R>(H, V, 1, Kd, Whk, out);
+        if (js != PIDE2D_OK) return js;
+        PIDE_CUDA(launch_dot_field(g, xi, out, part, acc + kAdjAcc + k, H->stream));
+    }
+    return PIDE2D_OK;
+}
+
+template <typename R>
+static pide2d_status do_adjoint(pide2d* H, const pide2d_model* dirs, int ndirs, double* grad) {
+    const Geometry g = H->L.g;
+    const int N = g.N;
+    cudaStream_t s = H->stream;
+    const TapeLayout t = tape_layout(H->L, H->n_steps, H->tape.interval, H->tape.ndirs);
+    const size_t fb = H->L.size[R_V0];
+    char* tb = H->tape.base;
+    char* scr = tb + t.scr;
+    double* om_p = reinterpret_cast<double*>(scr);
+    double* om_m = reinterpret_cast<double*>(scr + t.omega);
+    double* om_d = reinterpret_cast<double*>(scr + 2 * t.omega);
+    double* part = reinterpret_cast<double*>(scr + 3 * t.omega);
+    double* moment = reinterpret_cast<double*>(scr + 3 * t.omega + t.part);
+    double* par_p = reinterpret_cast<double*>(scr + 3 * t.omega + t.part + 256);
+    double* par_m = reinterpret_cast<double*>(scr + 3 * t.omega + t.part + 512);
+    void* rows = scr + 3 * t.omega + t.part + 768;
+    double* dpart = reinterpret_cast<double*>(scr + 3 * t.omega + t.part + 768 + t.rows);
+    double* acc = reinterpret_cast<double*>(tb + t.acc);
+    auto afield = [&](int i) { return tb + t.adj + (size_t)i * t.field; };
+    St<R>* lam = reinterpret_cast<St<R>*>(afield(A_LAM));
+    St<R>* mu = reinterpret_cast<St<R>*>(afield(A_MU));
+    St<R>* bmu = reinterpret_cast<St<R>*>(afield(A_BMU));
+    St<R>* nu = reinterpret_cast<St<R>*>(afield(A_NU));
+    double* xi = reinterpret_cast<double*>(afield(A_XI));
+    double* pend = reinterpret_cast<double*>(afield(A_PEND));
+    double* out = H->at<double>(R_OUT);
+    void* whf = tb + t.spec;
+    void* whif = tb + t.spec + t.spec1;
+
+    // the final state is put back at the end
+    PIDE_CUDA(cudaStreamSynchronize(s));
+    SavedState sv{H->hist, H->freel, H->bv, H->by, H->steps_done, H->stats, H->last_step_device};
+    for (size_t i = 0; i < H->hist.size(); ++i)
+        PIDE_CUDA(cudaMemcpyAsync(tb + t.fin + i * t.field, H->field(H->hist[i]), fb, cudaMemcpyDeviceToDevice, s));
+    PIDE_CUDA(cudaMemcpyAsync(tb + t.fin + 4 * t.field, H->field(H->bv), fb, cudaMemcpyDeviceToDevice, s));
+
+    // derivatives of the weights and rates along each direction: central
+    // differences of the FP64 precompute (eqs. 3.3, 3.5, 3.6)
+    std::vector<double> dpar((size_t)ndirs * 9);
+    for (int k = 0; k < ndirs; ++k) {
+        const pide2d_model& d = dirs[k];
+        const double fields[7] = {d.delta, d.lambda, d.eta[0], d.eta[1], d.rho[0], d.rho[1], d.rho[2]};
+        const double base[7] = {H->model.delta, H->model.lambda, H->model.eta[0], H->model.eta[1],
+                                H->model.rho[0], H->model.rho[1], H->model.rho[2]};
+        double ratio = 0.0;
+        for (int i = 0; i < 7; ++i) ratio = std::fmax(ratio, std::fabs(fields[i]) / std::fmax(std::fabs(base[i]), 1e-3));
+        if (!(ratio > 0.0) || !std::isfinite(ratio)) {
+            for (int i = 0; i < 9; ++i) dpar[(size_t)k * 9 + i] = 0.0;
+            PIDE_CUDA(cudaMemsetAsync(tb + t.spec + (size_t)(2 + k) * t.spec1, 0, t.spec1, s));
+            continue;
+        }
+        const double eps = 1e-5 / ratio;
+        pide2d_model mp = H->model, mm = H->model;
+        mp.delta += eps * d.delta;           mm.delta -= eps * d.delta;
+        mp.lambda += eps * d.lambda;         mm.lambda -= eps * d.lambda;
+        for (int i = 0; i < 2; ++i) { mp.eta[i] += eps * d.eta[i]; mm.eta[i] -= eps * d.eta[i]; }
+        for (int i = 0; i < 3; ++i) { mp.rho[i] += eps * d.rho[i]; mm.rho[i] -= eps * d.rho[i]; }
+        pide2d_status ps = run_precompute(H, mp, om_p, part, moment, par_p);
+        if (ps != PIDE2D_OK) return ps;
+        ps = run_precompute(H, mm, om_m, part, moment, par_m);
+        if (ps != PIDE2D_OK) return ps;
+        PIDE_CUDA(launch_central_difference(om_p, om_m, 0.5 / eps, om_d, (size_t)N * N, s));
+        double hp[9], hm[9];
+        PIDE_CUDA(cudaMemcpyAsync(hp, par_p, 9 * 8, cudaMemcpyDeviceToHost, s));
+        PIDE_CUDA(cudaMemcpyAsync(hm, par_m, 9 * 8, cudaMemcpyDeviceToHost, s));
+        const pide2d_status ws =
+            weight_spectrum<R>(H, om_d, tb + t.spec + (size_t)(2 + k) * t.spec1, nullptr, rows);
+        if (ws != PIDE2D_OK) return ws;
+        PIDE_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i < 9; ++i) dpar[(size_t)k * 9 + i] = (hp[i] - hm[i]) * (0.5 / eps);
+    }
+    // the transposed jump operator: the same correlation with the weights
+    // flipped in both axes (w'_l = w_{-l-1}, which also carries the midpoint
+    // interpolation over to its transpose)
+    PIDE_CUDA(launch_flip_weights(H->at<double>(R_OMEGA), om_d, N, s));
+    {
+        const pide2d_status ws = weight_spectrum<R>(H, om_d, whf, whif, rows);
+        if (ws != PIDE2D_OK) return ws;
+    }
+
+    // lambda^{S} = e_{S0}; everything else zero
+    for (int i = 0; i < A_COUNT; ++i) PIDE_CUDA(cudaMemsetAsync(afield(i), 0, t.field, s));
+    PIDE_CUDA(cudaMemsetAsync(acc, 0, (size_t)(kAdjAcc + ndirs) * 8, s));
+    {
+        const St<R> one = st_host_one<R>();
+        PIDE_CUDA(cudaMemcpyAsync(lam + (size_t)(N / 2) * g.ldS + N / 2, &one, sizeof one, cudaMemcpyHostToDevice, s));
+        PIDE_CUDA(cudaStreamSynchronize(s));
+    }
+    const double hg = H->h;
+    const double rw = H->par[1], a11 = H->par[4], a12 = H->par[5], a22 = H->par[6];
+    const double d11 = 0.5 * a11 / (hg * hg), d22 = 0.5 * a22 / (hg * hg), d12 = 0.25 * a12 / (hg * hg);
+    pide2d_status worst = PIDE2D_OK;
+
+    H->force_host_loop = true;
+    for (int seg = t.nckpt - 1; seg >= 0; --seg) {
+        // replay the segment forward, keeping every theta step
+        pide2d_status rs = restore_checkpoint(H, seg);
+        if (rs != PIDE2D_OK) { H->force_host_loop = false; return rs; }
+        H->seg_record = true;
+        H->seg_slot = 0;
+        H->seg_meta.clear();
+        const int n_end = std::min((seg + 1) * H->tape.interval, H->n_steps);
+        while (H->steps_done < n_end) {
+            int k = 0;
+            double r = 0.0;
+            rs = do_step<R>(H, &k, &r);
+            if (rs == PIDE2D_ERR_CUDA || rs == PIDE2D_ERR_ARG || rs == PIDE2D_ERR_STATE) {
+                H->seg_record = false;
+                H->force_host_loop = false;
+                return rs;
+            }
+        }
+        H->seg_record = false;
+        // backwards through the segment's theta steps
+        for (int slot = H->seg_slot - 1; slot >= 0; --slot) {
+            const pide2d::StepMeta m = H->seg_meta[slot];
+            const double htt = m.ht * m.theta, htm = m.ht * (1.0 - m.theta);
+            const St<R>* Vs = reinterpret_cast<const St<R>*>(tape_seg(H, t, slot, 0));
+            const St<R>* Vp = reinterpret_cast<const St<R>*>(slot > 0 ? tape_seg(H, t, slot - 1, 0)
+                                                                        : tape_ckpt(H, t, seg, 0));
+            const St<R>* BVp = reinterpret_cast<const St<R>*>(slot > 0 ? tape_seg(H, t, slot - 1, 1)
+                                                                         : tape_ckpt(H, t, seg, 4));
+            // mu = A^{-T} lambda: the forward solver with the flipped weights and a zero far field
+            SolveSpec<R> sp{};
+            sp.Y = mu;
+            sp.BY = bmu;
+            sp.W = lam;
+            sp.far = 0;
+            sp.Kd = 0.0;
+            sp.Wh = whf;
+            sp.Whi = whif;
+            sp.theta = m.theta;
+            sp.ht = m.ht;
+            sp.step_end = 1;
+            sp.device_loop = false;
+            int k = 0;
+            double r = 0.0;
+            bool conv = false;
+            rs = fixed_point_solve<R>(H, sp, &k, &r, &conv);
+            if (rs != PIDE2D_OK) { H->force_host_loop = false; return rs; }
+            if (!conv) worst = PIDE2D_ERR_NOT_CONVERGED;
+            // nu = T_SL^T mu
+            const double q[2] = {H->par[7] * m.ht / hg, H->par[8] * m.ht / hg};
+            SlWeights w{};
+            int o1 = 0, o2 = 0;
+            sl_stencil(H->sl_order, q[0], &o1, w.w1, w.dw1);
+            sl_stencil(H->sl_order, q[1], &o2, w.w2, w.dw2);
+            const int nt = H->sl_order == 1 ? 2 : 4;
+            PIDE_CUDA(launch_sl_transpose<R>(g, mu, nu, o1, o2, nt, w, s));
+            // <mu, dT_SL/dq_i Z>: the departure shift q = b h_t / h
+            SlShiftArgs<R> sa{};
+            sa.mu = mu;
+            sa.V = Vp;
+            sa.BV = BVp;
+            sa.htm = htm;
+            sa.rw = rw;
+            sa.d11 = d11;
+            sa.d22 = d22;
+            sa.d12 = d12;
+            sa.o1 = o1;
+            sa.o2 = o2;
+            sa.nt = nt;
+            sa.w = w;
+            sa.E1d = H->at<double>(R_E1D);
+            sa.E2d = H->at<double>(R_E2D);
+            sa.Kd_prev = H->contract.strike * std::exp(-H->model.r * m.tau_prev);
+            sa.payoff = H->contract.payoff;
+            PIDE_CUDA(launch_sl_shift_dots<R>(g, sa, dpart, acc + 4, m.ht / hg, s));
+            // xi = h_t theta mu + (the h_t (1-theta) nu of the step after); the state V^s
+            PIDE_CUDA(launch_adj_xi<R>(g, mu, nu, xi, pend, htt, htm, s));
+            rs = state_dots<R>(H, t, Vs, m.tau, ndirs);
+            if (rs != PIDE2D_OK) { H->force_host_loop = false; return rs; }
+            // lambda^{s-1} = nu + htm ((D - r_w) nu + B^T nu)
+            if (htm != 0.0) {
+                rs = jump_apply<R>(H, nu, 0, 0.0, whf, out);
+                if (rs != PIDE2D_OK) { H->force_host_loop = false; return rs; }
+                PIDE_CUDA(launch_adj_combine<R>(g, nu, out, lam, htm, rw, d11, d22, d12, s));
+            } else {
+                PIDE_CUDA(cudaMemcpyAsync(lam, nu, fb, cudaMemcpyDeviceToDevice, s));
+            }
+        }
+    }
+    // V^0 (the payoff, far field at tau = 0) with the remaining h_t (1-theta) nu
+    PIDE_CUDA(launch_adj_xi<R>(g, mu, nullptr, xi, pend, 0.0, 0.0, s));
+    {
+        const pide2d_status rs = state_dots<R>(H, t, reinterpret_cast<const St<R>*>(tape_ckpt(H, t, 0, 0)), 0.0, ndirs);
+        if (rs != PIDE2D_OK) { H->force_host_loop = false; return rs; }
+    }
+    H->force_host_loop = false;
+
+    // put the final state back
+    for (size_t i = 0; i < sv.hist.size(); ++i)
+        PIDE_CUDA(cudaMemcpyAsync(H->field(sv.hist[i]), tb + t.fin + i * t.field, fb, cudaMemcpyDeviceToDevice, s));
+    PIDE_CUDA(cudaMemcpyAsync(H->field(sv.bv), tb + t.fin + 4 * t.field, fb, cudaMemcpyDeviceToDevice, s));
+    H->hist = sv.hist;
+    H->freel = sv.freel;
+    H->bv = sv.bv;
+    H->by = sv.by;
+    H->steps_done = sv.steps_done;
+    H->stats = sv.stats;
+    H->last_step_device = sv.last_step_device;
+
+    std::vector<double> a(kAdjAcc + ndirs);
+    PIDE_CUDA(cudaMemcpyAsync(a.data(), acc, a.size() * 8, cudaMemcpyDeviceToHost, s));
+    PIDE_CUDA(cudaStreamSynchronize(s));
+    // dJ/dp = <G, dw> + sum_ij da_ij <xi, D_ij V> - dr_w <xi, V> + sum_i db_i <mu, dT/dq_i Z> h_t/h
+    for (int k = 0; k < ndirs; ++k) {
+        const double* dp = &dpar[(size_t)k * 9];   // sum_w, r_w, kappa1, kappa2, a11, a12, a22, b1, b2
+        const double ih2 = 1.0 / (hg * hg);
+        grad[k] = a[kAdjAcc + k] + ih2 * (0.5 * dp[4] * a[1] + 0.25 * dp[5] * a[2] + 0.5 * dp[6] * a[3]) -
+                  dp[1] * a[0] + dp[7] * a[4] + dp[8] * a[5];
+    }
+    return worst;
+}
+
 // ---------------------------------------------------------------------------
 // public entry points
 // ---------------------------------------------------------------------------
@@ -719,6 +1412,7 @@ pide2d_status pide2d_create(const pide2d_grid* grid, const pide2d_model* model, 
         }
     }
     if (e.empty() && opts && (opts->kmax < 0 || opts->kmax > 100000)) e = "opts.kmax out of range";
+    if (e.empty() && opts && (opts->host_loop < 0 || opts->host_loop > 1)) e = "opts.host_loop must be 0 or 1";
     if (!e.empty()) { g_create_error = e; return PIDE2D_ERR_ARG; }
 
     Layout L;
@@ -746,6 +1440,7 @@ pide2d_status pide2d_create(const pide2d_grid* grid, const pide2d_model* model, 
     H->tol = fp_tol;
     H->kmax = (opts && opts->kmax > 0) ? opts->kmax : 100;
     H->damping = opts ? (opts->damping != 0) : 1;
+    H->host_loop = opts ? (opts->host_loop != 0) : 0;
     H->n_steps = n_steps;
     H->sl_order = grid->sl_order == 0 ? 3 : grid->sl_order;
     H->L = L;
@@ -767,12 +1462,23 @@ pide2d_status pide2d_create(const pide2d_grid* grid, const pide2d_model* model, 
     return PIDE2D_OK;
 }
 
-pide2d_status pide2d_step(pide2d_t* H, int* fp_iters, double* fp_resid) {
-    if (!H) return PIDE2D_ERR_ARG;
+static pide2d_status step_nosync(pide2d_t* H, int* fp_iters, double* fp_resid) {
     if (H->broken) { H->err = "handle unusable after a CUDA error"; return PIDE2D_ERR_STATE; }
     if (H->steps_done >= H->n_steps) { H->err = "all time steps done"; return PIDE2D_ERR_STATE; }
     return H->grid.precision == PIDE2D_FP64 ? do_step<double>(H, fp_iters, fp_resid)
                                             : do_step<float>(H, fp_iters, fp_resid);
+}
+
+pide2d_status pide2d_step(pide2d_t* H, int* fp_iters, double* fp_resid) {
+    if (!H) return PIDE2D_ERR_ARG;
+    pide2d_status s = step_nosync(H, fp_iters, fp_resid);
+    if (s == PIDE2D_ERR_CUDA || s == PIDE2D_ERR_STATE || s == PIDE2D_ERR_ARG || !H->last_step_device) return s;
+    const pide2d_status r = read_ctl(H);
+    if (r != PIDE2D_OK) return r;
+    if (fp_iters) *fp_iters = H->ctl.last_step_k;
+    if (fp_resid) *fp_resid = H->ctl.step_resid;
+    const pide2d_status c = check_device_convergence(H);
+    return s != PIDE2D_OK ? s : c;
 }
 
 pide2d_status pide2d_solve(pide2d_t* H, double* price, double* values_out, pide2d_stats* stats) {
@@ -780,9 +1486,15 @@ pide2d_status pide2d_solve(pide2d_t* H, double* price, double* values_out, pide2
     if (H->broken) { H->err = "handle unusable after a CUDA error"; return PIDE2D_ERR_STATE; }
     pide2d_status worst = PIDE2D_OK;
     while (H->steps_done < H->n_steps) {
-        const pide2d_status s = pide2d_step(H, nullptr, nullptr);
-        if (s == PIDE2D_ERR_CUDA || s == PIDE2D_ERR_STATE) return s;
+        // device-loop steps are queued back to back; the host waits once, below
+        const pide2d_status s = step_nosync(H, nullptr, nullptr);
+        if (s == PIDE2D_ERR_CUDA || s == PIDE2D_ERR_STATE || s == PIDE2D_ERR_ARG) return s;
         if (s != PIDE2D_OK) worst = s;
+    }
+    {
+        const pide2d_status r = read_ctl(H);
+        if (r != PIDE2D_OK) return r;
+        if (check_device_convergence(H) != PIDE2D_OK) worst = PIDE2D_ERR_NOT_CONVERGED;
     }
     if (price) {
         const pide2d_status s = H->grid.precision == PIDE2D_FP64 ? do_price<double>(H, price) : do_price<float>(H, price);
@@ -792,7 +1504,7 @@ pide2d_status pide2d_solve(pide2d_t* H, double* price, double* values_out, pide2
         const pide2d_status s = pide2d_get_values(H, values_out);
         if (s != PIDE2D_OK) return s;
     }
-    if (stats) *stats = H->stats;
+    if (stats) *stats = combined_stats(H);
     return worst;
 }
 
@@ -857,6 +1569,48 @@ pide2d_status pide2d_profile_read(pide2d_t* H, pide2d_kernel_times* out) {
     return PIDE2D_OK;
 }
 
+pide2d_status pide2d_tape_bytes(pide2d_t* H, int interval, int ndirs, size_t* bytes) {
+    if (!H || !bytes || interval < 1 || ndirs < 0 || ndirs > 16) return PIDE2D_ERR_ARG;
+    *bytes = tape_layout(H->L, H->n_steps, interval, ndirs).total;
+    return PIDE2D_OK;
+}
+
+pide2d_status pide2d_record(pide2d_t* H, void* tape, size_t bytes, int interval, int ndirs) {
+    if (!H) return PIDE2D_ERR_ARG;
+    if (H->broken) return PIDE2D_ERR_STATE;
+    if (H->steps_done != 0) { H->err = "pide2d_record must precede the first step"; return PIDE2D_ERR_STATE; }
+    if (interval < 1 || ndirs < 0 || ndirs > 16) { H->err = "interval >= 1 and 0 <= ndirs <= 16"; return PIDE2D_ERR_ARG; }
+    const TapeLayout t = tape_layout(H->L, H->n_steps, interval, ndirs);
+    if (!tape || ((uintptr_t)tape & 255) != 0 || bytes < t.total) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "tape must be 256-byte aligned device memory of >= %zu bytes", t.total);
+        H->err = buf;
+        return PIDE2D_ERR_WORKSPACE;
+    }
+    H->tape.base = static_cast<char*>(tape);
+    H->tape.bytes = bytes;
+    H->tape.interval = interval;
+    H->tape.ndirs = ndirs;
+    H->tape.nckpt = t.nckpt;
+    H->tape.seg_slots = t.seg_slots;
+    H->tape.ckpt_cnt.assign(t.nckpt, 0);
+    return PIDE2D_OK;
+}
+
+pide2d_status pide2d_adjoint(pide2d_t* H, const pide2d_model* dirs, int ndirs, double* grad) {
+    if (!H || (ndirs > 0 && (!dirs || !grad)) || ndirs < 0) return PIDE2D_ERR_ARG;
+    if (H->broken) { H->err = "handle unusable after a CUDA error"; return PIDE2D_ERR_STATE; }
+    if (!H->tape.base) { H->err = "no tape: call pide2d_record before the first step"; return PIDE2D_ERR_STATE; }
+    if (H->steps_done != H->n_steps) { H->err = "pide2d_adjoint needs the finished solve"; return PIDE2D_ERR_STATE; }
+    if (ndirs > H->tape.ndirs) { H->err = "more directions than the tape was sized for"; return PIDE2D_ERR_ARG; }
+    {
+        const pide2d_status r = read_ctl(H);
+        if (r != PIDE2D_OK) return r;
+    }
+    return H->grid.precision == PIDE2D_FP64 ? do_adjoint<double>(H, dirs, ndirs, grad)
+                                            : do_adjoint<float>(H, dirs, ndirs, grad);
+}
+
 const char* pide2d_last_error(const pide2d_t* H) {
     if (!H) return g_create_error.c_str();
     return H->err.c_str();
@@ -869,6 +1623,12 @@ void pide2d_destroy(pide2d_t* H) {
         cudaEventDestroy(r.b);
     }
     for (auto e : H->pool) cudaEventDestroy(e);
+    if (!H->graphs.empty()) cudaStreamSynchronize(H->stream);
+    for (auto& g : H->graphs) {
+        cudaGraphExecDestroy(g.exec);
+        cudaGraphDestroy(g.graph);
+    }
+    if (H->cap) cudaStreamDestroy(H->cap);
     delete H;
 }
 

@@ -61,8 +61,10 @@ template <typename R> struct InvArgs {
     Geometry g;
     int mode;
     int do_resid;
+    const int* conv_flag;    // device flag; when set, do_resid = !*conv_flag (device-side loop)
     const void* S;
     St<R>* BY;               // FULL: set, INCR: accumulate
+    St<R>* const* BYind;     // device-side loop: BY is read from *BYind
     double* out;             // OUT: plain FP64 result field (pitch ldS)
     const St<R>* Y;          // FULL: Y^0 (with ring)
     const St<R>* W;          // FULL: W
@@ -85,6 +87,7 @@ template <typename R> struct DstRowArgs {
     Geometry g;
     const R* E;
     St<R>* Y;
+    St<R>* const* Yind;      // device-side loop: Y is read from *Yind (set per step on the device)
     R* D;                    // increment out (interior)
     void* resid;             // R-typed max |D| / max(1, |Y|) as unsigned bits
     void* S;                 // spectrum rows of the increment (R2C), cpx<R>
@@ -125,6 +128,61 @@ template <typename R> cudaError_t launch_greeks(const Geometry& g, const St<R>* 
                                                 cudaStream_t s);
 template <typename R> cudaError_t launch_state_to_double(const Geometry& g, const St<R>* src, double* dst,
                                                         int ld_dst, cudaStream_t s);
+
+// device-side fixed-point loop control (loop_ctl.cu)
+struct FpCtl {
+    int k;                   // iterations of the current theta step (reset per step)
+    int conv;                // 1 once the eq. 3.25 test passed in the current step
+    int total;               // iterations over all steps run by the device loop
+    int step_k;              // iterations of the current time step (the damped step has four theta steps)
+    int max_step;            // largest per-time-step count
+    int last_step_k;         // count of the last completed time step
+    int nonconv;             // theta steps that stopped at kmax or on a non-finite residual
+    int substeps;            // theta steps run by the device loop
+    double last_resid;       // last eq. 3.25 quantity
+    double step_resid;       // its value at the end of the last completed time step
+    void* Y;                 // fields of the current theta step (the loop graph reads them here)
+    void* BY;
+    int step_end;            // 1 if the current theta step ends a time step
+};
+// discrete adjoint (adjoint.cu)
+struct SlWeights {
+    double w1[4], w2[4];     // departure weights per axis (eq. 3.22)
+    double dw1[4], dw2[4];   // their derivatives with respect to the shift in cells
+};
+template <typename R> struct SlShiftArgs {
+    const St<R>* mu;         // adjoint of V^s
+    const St<R>* V;          // V^{s-1} (ring included)
+    const St<R>* BV;         // B_w V^{s-1}
+    double htm, rw, d11, d22, d12;
+    int o1, o2, nt;
+    SlWeights w;
+    const double* E1d; const double* E2d;
+    double Kd_prev;          // K e^{-r tau_{s-1}}
+    int payoff;
+};
+int adjoint_dot_blocks(int N);
+cudaError_t launch_flip_weights(const double* om, double* out, int N, cudaStream_t s);
+cudaError_t launch_central_difference(const double* a, const double* b, double scale, double* out, size_t n,
+                                      cudaStream_t s);
+template <typename R> cudaError_t launch_sl_transpose(const Geometry& g, const St<R>* mu, St<R>* nu, int o1, int o2,
+                                                     int nt, const SlWeights& w, cudaStream_t s);
+template <typename R> cudaError_t launch_adj_combine(const Geometry& g, const St<R>* nu, const double* bnu,
+                                                    St<R>* lam, double htm, double rw, double d11, double d22,
+                                                    double d12, cudaStream_t s);
+template <typename R> cudaError_t launch_adj_xi(const Geometry& g, const St<R>* mu, const St<R>* nu, double* xi,
+                                               double* pend, double htt, double htm_s, cudaStream_t s);
+template <typename R> cudaError_t launch_dots_state(const Geometry& g, const double* xi, const St<R>* V, double* part,
+                                                   double* acc, double scale, cudaStream_t s);
+cudaError_t launch_dot_field(const Geometry& g, const double* xi, const double* out, double* part, double* acc,
+                             cudaStream_t s);
+template <typename R> cudaError_t launch_sl_shift_dots(const Geometry& g, const SlShiftArgs<R>& a, double* part,
+                                                      double* acc, double scale, cudaStream_t s);
+
+template <typename R> cudaError_t launch_fp_check(const void* resid, FpCtl* ctl, double tol, int kmax,
+                                                 unsigned long long cond_handle, cudaStream_t s);
+cudaError_t launch_fp_tally(FpCtl* ctl, cudaStream_t s);
+cudaError_t launch_fp_setup(FpCtl* ctl, void* Y, void* BY, int step_end, cudaStream_t s);
 
 // precompute (precompute.cu)
 struct LevyParams {

@@ -237,6 +237,8 @@ PIDE_FFT_KERNEL(R, P) k_row_inverse(InvArgs<R> a) {
     const C* S = (const C*)a.S;
     const int rows = a.g.rows;
     const C* tw = (const C*)a.tw;
+    // the device-side fixed-point loop decides on the device whether a residual is needed
+    const bool do_resid = a.conv_flag ? (*a.conv_flag == 0) : (a.do_resid != 0);
     auto load = [&](int pos) -> C {
         const bool hi = pos > P / 2;
         const int k = hi ? P - pos : pos;
@@ -251,9 +253,10 @@ PIDE_FFT_KERNEL(R, P) k_row_inverse(InvArgs<R> a) {
         return mk<R>(xa.x - xb.y, xa.y + xb.x);
     };
     const int ld = a.g.ldS, ldR = a.g.ldR;
+    S_* const BYv = a.BYind ? *a.BYind : a.BY;
     auto epilogue = [&](int m1, C zz) {
         if (m1 == 0) {
-            if (a.do_resid) {
+            if (do_resid) {
                 buf[padi(0)] = mk<R>(0, 0);
                 buf[padi(N)] = mk<R>(0, 0);
             }
@@ -272,30 +275,30 @@ PIDE_FFT_KERNEL(R, P) k_row_inverse(InvArgs<R> a) {
                 if (a.mode == INV_OUT) {
                     a.out[idx] = (double)zv;
                 } else if (a.mode == INV_FULL) {
-                    a.BY[idx] = st_from_r<S_, R>(zv);
-                    if (a.do_resid) {
+                    BYv[idx] = st_from_r<S_, R>(zv);
+                    if (do_resid) {
                         const S_ y = a.Y[idx];
                         rr[half] = st_diff(a.W[idx], y) + a.htt * zv - a.htt * a.rw * st_r(y)
                                    + a.htt * diff_state(a.Y, idx, ld, a.d11, a.d22, a.d12);
                     }
                 } else {  // INV_INCR
-                    a.BY[idx] = st_add(a.BY[idx], zv);
-                    if (a.do_resid) {
+                    BYv[idx] = st_add(BYv[idx], zv);
+                    if (do_resid) {
                         const R d = a.D[idr];
                         rr[half] = a.r[idr] + a.htt * zv
                                    - (a.cid * d - a.htt * diff_plain(a.D, idr, ldR, a.d11, a.d22, a.d12));
                     }
                 }
-                if (a.do_resid) a.r[idr] = rr[half];
+                if (do_resid) a.r[idr] = rr[half];
             }
         }
-        if (a.do_resid) {
+        if (do_resid) {
             buf[padi(m1)] = mk<R>(rr[0], rr[1]);
             buf[padi(P - m1)] = mk<R>(-rr[0], -rr[1]);
         }
     };
     block_fft<R, +1, P>(buf, t, tw, load, epilogue);
-    if (!a.do_resid) return;   // uniform across the block
+    if (!do_resid) return;   // uniform across the block
     constexpr int GE = rgroup<R>();
     auto store_e = [&](int k, C zz) {
         if (k >= N) return;
@@ -392,6 +395,7 @@ PIDE_FFT_KERNEL(R, P) k_dst_row(DstRowArgs<R> a) {
         }
         return mk<R>(ea, eb);
     };
+    St<R>* const Yv = a.Yind ? *a.Yind : a.Y;
     R rmax = 0;
     const int ld = a.g.ldS, ldR = a.g.ldR;
     // the increment also enters the next B_w sweep: it is laid out at its
@@ -402,16 +406,16 @@ PIDE_FFT_KERNEL(R, P) k_dst_row(DstRowArgs<R> a) {
             da = R(-0.5) * zz.y;
             {
                 const size_t idx = (size_t)m2 * ld + m1;
-                const St<R> y = st_add(a.Y[idx], da);
-                a.Y[idx] = y;
+                const St<R> y = st_add(Yv[idx], da);
+                Yv[idx] = y;
                 a.D[(size_t)m2 * ldR + m1] = da;
                 rmax = fmax(rmax, fabs(da) / fmax(R(1), fabs(st_r(y))));
             }
             if (hasb) {
                 db = R(0.5) * zz.x;
                 const size_t idx = (size_t)(m2 + 1) * ld + m1;
-                const St<R> y = st_add(a.Y[idx], db);
-                a.Y[idx] = y;
+                const St<R> y = st_add(Yv[idx], db);
+                Yv[idx] = y;
                 a.D[(size_t)(m2 + 1) * ldR + m1] = db;
                 rmax = fmax(rmax, fabs(db) / fmax(R(1), fabs(st_r(y))));
             }

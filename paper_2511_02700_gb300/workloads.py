@@ -51,7 +51,10 @@ LARGE_FP32_4096 = Workload("large_fp32_4096", n=4096, steps=1024, alpha=0.5, tol
 
 
 def batch_draw(count: int = 512, seed: int = 2511027):
-    """Independent pricings with seed-drawn parameters (uniform ranges)."""
+    """Independent pricings with seed-drawn parameters (uniform ranges):
+    alpha [0.1, 0.45], kappa [0.2, 1], sigma_i [0.1, 0.4], corr [-0.6, 0.6],
+    beta_i [-0.2, 0.2], K [80, 120], T [0.1, 2]; N from {128, 256, 512} with
+    N/4 steps; FP32-bulk, fixed-point tol 1e-8."""
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
     for i in range(count):
@@ -64,7 +67,7 @@ def batch_draw(count: int = 512, seed: int = 2511027):
         T = float(rng.uniform(0.1, 2.0))
         n = int(rng.choice([128, 256, 512]))
         out.append(Workload(f"batch_{i}", n=n, steps=n // 4, alpha=a, kappa=kap, beta=b, sigma=s, corr=c,
-                            strike=K, maturity=T, precision="fp32"))
+                            strike=K, maturity=T, tol=1e-8, precision="fp32"))
     return out
 
 

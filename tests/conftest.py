@@ -57,3 +57,14 @@ def gpu_solver(w, payoff=0, **kw):
     model = B.model_from_subordinated_bm(w.alpha, w.kappa, w.beta, w.sigma, w.corr, w.r)
     contract = B.make_contract(payoff, w.strike, w.maturity)
     return B.Solver(grid, model, contract, w.steps, theta=w.theta, tol=w.tol, **kw)
+
+
+def gpu_job(w, payoff=0):
+    """pide2d_job (C ABI batch entry) for a workloads.Workload."""
+    from paper_2511_02700_gb300 import binding as B
+    prec = B.PIDE2D_FP64 if w.precision == "fp64" else B.PIDE2D_FP32_BULK
+    grid = B.make_grid(w.n, prec, w.sl_order, half_width=w.half_width)
+    model = B.model_from_subordinated_bm(w.alpha, w.kappa, w.beta, w.sigma, w.corr, w.r)
+    contract = B.make_contract(payoff, w.strike, w.maturity)
+    return B.make_job(grid, model, contract, w.steps, theta=w.theta, tol=w.tol)
+

@@ -1,0 +1,69 @@
+"""pide2d_batch_solve: many independent pricings (uneven grids) on one GPU.
+
+Each job of a batch runs the same kernels as a single pide2d_solve, so the
+batch prices must equal the single-solve prices exactly; one small job is
+also checked against the oracle at the FP32-bulk tolerance.
+"""
+import pytest
+
+from conftest import gpu_job, gpu_solver, oracle_inputs
+from paper_2511_02700_gb300.workloads import batch_draw, with_
+
+
+def test_batch_workspace_bytes_and_arguments():
+    from paper_2511_02700_gb300 import binding as B
+    from paper_2511_02700_gb300 import build
+    build.build()
+    jobs = [gpu_job(with_(w, n=n)) for w, n in zip(batch_draw(3), (64, 256, 128))]
+    one = B.pide2d_workspace_bytes(jobs[1].grid)
+    nb = B.pide2d_batch_workspace_bytes(jobs, 2)
+    assert nb >= 2 * one and nb < 2 * one + 512
+    assert B.pide2d_batch_workspace_bytes(jobs, 8) == B.pide2d_batch_workspace_bytes(jobs, 3)
+    with pytest.raises(B.PideError):
+        B.pide2d_batch_workspace_bytes(jobs, 0)
+    bad = gpu_job(with_(batch_draw(1)[0], n=100))
+    with pytest.raises(B.PideError):
+        B.pide2d_batch_workspace_bytes(jobs + [bad], 2)
+
+
+def _small_batch(count=24):
+    out = []
+    for i, w in enumerate(batch_draw(count, seed=77)):
+        n = (32, 64, 128)[i % 3]
+        out.append(with_(w, n=n, steps=n // 8))
+    return out
+
+
+@pytest.mark.gpu
+def test_batch_equals_single_solves():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_02700_gb300 import binding as B
+    ws = _small_batch()
+    prices, sts, stats = B.solve_batch([gpu_job(w) for w in ws], lanes=6)
+    assert all(s == 0 for s in sts), sts
+    assert stats.jobs_done == len(ws) and stats.failures == 0
+    cells = 0.0
+    for w, p in zip(ws, prices):
+        s = gpu_solver(w)
+        p1, _, st1, _ = s.solve()
+        s.close()
+        assert p == p1, (w.name, p, p1)
+        cells += st1.cell_iters
+    assert stats.cell_iters == cells
+
+
+@pytest.mark.gpu
+def test_batch_job_matches_oracle():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle as O
+    from paper_2511_02700_gb300 import binding as B
+    w = with_(batch_draw(1, seed=5)[0], n=64, steps=16)
+    prices, sts, _ = B.solve_batch([gpu_job(w), gpu_job(with_(w, n=32, steps=8))], lanes=2)
+    m, g, c = oracle_inputs(w)
+    ref = O.Scheme(m, g, c, w.steps, theta=w.theta, tol=w.tol, sl_order=w.sl_order).solve().price
+    assert sts == [0, 0]
+    assert abs(prices[0] - ref) <= 1e-5 * abs(ref), (prices[0], ref)
