@@ -44,6 +44,8 @@ def args_parse():
     p.add_argument("--n", type=int, default=4096, help="grid size (default: the large 4096^2 workload)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-batch", action="store_true", help="skip the 512-pricing batch measurement")
+    p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
     p.add_argument("--host-loop", action="store_true",
                    help="drive the fixed-point loop from the host in the timed region too (one launch per "
                         "kernel, as the profilers see it)")
@@ -338,6 +340,8 @@ def run_ours(a):
     cb = None
     if not a.no_cpu_baseline and ws == 1:
         cb = oracle_sample(steps=6, warmup=1)
+    batch = None if (a.no_batch or ws > 1) else run_batch(B, torch, dev)
+    adjoint = None if (a.no_adjoint or ws > 1) else run_adjoint(B, torch, dev)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": t_max / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -347,9 +351,122 @@ def run_ours(a):
                        "l2": "working set > L2 (inputs larger than the 129 MB L2, no flush)"},
             "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": gpu_launches,
             "clocks": ck, "fp_iters_per_step": iters, "create_s": create_s, "kernels": kernels,
+            "batch": batch, "adjoint": adjoint,
             "loop": "host-driven fixed-point loop" if a.host_loop else
                     "device-side fixed-point loop (CUDA graph while-node), one host sync per time step"}
     print(json.dumps(line), flush=True)
+
+
+def _job(B, w, payoff=0):
+    prec = B.PIDE2D_FP64 if w.precision == "fp64" else B.PIDE2D_FP32_BULK
+    grid = B.make_grid(w.n, prec, w.sl_order, half_width=w.half_width)
+    model = B.model_from_subordinated_bm(w.alpha, w.kappa, w.beta, w.sigma, w.corr, w.r)
+    contract = B.make_contract(payoff, w.strike, w.maturity)
+    return grid, model, contract
+
+
+def run_batch(B, torch, dev, lanes=16, fp64_sample=16):
+    """The 512 seed-drawn pricings (N in {128, 256, 512}, FP32-bulk) through
+    pide2d_batch_solve, wall time from the call to the prices on the host;
+    then the first `fp64_sample` jobs again as plain FP64 GPU solves, for the
+    price error and the FP64 throughput on the same GPU."""
+    from paper_2511_02700_gb300.workloads import batch_draw, with_
+    ws = batch_draw(512)
+    jobs = []
+    for w in ws:
+        g, m, c = _job(B, w)
+        jobs.append(B.make_job(g, m, c, w.steps, theta=w.theta, tol=w.tol))
+    B.solve_batch(jobs[:lanes], lanes=lanes)              # warm-up: module load, streams
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    prices, sts, st = B.solve_batch(jobs, lanes=lanes)
+    t1 = time.perf_counter()
+    errs, cells64, t64 = [], 0.0, 0.0
+    for w, p32 in zip(ws[:fp64_sample], prices[:fp64_sample]):
+        w64 = with_(w, precision="fp64")
+        g, m, c = _job(B, w64)
+        torch.cuda.synchronize(dev)
+        a0 = time.perf_counter()
+        s = B.Solver(g, m, c, w64.steps, theta=w64.theta, tol=w64.tol, device=dev)
+        p64, _, st64, _ = s.solve()
+        a1 = time.perf_counter()
+        s.close()
+        errs.append(abs(p32 - p64) / max(abs(p64), 1e-300))
+        cells64 += st64.cell_iters
+        t64 += a1 - a0
+    return {"workload": "batch_draw(512): N in {128,256,512}, N/4 steps, FP32-bulk, tol 1e-8",
+            "jobs": len(jobs), "lanes": lanes, "failures": st.failures, "wall_s": t1 - t0,
+            "value": st.cell_iters / (t1 - t0), "unit": UNIT, "jobs_per_s": len(jobs) / (t1 - t0),
+            "fp64_sample_jobs": fp64_sample, "price_max_rel_err_vs_fp64": max(errs),
+            "fp64_plain_value": cells64 / t64, "fp64_plain_wall_s": t64,
+            "note": "FP64 plain = the same jobs solved one by one in FP64 mode on the same GPU (create + solve)"}
+
+
+def run_adjoint(B, torch, dev):
+    """Adjoint on the 1024^2, 256-step FP64 workload: forward solve with
+    checkpoints every 16 steps, then pide2d_adjoint for the six workload
+    parameters; checked against FP64 central differences (step 1e-4) of the
+    CUDA path's prices.  The FP32-bulk adjoint is timed beside it."""
+    from paper_2511_02700_gb300.workloads import ADJOINT_FP64_1024, ADJOINT_INTERVAL, with_
+    w = ADJOINT_FP64_1024
+    names = B.SUBORDINATED_BM_PARAMS
+    out = {"workload": f"{w.name}: alpha {w.alpha}, {w.steps} steps, tol {w.tol}, checkpoint interval "
+                       f"{ADJOINT_INTERVAL}", "params": list(names)}
+
+    def forward_adjoint(wx):
+        g, m, c = _job(B, wx)
+        dirs = B.subordinated_bm_directions(wx.alpha, wx.kappa, wx.beta, wx.sigma, wx.corr)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        s = B.Solver(g, m, c, wx.steps, theta=wx.theta, tol=wx.tol, device=dev)
+        s.record(interval=ADJOINT_INTERVAL, ndirs=6)
+        price, _, st, _ = s.solve()
+        t1 = time.perf_counter()
+        grad, ast = s.adjoint(dirs)
+        t2 = time.perf_counter()
+        s.close()
+        return price, grad, t1 - t0, t2 - t1, st.cell_iters
+
+    def plain(wx):
+        g, m, c = _job(B, wx)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        s = B.Solver(g, m, c, wx.steps, theta=wx.theta, tol=wx.tol, device=dev)
+        price, _, st, _ = s.solve()
+        t1 = time.perf_counter()
+        s.close()
+        return price, t1 - t0, st.cell_iters
+
+    p64, t_plain, cells = plain(w)
+    price, grad, t_fwd, t_adj, _ = forward_adjoint(w)
+    out.update({"price": price, "grad": dict(zip(names, grad)), "fp64_plain_solve_s": t_plain,
+                "fp64_forward_with_checkpoints_s": t_fwd, "fp64_adjoint_s": t_adj,
+                "adjoint_over_plain_solve": t_adj / t_plain,
+                "fp64_plain_value": cells / t_plain, "unit": UNIT})
+    # FP64 central differences of the CUDA path's prices
+    eps = 1e-4
+    base = {"sigma1": w.sigma[0], "sigma2": w.sigma[1], "corr": w.corr, "kappa": w.kappa,
+            "beta1": w.beta[0], "beta2": w.beta[1]}
+    fd = []
+    for nm in names:
+        pr = []
+        for sgn in (1.0, -1.0):
+            v = dict(base)
+            v[nm] += sgn * eps
+            wx = with_(w, sigma=(v["sigma1"], v["sigma2"]), corr=v["corr"], kappa=v["kappa"],
+                       beta=(v["beta1"], v["beta2"]))
+            pr.append(plain(wx)[0])
+        fd.append((pr[0] - pr[1]) / (2 * eps))
+    scale = max(abs(x) for x in fd)
+    out["fd_grad"] = dict(zip(names, fd))
+    out["fd_max_abs_err_over_max_grad"] = max(abs(a_ - b_) for a_, b_ in zip(grad, fd)) / scale
+    # FP32-bulk forward + adjoint of the same workload
+    w32 = with_(w, precision="fp32", tol=1e-8)
+    p32, g32, t_fwd32, t_adj32, _ = forward_adjoint(w32)
+    out.update({"fp32_bulk_price_rel_err_vs_fp64": abs(p32 - p64) / abs(p64),
+                "fp32_bulk_forward_with_checkpoints_s": t_fwd32, "fp32_bulk_adjoint_s": t_adj32,
+                "fp32_bulk_grad_max_abs_err_over_max_grad": max(abs(a_ - b_) for a_, b_ in zip(g32, grad)) / scale})
+    return out
 
 
 def run_e2e(B, torch, dev, grid, model, contract, w, steps):

@@ -50,6 +50,11 @@ def convergence_sweep(precision: str):
 LARGE_FP32_4096 = Workload("large_fp32_4096", n=4096, steps=1024, alpha=0.5, tol=1e-7, precision="fp32")
 
 
+# adjoint: 1024^2 grid, 256 steps, FP64, tol 1e-10, checkpoints every 16 steps (alpha 0.25 and 0.5)
+ADJOINT_FP64_1024 = Workload("adjoint_fp64_1024", n=1024, steps=256, alpha=0.25, tol=1e-10, precision="fp64")
+ADJOINT_INTERVAL = 16
+
+
 def batch_draw(count: int = 512, seed: int = 2511027):
     """Independent pricings with seed-drawn parameters (uniform ranges):
     alpha [0.1, 0.45], kappa [0.2, 1], sigma_i [0.1, 0.4], corr [-0.6, 0.6],
