@@ -462,3 +462,39 @@ def test_price_gradient_single_asset_matches_fourier_derivatives():
     assert abs(gr["beta1"] - d_beta1) < 0.1 * abs(d_beta1), (gr, d_beta1)
     for p in ("sigma2", "corr", "beta2"):
         assert abs(gr[p]) < 0.01 * abs(gr["sigma1"]), (p, gr)
+
+
+@pytest.mark.parametrize("alpha", [0.0, 0.25, 0.5, 0.75])
+def test_integral_discretisation_converges_at_least_at_prop31_rate(alpha):
+    """Prop. 3.1: the quadrature of the integral term (zones R_I, R_II, R_III,
+    eqs. 3.3-3.6) has error O(h^(2 - A)) with A = 2 alpha for the NTS density.
+    Applied to a smooth Gaussian bump with exact derivatives, the discrete
+    operator's successive differences shrink at least at that rate, and the
+    sequence converges (the limit is the integral truncated at z_III)."""
+    from oracle.scheme import precompute
+    m = model_from_subordinated_bm(alpha, 0.5, (-0.10, -0.05), (0.20, 0.25), 0.3, 0.03)
+    w, x1, x2 = 0.6, 0.1, -0.15
+
+    def f(a, b):
+        return np.exp(-(a * a + b * b) / (2 * w * w))
+
+    v0 = f(x1, x2)
+    d1, d2 = -x1 / w ** 2 * v0, -x2 / w ** 2 * v0
+    d11 = (x1 * x1 / w ** 4 - 1 / w ** 2) * v0
+    d22 = (x2 * x2 / w ** 4 - 1 / w ** 2) * v0
+    d12 = x1 * x2 / w ** 4 * v0
+    J = []
+    for n in (32, 64, 128, 256):
+        g = Grid(n)
+        pre = precompute(m, g)
+        l = np.arange(-g.n_z, g.n_z)
+        L1, L2 = np.meshgrid(l, l)
+        z1, z2 = (L1 + 0.5) * g.h, (L2 + 0.5) * g.h
+        om, a = pre.omega, pre.a
+        # sum_l w_l [v(s+z_l) - v(s) - sum_i (e^{z_i} - 1) dv/ds_i] + R_I Taylor term (eq. 3.3)
+        J.append(np.sum(om * f(x1 + z1, x2 + z2)) - om.sum() * v0
+                 - np.sum(om * (np.exp(z1) - 1)) * d1 - np.sum(om * (np.exp(z2) - 1)) * d2
+                 + 0.5 * (a[0, 0] * d11 + 2 * a[0, 1] * d12 + a[1, 1] * d22) - 0.5 * (a[0, 0] * d1 + a[1, 1] * d2))
+    d = np.abs(np.diff(J))
+    assert d[2] < d[1] < d[0], J
+    assert math.log2(d[1] / d[2]) >= (2 - 2 * alpha) - 0.25, (alpha, J)
