@@ -251,9 +251,10 @@ pide2d_status pide2d_adjoint(pide2d_t* h, const pide2d_model* dirs, int ndirs, d
 
 /* ------------------------------------------------------------------------
  * Batches: many independent pricings on one GPU (one time loop each, as in
- * Algorithm 1).  Jobs are taken from a queue (largest first) by `lanes` host
- * threads, each with its own CUDA stream and workspace lane, so small grids
- * overlap on the device.
+ * Algorithm 1).  Jobs of one geometry (n, precision, sl_order, number of
+ * steps) are advanced in lockstep, up to `lanes` at a time: every kernel of
+ * a theta step and of each fixed-point iteration is launched once for all
+ * of them, and a job whose iteration has converged skips its share.
  * ------------------------------------------------------------------------ */
 typedef struct {
     pide2d_grid grid;
@@ -272,17 +273,17 @@ typedef struct {
 } pide2d_batch_stats;
 
 /* Workspace for pide2d_batch_solve: min(lanes, count) lanes of the largest
- * job's pide2d_workspace_bytes (256-byte rounded).  1 <= lanes <= 256.
- * Errors: ERR_ARG. */
+ * job's pide2d_workspace_bytes (256-byte rounded), plus the argument arrays
+ * of the multi-job launches.  1 <= lanes <= 1024.  Errors: ERR_ARG. */
 pide2d_status pide2d_batch_workspace_bytes(const pide2d_job* jobs, int count, int lanes, size_t* bytes);
 
 /* Prices `count` jobs: prices[j] (host, count doubles) receives job j's value
  * at S0; statuses (host, count ints, optional) each job's status; stats
- * optional.  opts->host_loop is ignored: every job runs the host-driven
- * fixed-point loop (with several lanes that overlaps better on GB300).
- * workspace: device, >= pide2d_batch_workspace_bytes(), 256-byte aligned,
- * caller-owned.  Uses the calling thread's current device; creates
- * and destroys `lanes` non-blocking streams (no device allocation).  Blocks
+ * optional.  opts->host_loop is ignored (the multi-job loop reads the
+ * number of jobs still iterating after each iteration).  workspace: device,
+ * >= pide2d_batch_workspace_bytes(), 256-byte aligned, caller-owned.  Uses
+ * the calling thread's current device; creates and destroys a few
+ * non-blocking streams and host threads (no device allocation).  Blocks
  * until every job is done.  Returns OK if every job succeeded, else the
  * status of a failed job (ERR_CUDA first); message via pide2d_last_error(NULL). */
 pide2d_status pide2d_batch_solve(const pide2d_job* jobs, int count, const pide2d_options* opts, int lanes,

@@ -179,6 +179,7 @@ struct pide2d {
     } tape;
     bool seg_record = false;       // replay of a tape segment: keep every theta step's V and B_w V
     bool force_host_loop = false;
+    bool group_nonconv = false;    // a theta step of the multi-job loop stopped without converging
     int seg_slot = 0;
     struct StepMeta { double theta, ht, tau_prev, tau; };
     std::vector<StepMeta> seg_meta;
@@ -521,29 +522,33 @@ struct SolveSpec {
     bool device_loop;
 };
 
+// kernel arguments of one implicit solve (see fixed_point_solve): the full
+// sweep of Y^{0} (fa, caf, iaf) and the iteration body (da, ra, cai, iai).
+// Blocks that key the loop graphs are zeroed bytewise.
 template <typename R>
-static pide2d_status fixed_point_solve(pide2d* H, const SolveSpec<R>& sp, int* iters_out, double* resid_out,
-                                       bool* conv_out) {
+struct SolveArgs {
+    FwdArgs<R> fa;
+    ColArgs<R> caf, cai;
+    InvArgs<R> iaf, iai;
+    DstColArgs<R> da;
+    DstRowArgs<R> ra;
+};
+
+template <typename R>
+static void build_solve_args(pide2d* H, const SolveSpec<R>& sp, SolveArgs<R>* out) {
     const Geometry g = H->L.g;
     const int N = g.N;
     const double hg = H->h;
     const double htt = sp.ht * sp.theta;
     const double rw = H->par[1], a11 = H->par[4], a12 = H->par[5], a22 = H->par[6];
     const R d11 = (R)(0.5 * a11 / (hg * hg)), d22 = (R)(0.5 * a22 / (hg * hg)), d12 = (R)(0.25 * a12 / (hg * hg));
-    St<R>* Y = sp.Y;
-    St<R>* BY = sp.BY;
-    R* rres = H->at<R>(R_RES);
-    R* dlt = H->at<R>(R_DLT);
-    R* E = H->at<R>(R_E);
     const void* tw = H->at<void>(R_TWR);
-    *conv_out = false;
-
-    // B_w Y^{0} by a full sweep and the first residual
-    FwdArgs<R> fa{};
+    std::memset(out, 0, sizeof *out);
+    FwdArgs<R>& fa = out->fa;
     fa.g = g;
     fa.mode = sp.far ? FWD_FULL : FWD_FULL0;
-    fa.Y = Y;
-    fa.D = dlt;
+    fa.Y = sp.Y;
+    fa.D = H->at<R>(R_DLT);
     fa.E1 = (const R*)(sizeof(R) == 4 ? (const void*)H->at<float>(R_E1F) : (const void*)H->at<double>(R_E1D));
     fa.E2 = (const R*)(sizeof(R) == 4 ? (const void*)H->at<float>(R_E2F) : (const void*)H->at<double>(R_E2D));
     fa.Kd = (R)sp.Kd;
@@ -552,10 +557,7 @@ static pide2d_status fixed_point_solve(pide2d* H, const SolveSpec<R>& sp, int* i
     fa.pair0 = 0;
     fa.npairs = N + 1;
     fa.tw = tw;
-    PIDE_LAUNCH(PIDE2D_KERNEL_ROW_FORWARD_FULL, launch_row_forward<R>(fa, H->stream));
-    // argument blocks of the iteration body are zeroed bytewise: their bytes key the loop graphs
-    ColArgs<R> ca;
-    std::memset(&ca, 0, sizeof ca);
+    ColArgs<R>& ca = out->caf;
     ca.g = g;
     ca.mode = COL_FULL;
     ca.S = H->at<void>(R_S);
@@ -563,53 +565,66 @@ static pide2d_status fixed_point_solve(pide2d* H, const SolveSpec<R>& sp, int* i
     ca.rlo = 0;
     ca.rhi = g.P + 2;
     ca.tw = tw;
-    PIDE_LAUNCH(PIDE2D_KERNEL_COL_FULL, launch_col<R>(ca, H->stream));
-    InvArgs<R> ia;
-    std::memset(&ia, 0, sizeof ia);
+    InvArgs<R>& ia = out->iaf;
     ia.g = g;
     ia.mode = INV_FULL;
     ia.do_resid = 1;
     ia.S = H->at<void>(R_S);
-    ia.BY = BY;
-    ia.Y = Y;
+    ia.BY = sp.BY;
+    ia.Y = sp.Y;
     ia.W = sp.W;
-    ia.r = rres;
-    ia.D = dlt;
+    ia.r = H->at<R>(R_RES);
+    ia.D = H->at<R>(R_DLT);
     ia.htt = (R)htt;
     ia.cid = (R)(1.0 + htt * rw);
     ia.d11 = d11;
     ia.d22 = d22;
     ia.d12 = d12;
     ia.rw = (R)rw;
-    ia.E = E;
+    ia.E = H->at<R>(R_E);
     ia.tw = tw;
-    PIDE_LAUNCH(PIDE2D_KERNEL_ROW_INVERSE_FULL, launch_row_inverse<R>(ia, H->stream));
-
-    DstColArgs<R> da;
-    std::memset(&da, 0, sizeof da);
+    DstColArgs<R>& da = out->da;
     da.g = g;
-    da.E = E;
+    da.E = H->at<R>(R_E);
     da.sin2 = H->at<R>(R_SIN2R);
     da.c0 = 1.0 + htt * rw;
     da.c1 = 2.0 * htt * a11 / (hg * hg);
     da.c2 = 2.0 * htt * a22 / (hg * hg);
     da.scale = (2.0 / N) * (2.0 / N);
     da.tw = tw;
-    DstRowArgs<R> ra;
-    std::memset(&ra, 0, sizeof ra);
+    DstRowArgs<R>& ra = out->ra;
     ra.g = g;
-    ra.E = E;
-    ra.Y = Y;
-    ra.D = dlt;
+    ra.E = H->at<R>(R_E);
+    ra.Y = sp.Y;
+    ra.D = H->at<R>(R_DLT);
     ra.resid = H->at<void>(R_RESID);
     ra.S = H->at<void>(R_S);
     ra.tw = tw;
+    std::memcpy(&out->cai, &ca, sizeof ca);     // bytewise: padding stays zero for the graph keys
+    out->cai.mode = COL_INCR;
+    out->cai.Wh = sp.Whi;
+    out->cai.rlo = N / 2 + 2;
+    out->cai.rhi = N / 2 + N + 2;
+    std::memcpy(&out->iai, &ia, sizeof ia);
+    out->iai.mode = INV_INCR;
+}
 
-    ca.mode = COL_INCR;
-    ca.Wh = sp.Whi;
-    ca.rlo = N / 2 + 2;
-    ca.rhi = N / 2 + N + 2;
-    ia.mode = INV_INCR;
+template <typename R>
+static pide2d_status fixed_point_solve(pide2d* H, const SolveSpec<R>& sp, int* iters_out, double* resid_out,
+                                       bool* conv_out) {
+    *conv_out = false;
+    SolveArgs<R> A;
+    build_solve_args<R>(H, sp, &A);
+    St<R>* Y = sp.Y;
+    St<R>* BY = sp.BY;
+    // B_w Y^{0} by a full sweep and the first residual
+    PIDE_LAUNCH(PIDE2D_KERNEL_ROW_FORWARD_FULL, launch_row_forward<R>(A.fa, H->stream));
+    PIDE_LAUNCH(PIDE2D_KERNEL_COL_FULL, launch_col<R>(A.caf, H->stream));
+    PIDE_LAUNCH(PIDE2D_KERNEL_ROW_INVERSE_FULL, launch_row_inverse<R>(A.iaf, H->stream));
+    DstColArgs<R>& da = A.da;
+    DstRowArgs<R>& ra = A.ra;
+    ColArgs<R>& ca = A.cai;
+    InvArgs<R>& ia = A.iai;
 
     if (sp.device_loop) {
         // the iteration loop runs on the device (graph while-node); the step's
@@ -665,9 +680,11 @@ static pide2d_status fixed_point_solve(pide2d* H, const SolveSpec<R>& sp, int* i
 // one theta step (eq. 3.23): W and Y^{n,0} (Algorithm 1 steps 2-3), then the
 // implicit solve
 // ---------------------------------------------------------------------------
+// arguments of one theta step (eq. 3.23): W and Y^{n,0} (Algorithm 1 steps 2-3)
+// into pa, the implicit solve into sp
 template <typename R>
-static pide2d_status theta_step(pide2d* H, const int* list, int cnt, double theta, double ht, double tau_prev,
-                                double tau, int res, int step_end, int* iters_out, double* resid_out) {
+static pide2d_status build_theta_step(pide2d* H, const int* list, int cnt, double theta, double ht, double tau_prev,
+                                      double tau, int res, int step_end, PrepArgs<R>* pa_out, SolveSpec<R>* sp_out) {
     const Geometry g = H->L.g;
     const int N = g.N;
     const double hg = H->h;
@@ -681,7 +698,8 @@ static pide2d_status theta_step(pide2d* H, const int* list, int cnt, double thet
     St<R>* BV = (St<R>*)H->field(H->bv);
     St<R>* BY = (St<R>*)H->field(H->by);
 
-    PrepArgs<R> pa{};
+    PrepArgs<R>& pa = *pa_out;
+    std::memset(&pa, 0, sizeof pa);
     pa.g = g;
     for (int i = 0; i < 4; ++i) pa.V[i] = (const St<R>*)H->field(list[i < cnt ? i : 0]);
     pa.hcount = cnt;
@@ -713,9 +731,9 @@ static pide2d_status theta_step(pide2d* H, const int* list, int cnt, double thet
     pa.Kd_prev = Kd_prev;
     pa.Kd_now = Kd_now;
     pa.payoff = H->contract.payoff;
-    PIDE_LAUNCH(PIDE2D_KERNEL_PREP, launch_prep<R>(pa, H->stream));
 
-    SolveSpec<R> sp{};
+    SolveSpec<R>& sp = *sp_out;
+    sp = SolveSpec<R>{};
     sp.Y = Y;
     sp.BY = BY;
     sp.W = W;
@@ -727,6 +745,20 @@ static pide2d_status theta_step(pide2d* H, const int* list, int cnt, double thet
     sp.ht = ht;
     sp.step_end = step_end;
     sp.device_loop = !H->host_loop && !H->prof && !H->force_host_loop;
+    return PIDE2D_OK;
+}
+
+template <typename R>
+static pide2d_status theta_step(pide2d* H, const int* list, int cnt, double theta, double ht, double tau_prev,
+                                double tau, int res, int step_end, int* iters_out, double* resid_out) {
+    const int N = H->L.g.N;
+    PrepArgs<R> pa;
+    SolveSpec<R> sp;
+    {
+        const pide2d_status bs = build_theta_step<R>(H, list, cnt, theta, ht, tau_prev, tau, res, step_end, &pa, &sp);
+        if (bs != PIDE2D_OK) return bs;
+    }
+    PIDE_LAUNCH(PIDE2D_KERNEL_PREP, launch_prep<R>(pa, H->stream));
     int k = 0;
     double resid = 0.0;
     bool conv = false;
@@ -1067,6 +1099,230 @@ static pide2d_status do_price(pide2d* H, double* price) {
 template <typename R> St<R> st_host_one();
 template <> float2 st_host_one<float>() { return make_float2(1.f, 0.f); }
 template <> double st_host_one<double>() { return 1.0; }
+
+// ---------------------------------------------------------------------------
+// multi-job time loop: K handles of one geometry advanced in lockstep, every
+// kernel launched once for all of them (grid dimension y / z = job)
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t kArgAlign = 256;
+size_t arr_bytes(size_t each, int K) { return align256(each * (size_t)K); }
+
+template <typename R>
+struct GroupLayout {
+    size_t pa, fa, caf, iaf, da, ra, cai, iai, chk, conv, kconv, kcount, nonconv, last, active, total;
+    GroupLayout(int K) {
+        size_t o = 0;
+        pa = o;      o += arr_bytes(sizeof(PrepArgs<R>), K);
+        fa = o;      o += arr_bytes(sizeof(FwdArgs<R>), K);
+        caf = o;     o += arr_bytes(sizeof(ColArgs<R>), K);
+        iaf = o;     o += arr_bytes(sizeof(InvArgs<R>), K);
+        da = o;      o += arr_bytes(sizeof(DstColArgs<R>), K);
+        ra = o;      o += arr_bytes(sizeof(DstRowArgs<R>), K);
+        cai = o;     o += arr_bytes(sizeof(ColArgs<R>), K);
+        iai = o;     o += arr_bytes(sizeof(InvArgs<R>), K);
+        chk = o;     o += arr_bytes(sizeof(JobCheck), K);
+        conv = o;    o += arr_bytes(4, K);
+        kconv = o;   o += arr_bytes(4, K);
+        kcount = o;  o += arr_bytes(4, K);
+        nonconv = o; o += arr_bytes(4, K);
+        last = o;    o += arr_bytes(8, K);
+        active = o;  o += kArgAlign;
+        total = o;
+    }
+};
+
+// the next theta step of one job, as do_step would take it
+struct JobPlan {
+    int list[4];
+    int cnt;
+    double theta, ht, tau_prev, tau;
+    int res;
+    int step_end;
+};
+}  // namespace
+
+namespace pide {
+size_t group_scratch_bytes(int K) {
+    return std::max(GroupLayout<float>(K).total, GroupLayout<double>(K).total);
+}
+
+}  // namespace pide
+
+template <typename R>
+static pide2d_status group_solve(pide2d* const* hs, int K, char* scratch, std::string* err) {
+    pide2d* H0 = hs[0];
+    cudaStream_t s = H0->stream;
+    const GroupLayout<R> L(K);
+    std::vector<char> blob(L.chk);                         // the argument arrays, rebuilt per theta step
+    std::vector<JobCheck> chk(K);
+    for (int j = 0; j < K; ++j) {
+        chk[j].resid = hs[j]->at<void>(R_RESID);
+        chk[j].tol = hs[j]->tol;
+        chk[j].kmax = hs[j]->kmax;
+        chk[j].pad = 0;
+    }
+    auto fail = [&](pide2d* H, pide2d_status st) {
+        *err = H->err;
+        return st;
+    };
+    {
+        pide2d* H = H0;
+        PIDE_CUDA(cudaMemcpyAsync(scratch + L.chk, chk.data(), sizeof(JobCheck) * K, cudaMemcpyHostToDevice, s));
+        PIDE_CUDA(cudaMemsetAsync(scratch + L.nonconv, 0, 4 * (size_t)K, s));
+    }
+    JobsState st{};
+    st.conv = reinterpret_cast<int*>(scratch + L.conv);
+    st.kconv = reinterpret_cast<int*>(scratch + L.kconv);
+    st.kcount = reinterpret_cast<int*>(scratch + L.kcount);
+    st.nonconv = reinterpret_cast<int*>(scratch + L.nonconv);
+    st.last = reinterpret_cast<double*>(scratch + L.last);
+    st.active = reinterpret_cast<int*>(scratch + L.active);
+    const JobCheck* dchk = reinterpret_cast<const JobCheck*>(scratch + L.chk);
+    int kmax_all = 0;
+    for (int j = 0; j < K; ++j) kmax_all = std::max(kmax_all, hs[j]->kmax);
+    std::vector<int> kc(K);
+    std::vector<double> lastv(K);
+    std::vector<int> cur(K), v0(K), ktot(K);
+    std::vector<JobPlan> plan(K);
+
+    while (H0->steps_done < H0->n_steps) {
+        const bool damped = H0->steps_done == 0 && H0->damping;
+        const int nsub = damped ? 4 : 1;
+        for (int j = 0; j < K; ++j) {
+            cur[j] = v0[j] = hs[j]->hist[0];
+            ktot[j] = 0;
+        }
+        for (int sub = 0; sub < nsub; ++sub) {
+            PrepArgs<R> pa0{};
+            SolveArgs<R> A0{};
+            for (int j = 0; j < K; ++j) {
+                pide2d* H = hs[j];
+                JobPlan& p = plan[j];
+                p.res = H->freel.back();
+                H->freel.pop_back();
+                if (damped) {
+                    const double q = H->dt / 4.0;
+                    p.list[0] = cur[j];
+                    p.cnt = 1;
+                    p.theta = 1.0;
+                    p.ht = q;
+                    p.tau_prev = sub * q;
+                    p.tau = (sub + 1) * q;
+                    p.step_end = sub == 3 ? 1 : 0;
+                } else {
+                    const int n = H->steps_done + 1;
+                    p.cnt = (int)H->hist.size() < 4 ? (int)H->hist.size() : 4;
+                    for (int i = 0; i < p.cnt; ++i) p.list[i] = H->hist[i];
+                    p.theta = H->theta;
+                    p.ht = H->dt;
+                    p.tau_prev = (n - 1) * H->dt;
+                    p.tau = n * H->dt;
+                    p.step_end = 1;
+                }
+                PrepArgs<R> pa;
+                SolveSpec<R> sp;
+                const pide2d_status bs =
+                    build_theta_step<R>(H, p.list, p.cnt, p.theta, p.ht, p.tau_prev, p.tau, p.res, p.step_end, &pa, &sp);
+                if (bs != PIDE2D_OK) return fail(H, bs);
+                SolveArgs<R> A;
+                build_solve_args<R>(H, sp, &A);
+                A.iai.conv_flag = st.conv + j;
+                std::memcpy(blob.data() + L.pa + j * sizeof pa, &pa, sizeof pa);
+                std::memcpy(blob.data() + L.fa + j * sizeof A.fa, &A.fa, sizeof A.fa);
+                std::memcpy(blob.data() + L.caf + j * sizeof A.caf, &A.caf, sizeof A.caf);
+                std::memcpy(blob.data() + L.iaf + j * sizeof A.iaf, &A.iaf, sizeof A.iaf);
+                std::memcpy(blob.data() + L.da + j * sizeof A.da, &A.da, sizeof A.da);
+                std::memcpy(blob.data() + L.ra + j * sizeof A.ra, &A.ra, sizeof A.ra);
+                std::memcpy(blob.data() + L.cai + j * sizeof A.cai, &A.cai, sizeof A.cai);
+                std::memcpy(blob.data() + L.iai + j * sizeof A.iai, &A.iai, sizeof A.iai);
+                if (j == 0) {
+                    pa0 = pa;
+                    A0 = A;
+                }
+            }
+            pide2d* H = H0;
+            auto arr = [&](size_t off) { return scratch + off; };
+            PIDE_CUDA(cudaMemcpyAsync(scratch, blob.data(), L.chk, cudaMemcpyHostToDevice, s));
+            bool expl = false;
+            for (int j = 0; j < K; ++j) expl = expl || plan[j].theta != 1.0;
+            PIDE_CUDA(launch_prep_jobs<R>(pa0, (const PrepArgs<R>*)arr(L.pa), K, expl, s));
+            JobsCtl all{st.conv, st.kconv, 0, 0};
+            PIDE_CUDA(launch_row_forward_jobs<R>(A0.fa, (const FwdArgs<R>*)arr(L.fa), K, all, s));
+            PIDE_CUDA(launch_col_jobs<R>(A0.caf, (const ColArgs<R>*)arr(L.caf), K, all, s));
+            PIDE_CUDA(launch_row_inverse_jobs<R>(A0.iaf, (const InvArgs<R>*)arr(L.iaf), K, all, s));
+            PIDE_CUDA(launch_jobs_reset<R>(K, dchk, st, s));
+            for (int it = 1; it <= kmax_all; ++it) {
+                const JobsCtl head{st.conv, st.kconv, it, 1};
+                const JobsCtl tail{st.conv, st.kconv, it, 2};
+                PIDE_CUDA(launch_dst_col_jobs<R>(A0.da, (const DstColArgs<R>*)arr(L.da), K, head, s));
+                PIDE_CUDA(launch_dst_row_jobs<R>(A0.ra, (const DstRowArgs<R>*)arr(L.ra), K, head, s));
+                PIDE_CUDA(launch_jobs_check<R>(K, dchk, st, it, s));
+                PIDE_CUDA(launch_col_jobs<R>(A0.cai, (const ColArgs<R>*)arr(L.cai), K, tail, s));
+                PIDE_CUDA(launch_row_inverse_jobs<R>(A0.iai, (const InvArgs<R>*)arr(L.iai), K, tail, s));
+                int act = 0;
+                PIDE_CUDA(cudaMemcpyAsync(&act, st.active, 4, cudaMemcpyDeviceToHost, s));
+                PIDE_CUDA(cudaStreamSynchronize(s));
+                if (act == 0) break;
+            }
+            PIDE_CUDA(cudaMemcpyAsync(kc.data(), st.kcount, 4 * (size_t)K, cudaMemcpyDeviceToHost, s));
+            PIDE_CUDA(cudaMemcpyAsync(lastv.data(), st.last, 8 * (size_t)K, cudaMemcpyDeviceToHost, s));
+            PIDE_CUDA(cudaStreamSynchronize(s));
+            // bookkeeping of each job, as theta_step / do_step do it
+            for (int j = 0; j < K; ++j) {
+                pide2d* Hj = hs[j];
+                const JobPlan& p = plan[j];
+                std::swap(Hj->bv, Hj->by);
+                const int N = Hj->L.g.N;
+                Hj->stats.cell_iters += (double)N * N * (kc[j] + 1);
+                Hj->stats.last_resid = lastv[j];
+                ktot[j] += kc[j];
+                if (damped) {
+                    if (cur[j] != v0[j]) Hj->freel.push_back(cur[j]);
+                    cur[j] = p.res;
+                } else {
+                    Hj->hist.insert(Hj->hist.begin(), p.res);
+                    if (Hj->hist.size() > 4) {
+                        Hj->freel.push_back(Hj->hist.back());
+                        Hj->hist.pop_back();
+                    }
+                }
+            }
+        }
+        for (int j = 0; j < K; ++j) {
+            pide2d* Hj = hs[j];
+            if (damped) Hj->hist.assign({cur[j], v0[j]});
+            Hj->steps_done++;
+            Hj->stats.steps_done = Hj->steps_done;
+            Hj->stats.fp_iters_total += ktot[j];
+            if (ktot[j] > Hj->stats.fp_iters_max) Hj->stats.fp_iters_max = ktot[j];
+            Hj->last_step_device = false;
+        }
+    }
+    // jobs with a theta step that stopped at kmax or on a non-finite residual
+    std::vector<int> nc(K);
+    {
+        pide2d* H = H0;
+        PIDE_CUDA(cudaMemcpyAsync(nc.data(), st.nonconv, 4 * (size_t)K, cudaMemcpyDeviceToHost, s));
+        PIDE_CUDA(cudaStreamSynchronize(s));
+    }
+    for (int j = 0; j < K; ++j) {
+        if (nc[j]) {
+            hs[j]->err = "fixed-point iteration not converged in a theta step (multi-job loop)";
+            hs[j]->group_nonconv = true;
+        }
+    }
+    return PIDE2D_OK;
+}
+
+namespace pide {
+void set_handle_stream(pide2d_t* h, void* stream) { h->stream = static_cast<cudaStream_t>(stream); }
+
+pide2d_status solve_group(pide2d_t* const* hs, int K, void* scratch, std::string* err) {
+    return hs[0]->grid.precision == PIDE2D_FP64 ? group_solve<double>(hs, K, static_cast<char*>(scratch), err)
+                                                 : group_solve<float>(hs, K, static_cast<char*>(scratch), err);
+}
+}  // namespace pide
 
 // ---------------------------------------------------------------------------
 // discrete adjoint of the time loop (see adjoint.cu for the recursion)
@@ -1495,6 +1751,7 @@ pide2d_status pide2d_solve(pide2d_t* H, double* price, double* values_out, pide2
         const pide2d_status r = read_ctl(H);
         if (r != PIDE2D_OK) return r;
         if (check_device_convergence(H) != PIDE2D_OK) worst = PIDE2D_ERR_NOT_CONVERGED;
+        if (H->group_nonconv) worst = PIDE2D_ERR_NOT_CONVERGED;
     }
     if (price) {
         const pide2d_status s = H->grid.precision == PIDE2D_FP64 ? do_price<double>(H, price) : do_price<float>(H, price);

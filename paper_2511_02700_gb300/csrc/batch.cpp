@@ -1,26 +1,38 @@
 // pide2d_batch_*: many independent pricings on one GPU.
 //
-// The jobs run through the single-pricing path (pide2d_create/solve).  L
-// host threads each own one CUDA stream and one lane of the caller's
-// workspace, and take jobs from a shared queue (largest grids first), so
-// the small, launch-bound grids of a batch overlap on the GPU instead of
-// running back to back.  Nothing here allocates device memory.
+// Jobs are grouped by geometry (N, precision, departure order, number of
+// steps).  Each group is split into chunks of at most `lanes` jobs.  A chunk
+// gets one workspace lane per job and is advanced in lockstep by the
+// multi-job time loop (solve_group in api.cu): every kernel of a theta step
+// and of each fixed-point iteration is launched once for the whole chunk,
+// with the job in the grid's y (or z) dimension, and jobs that have
+// converged skip their blocks.  The precompute of each job (weights, rates,
+// payoff) runs per job, from a few host threads.  Nothing here allocates
+// device memory.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <atomic>
-#include <cstring>
+#include <cmath>
+#include <functional>
+#include <map>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "../../include/pide2d.h"
 
 namespace pide {
 void set_global_error(const std::string& msg);
+size_t group_scratch_bytes(int K);
+pide2d_status solve_group(pide2d_t* const* hs, int K, void* scratch, std::string* err);
+void set_handle_stream(pide2d_t* h, void* stream);
 }
 
 namespace {
+
+constexpr int kCreateThreads = 8;
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -36,26 +48,31 @@ pide2d_status lane_bytes(const pide2d_job* jobs, int count, size_t* out) {
     return PIDE2D_OK;
 }
 
+int job_steps(const pide2d_job& j) {
+    return j.dt > 0.0 ? (int)std::llround(j.contract.maturity / j.dt) : 0;
+}
+
 }  // namespace
 
 extern "C" {
 
 pide2d_status pide2d_batch_workspace_bytes(const pide2d_job* jobs, int count, int lanes, size_t* bytes) {
-    if (!jobs || count < 1 || lanes < 1 || lanes > 256 || !bytes) {
+    if (!jobs || count < 1 || lanes < 1 || lanes > 1024 || !bytes) {
         pide::set_global_error("pide2d_batch_workspace_bytes: invalid arguments");
         return PIDE2D_ERR_ARG;
     }
     size_t lb = 0;
     const pide2d_status s = lane_bytes(jobs, count, &lb);
     if (s != PIDE2D_OK) return s;
-    *bytes = lb * (size_t)std::min(lanes, count);
+    const int L = std::min(lanes, count);
+    *bytes = lb * (size_t)L + align256(pide::group_scratch_bytes(L));
     return PIDE2D_OK;
 }
 
 pide2d_status pide2d_batch_solve(const pide2d_job* jobs, int count, const pide2d_options* opts, int lanes,
                                  void* workspace, size_t workspace_bytes, double* prices, int* statuses,
                                  pide2d_batch_stats* stats) {
-    if (!jobs || count < 1 || lanes < 1 || lanes > 256 || !prices) {
+    if (!jobs || count < 1 || lanes < 1 || lanes > 1024 || !prices) {
         pide::set_global_error("pide2d_batch_solve: invalid arguments");
         return PIDE2D_ERR_ARG;
     }
@@ -63,7 +80,8 @@ pide2d_status pide2d_batch_solve(const pide2d_job* jobs, int count, const pide2d
     pide2d_status s = lane_bytes(jobs, count, &lb);
     if (s != PIDE2D_OK) return s;
     lanes = std::min(lanes, count);
-    if (!workspace || ((uintptr_t)workspace & 255) != 0 || workspace_bytes < lb * (size_t)lanes) {
+    const size_t need = lb * (size_t)lanes + align256(pide::group_scratch_bytes(lanes));
+    if (!workspace || ((uintptr_t)workspace & 255) != 0 || workspace_bytes < need) {
         pide::set_global_error("pide2d_batch_solve: workspace too small or misaligned");
         return PIDE2D_ERR_WORKSPACE;
     }
@@ -72,63 +90,107 @@ pide2d_status pide2d_batch_solve(const pide2d_job* jobs, int count, const pide2d
         pide::set_global_error("pide2d_batch_solve: no current CUDA device");
         return PIDE2D_ERR_CUDA;
     }
-    // largest grids first, so the tail of the queue is short jobs
-    std::vector<int> order(count);
-    for (int i = 0; i < count; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        const double wa = (double)jobs[a].grid.n * jobs[a].grid.n * (jobs[a].contract.maturity / jobs[a].dt);
-        const double wb = (double)jobs[b].grid.n * jobs[b].grid.n * (jobs[b].contract.maturity / jobs[b].dt);
-        return wa > wb;
-    });
-    // Every job runs the host-driven fixed-point loop: with many lanes the
-    // per-iteration host round trip of one lane overlaps the kernels of the
-    // others, and on GB300 the lanes' CUDA-graph while-loops did not overlap
-    // (measured: 512 jobs in 7.2 s with the host loop, 17-19 s with the
-    // device loop, 8 to 32 lanes alike).
+    char* ws = static_cast<char*>(workspace);
+    void* scratch = ws + lb * (size_t)lanes;
     pide2d_options o{};
     if (opts) o = *opts;
     else o.kmax = 100, o.damping = 1;
-    o.host_loop = 1;
-    std::atomic<int> next(0);
+    o.host_loop = 1;          // the multi-job loop is driven from the host
+
+    // groups of one geometry, largest grids first
+    std::map<std::tuple<int, int, int, int>, std::vector<int>, std::greater<std::tuple<int, int, int, int>>> groups;
+    for (int j = 0; j < count; ++j) {
+        const pide2d_grid& g = jobs[j].grid;
+        const int order = g.sl_order == 0 ? 3 : g.sl_order;
+        groups[std::make_tuple(g.n, g.precision, order, job_steps(jobs[j]))].push_back(j);
+    }
+
+    cudaStream_t stream = nullptr;
+    if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) {
+        pide::set_global_error("pide2d_batch_solve: cudaStreamCreate failed");
+        return PIDE2D_ERR_CUDA;
+    }
     std::vector<int> st(count, PIDE2D_OK);
     std::vector<pide2d_stats> js(count);
-    std::vector<std::string> errors(lanes);
-    auto worker = [&](int lane) {
-        cudaSetDevice(device);
-        cudaStream_t stream = nullptr;
-        if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) {
-            errors[lane] = "cudaStreamCreate failed";
-            return;
-        }
-        void* ws = static_cast<char*>(workspace) + lb * (size_t)lane;
-        for (;;) {
-            const int q = next.fetch_add(1);
-            if (q >= count) break;
-            const int j = order[q];
-            const pide2d_job& job = jobs[j];
-            pide2d_t* h = nullptr;
-            pide2d_status r = pide2d_create(&job.grid, &job.model, &job.contract, job.theta, job.dt, job.fp_tol,
-                                            &o, ws, lb, stream, &h);
-            if (r == PIDE2D_OK) {
-                r = pide2d_solve(h, &prices[j], nullptr, &js[j]);
-                if (r != PIDE2D_OK && r != PIDE2D_ERR_NOT_CONVERGED) errors[lane] = pide2d_last_error(h);
-                pide2d_destroy(h);
-            } else {
-                prices[j] = 0.0;
-                errors[lane] = pide2d_last_error(nullptr);
+    std::string last_error;
+    bool cuda_failed = false;
+
+    for (auto& kv : groups) {
+        const std::vector<int>& members = kv.second;
+        for (size_t c0 = 0; c0 < members.size() && !cuda_failed; c0 += (size_t)lanes) {
+            const int K = (int)std::min(members.size() - c0, (size_t)lanes);
+            std::vector<pide2d_t*> hs(K, nullptr);
+            // per-job precompute, a few handles at a time from host threads
+            std::atomic<int> next(0);
+            std::vector<std::string> errs(kCreateThreads);
+            auto creator = [&](int tid) {
+                cudaSetDevice(device);
+                cudaStream_t cs = nullptr;
+                if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+                    errs[tid] = "cudaStreamCreate failed";
+                    return;
+                }
+                for (;;) {
+                    const int q = next.fetch_add(1);
+                    if (q >= K) break;
+                    const int j = members[c0 + q];
+                    const pide2d_job& job = jobs[j];
+                    pide2d_t* h = nullptr;
+                    const pide2d_status r = pide2d_create(&job.grid, &job.model, &job.contract, job.theta, job.dt,
+                                                          job.fp_tol, &o, ws + lb * (size_t)q, lb, cs, &h);
+                    if (r == PIDE2D_OK) {
+                        pide::set_handle_stream(h, stream);     // create has finished on cs
+                        hs[q] = h;
+                    } else {
+                        st[j] = r;
+                        prices[j] = 0.0;
+                        errs[tid] = pide2d_last_error(nullptr);
+                    }
+                }
+                cudaStreamSynchronize(cs);
+                cudaStreamDestroy(cs);
+            };
+            const int nt = std::min(kCreateThreads, K);
+            std::vector<std::thread> pool;
+            for (int t = 0; t < nt; ++t) pool.emplace_back(creator, t);
+            for (auto& t : pool) t.join();
+            for (const auto& e : errs)
+                if (!e.empty()) last_error = e;
+            // the created jobs run together
+            std::vector<pide2d_t*> live;
+            std::vector<int> live_idx;
+            for (int q = 0; q < K; ++q)
+                if (hs[q]) {
+                    live.push_back(hs[q]);
+                    live_idx.push_back(members[c0 + q]);
+                }
+            if (!live.empty()) {
+                std::string err;
+                const pide2d_status gs = pide::solve_group(live.data(), (int)live.size(), scratch, &err);
+                if (gs != PIDE2D_OK) {
+                    for (int j : live_idx) st[j] = gs;
+                    last_error = err;
+                    if (gs == PIDE2D_ERR_CUDA) cuda_failed = true;
+                } else {
+                    for (size_t q = 0; q < live.size(); ++q) {
+                        const int j = live_idx[q];
+                        const pide2d_status r = pide2d_solve(live[q], &prices[j], nullptr, &js[j]);
+                        st[j] = r;
+                        if (r != PIDE2D_OK) last_error = pide2d_last_error(live[q]);
+                    }
+                }
             }
-            st[j] = r;
+            for (auto* h : hs)
+                if (h) pide2d_destroy(h);
         }
-        cudaStreamSynchronize(stream);
-        cudaStreamDestroy(stream);
-    };
-    std::vector<std::thread> pool;
-    for (int l = 0; l < lanes; ++l) pool.emplace_back(worker, l);
-    for (auto& t : pool) t.join();
+    }
+    cudaStreamSynchronize(stream);
+    cudaStreamDestroy(stream);
 
     pide2d_status worst = PIDE2D_OK;
     pide2d_batch_stats bs{};
     for (int j = 0; j < count; ++j) {
+        if (cuda_failed && st[j] == PIDE2D_OK && js[j].steps_done == 0) st[j] = PIDE2D_ERR_CUDA;
         if (statuses) statuses[j] = st[j];
         if (st[j] == PIDE2D_OK || st[j] == PIDE2D_ERR_NOT_CONVERGED) {
             bs.jobs_done += 1;
@@ -141,8 +203,7 @@ pide2d_status pide2d_batch_solve(const pide2d_job* jobs, int count, const pide2d
         }
     }
     if (stats) *stats = bs;
-    for (const auto& e : errors)
-        if (!e.empty()) pide::set_global_error(e);
+    if (!last_error.empty()) pide::set_global_error(last_error);
     return worst;
 }
 

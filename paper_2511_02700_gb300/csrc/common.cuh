@@ -215,30 +215,103 @@ __device__ __forceinline__ void fft_stage(int t, const cpx<R>* __restrict__ tw, 
     __syncthreads();
 }
 
-// Stages NS, 16 NS, ... of a length-P transform: radix 16 while it fits, one
-// radix-2/4/8 stage last.  `load` feeds the first of them, `store` takes the
-// last one's outputs (natural order); the others go through `buf`.
+// The last Stockham stage when P = 32 NS: a radix-32 butterfly per pair of
+// lanes, so a length 16^k * 2 transform needs no separate radix-2 pass
+// through shared memory.  With r = 2m + h, lane h of the pair (h = t & 1)
+// takes the inputs r = 2m + h, twiddles them by w^{k r} = w^{2km} w^{kh}, and
+// forms Y_h[q] = sum_m v_m e^{DIR 2 pi i m q / 16}; the outputs are
+//   X[q + 16 p] = sum_h e^{DIR 2 pi i h (q + 16 p) / 32} w^{kh} Y_h[q],
+// a radix-2 butterfly across the pair (one shuffle per value): lane h
+// finishes q in [8h, 8h + 8) for p = 0, 1.
 template <typename R, int DIR, int P, int NS, class L, class S>
+__device__ __forceinline__ void fft_stage_r32(int t, const cpx<R>* __restrict__ tw, const L& load, const S& store) {
+    static_assert(NS * 32 == P, "radix-32 stage must be the last one");
+    const int j = t >> 1, h = t & 1;        // butterfly j = k < NS
+    const int k = j;
+    cpx<R> v[16];
+    if constexpr (is_smem_io<L>::value && (2 * NS) % 16 == 0) {
+        const int pb = padi(j + h * NS);
+        constexpr int ST = 2 * NS + (2 * NS) / 16;
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = load.at(pb, m * ST);
+    } else {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = load(j + (2 * m + h) * NS);
+    }
+    if constexpr (NS > 1) {
+        // w^{2km} = w^{2k(4a+b)}: six table loads, nine products
+        const int e = 2 * k;
+        cpx<R> wb[4], wa[4];
+#pragma unroll
+        for (int q = 1; q < 4; ++q) {
+            wb[q] = __ldg(&tw[e * q]);
+            wa[q] = __ldg(&tw[4 * e * q]);
+            if (DIR > 0) { wb[q].y = -wb[q].y; wa[q].y = -wa[q].y; }
+        }
+#pragma unroll
+        for (int m = 1; m < 16; ++m) {
+            const int qa = m >> 2, qb = m & 3;
+            cpx<R> w;
+            if (qa == 0) w = wb[qb];
+            else if (qb == 0) w = wa[qa];
+            else w = cmul(wa[qa], wb[qb]);
+            v[m] = cmul(v[m], w);
+        }
+    }
+    dft_small<DIR, 16>(v);
+    // Z_h[q] = w^{h (k + q NS)} Y_h[q] (the identity for h = 0)
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        cpx<R> w = __ldg(&tw[h * (k + q * NS)]);
+        if (DIR > 0) w.y = -w.y;
+        v[q] = cmul(v[q], w);
+    }
+    __syncthreads();                        // every input of the stage is read before any store
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const cpx<R> send = h ? v[i] : v[8 + i];
+        const cpx<R> own = h ? v[8 + i] : v[i];
+        cpx<R> recv;
+        recv.x = __shfl_xor_sync(0xffffffffu, send.x, 1);
+        recv.y = __shfl_xor_sync(0xffffffffu, send.y, 1);
+        const cpx<R> z0 = h ? recv : own;   // Z_0[8h + i]
+        const cpx<R> z1 = h ? own : recv;   // Z_1[8h + i]
+        const int q = 8 * h + i;
+        store(k + q * NS, mk<R>(z0.x + z1.x, z0.y + z1.y));
+        store(k + (q + 16) * NS, mk<R>(z0.x - z1.x, z0.y - z1.y));
+    }
+    __syncthreads();
+}
+
+// Stages NS, 16 NS, ... of a length-P transform: radix 16 while it fits; a
+// remainder of 2 is merged into the last radix-16 stage (radix 32 across lane
+// pairs), a remainder of 4 or 8 is one more stage.  `load` feeds the first of
+// them, `store` takes the last one's outputs (natural order); the others go
+// through `buf`.
+template <typename R, int DIR, int P, int NS, bool FUSE2, class L, class S>
 __device__ __forceinline__ void fft_from(cpx<R>* buf, int t, const cpx<R>* __restrict__ tw, const L& load,
                                          const S& store) {
     constexpr int RAD = (NS * 16 <= P) ? 16 : P / NS;
     if constexpr (NS * RAD == P) {
         fft_stage<R, DIR, RAD, P, NS>(t, tw, load, store);
+    } else if constexpr (FUSE2 && NS * 32 == P) {
+        fft_stage_r32<R, DIR, P, NS>(t, tw, load, store);
     } else {
         fft_stage<R, DIR, RAD, P, NS>(t, tw, load, SmemStore<R>{buf});
-        fft_from<R, DIR, P, NS * RAD>(buf, t, tw, SmemLoad<R>{buf}, store);
+        fft_from<R, DIR, P, NS * RAD, FUSE2>(buf, t, tw, SmemLoad<R>{buf}, store);
     }
 }
 
 // Unscaled length-P complex DFT (DIR = -1: e^{-2 pi i jk/P}, DIR = +1: e^{+...})
 // with input x[j] = load(j) and output X[k] handed to store(k, X[k]);
-// tw[k] = e^{-2 pi i k/P}.  Every thread of the block must call it (it
+// tw[k] = e^{-2 pi i k/P}.  FUSE2 = false keeps a remainder of 2 as its own
+// stage (for store functors heavy enough that the radix-32 stage spills).  Every thread of the block must call it (it
 // synchronises the block); inputs read from `buf` must have been written and
 // synchronised before the call.
-template <typename R, int DIR, int P, class L, class S>
+template <typename R, int DIR, int P, bool FUSE2 = true, class L, class S>
 __device__ __forceinline__ void block_fft(cpx<R>* buf, int t, const cpx<R>* __restrict__ tw, const L& load,
                                           const S& store) {
-    fft_from<R, DIR, P, 1>(buf, t, tw, load, store);
+    fft_from<R, DIR, P, 1, FUSE2>(buf, t, tw, load, store);
 }
 
 // order-preserving bit pattern of a non-negative double (for atomicMax)

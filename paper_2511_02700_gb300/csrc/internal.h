@@ -111,6 +111,24 @@ template <typename R> struct PrepArgs {
     int payoff;
 };
 
+// Multi-job launches: grid dimension y (z for the 2D node kernels) indexes
+// the job, whose arguments are read from a device array.  Inside the
+// fixed-point loop a job that has stopped skips its blocks.
+struct JobsCtl {
+    const int* conv;         // per job: 1 once its loop stopped (converged, kmax or non-finite)
+    const int* kconv;        // per job: the iteration at which it stopped
+    int iter;                // current iteration, 1-based
+    int mode;                // 0: every job; 1: jobs still iterating; 2: those and the ones stopped at `iter`
+#ifdef __CUDACC__
+    __device__ __forceinline__ bool skip(int j) const {
+        if (mode == 0) return false;
+        const int c = conv[j];
+        if (mode == 1) return c != 0;
+        return c != 0 && kconv[j] < iter;
+    }
+#endif
+};
+
 // launchers (sweep.cu), explicitly instantiated for float and double
 template <typename R> cudaError_t launch_row_forward(const FwdArgs<R>& a, cudaStream_t s);
 template <typename R> cudaError_t launch_col(const ColArgs<R>& a, cudaStream_t s);
@@ -118,6 +136,19 @@ template <typename R> cudaError_t launch_row_inverse(const InvArgs<R>& a, cudaSt
 template <typename R> cudaError_t launch_dst_col(const DstColArgs<R>& a, cudaStream_t s);
 template <typename R> cudaError_t launch_dst_row(const DstRowArgs<R>& a, cudaStream_t s);
 template <typename R> cudaError_t launch_prep(const PrepArgs<R>& a, cudaStream_t s);
+// the same kernels over K jobs of one geometry (a0: any job's arguments, for the launch shape)
+template <typename R> cudaError_t launch_row_forward_jobs(const FwdArgs<R>& a0, const FwdArgs<R>* arr, int K,
+                                                         JobsCtl jc, cudaStream_t s);
+template <typename R> cudaError_t launch_col_jobs(const ColArgs<R>& a0, const ColArgs<R>* arr, int K, JobsCtl jc,
+                                                 cudaStream_t s);
+template <typename R> cudaError_t launch_row_inverse_jobs(const InvArgs<R>& a0, const InvArgs<R>* arr, int K,
+                                                         JobsCtl jc, cudaStream_t s);
+template <typename R> cudaError_t launch_dst_col_jobs(const DstColArgs<R>& a0, const DstColArgs<R>* arr, int K,
+                                                     JobsCtl jc, cudaStream_t s);
+template <typename R> cudaError_t launch_dst_row_jobs(const DstRowArgs<R>& a0, const DstRowArgs<R>* arr, int K,
+                                                     JobsCtl jc, cudaStream_t s);
+template <typename R> cudaError_t launch_prep_jobs(const PrepArgs<R>& a0, const PrepArgs<R>* arr, int K,
+                                                  bool explicit_part, cudaStream_t s);
 // omega-hat: forward column FFT of the FP64 row spectra, written as cpx<RO>
 template <typename RO> cudaError_t launch_weights_col(const Geometry& g, const void* Sd, void* Wh, void* Whi,
                                                        const void* twd, cudaStream_t s);
@@ -182,6 +213,24 @@ template <typename R> cudaError_t launch_sl_shift_dots(const Geometry& g, const 
 template <typename R> cudaError_t launch_fp_check(const void* resid, FpCtl* ctl, double tol, int kmax,
                                                  unsigned long long cond_handle, cudaStream_t s);
 cudaError_t launch_fp_tally(FpCtl* ctl, cudaStream_t s);
+
+// multi-job loop control (loop_ctl.cu)
+struct JobCheck {
+    const void* resid;       // the job's R-typed eq. 3.25 maximum (reset to 0 after each read)
+    double tol;
+    int kmax;
+    int pad;
+};
+struct JobsState {
+    int* conv;               // [K] 1 once the job's loop stopped
+    int* kconv;              // [K] iteration at which it stopped
+    int* kcount;             // [K] iterations of the current theta step
+    int* nonconv;            // [K] 1 if a theta step stopped without meeting the tolerance
+    double* last;            // [K] last eq. 3.25 quantity
+    int* active;             // jobs still iterating after the last check
+};
+template <typename R> cudaError_t launch_jobs_reset(int K, const JobCheck* jc, JobsState st, cudaStream_t s);
+template <typename R> cudaError_t launch_jobs_check(int K, const JobCheck* jc, JobsState st, int iter, cudaStream_t s);
 cudaError_t launch_fp_setup(FpCtl* ctl, void* Y, void* BY, int step_end, cudaStream_t s);
 
 // precompute (precompute.cu)

@@ -67,6 +67,64 @@ cudaError_t launch_fp_setup(FpCtl* ctl, void* Y, void* BY, int step_end, cudaStr
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// multi-job fixed-point loop (one launch per kernel over all jobs of a group):
+// the stopping rule of each job, and the count of jobs still iterating
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_jobs_reset(int K, const JobCheck* jc, JobsState st) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < K; j += gridDim.x * blockDim.x) {
+        st.conv[j] = 0;
+        st.kconv[j] = 0;
+        st.kcount[j] = 0;
+        *(R*)jc[j].resid = R(0);
+    }
+}
+
+template <typename R>
+__global__ void k_jobs_check(int K, const JobCheck* jc, JobsState st, int iter) {
+    __shared__ int act;
+    if (threadIdx.x == 0) act = 0;
+    __syncthreads();
+    int mine = 0;
+    for (int j = threadIdx.x; j < K; j += blockDim.x) {
+        if (st.conv[j]) continue;
+        R* rp = (R*)jc[j].resid;
+        const double r = (double)*rp;
+        *rp = R(0);                         // the next iteration's maximum starts from zero
+        st.kcount[j] = iter;
+        st.last[j] = r;
+        const bool ok = r < jc[j].tol;
+        if (ok || iter >= jc[j].kmax || !isfinite(r)) {
+            st.conv[j] = 1;
+            st.kconv[j] = iter;
+            if (!ok) st.nonconv[j] = 1;
+        } else {
+            ++mine;
+        }
+    }
+    if (mine) atomicAdd(&act, mine);
+    __syncthreads();
+    if (threadIdx.x == 0) *st.active = act;
+}
+
+template <typename R>
+cudaError_t launch_jobs_reset(int K, const JobCheck* jc, JobsState st, cudaStream_t s) {
+    k_jobs_reset<R><<<(K + 255) / 256, 256, 0, s>>>(K, jc, st);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_jobs_check(int K, const JobCheck* jc, JobsState st, int iter, cudaStream_t s) {
+    k_jobs_check<R><<<1, 1024, 0, s>>>(K, jc, st, iter);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_jobs_reset<float>(int, const JobCheck*, JobsState, cudaStream_t);
+template cudaError_t launch_jobs_reset<double>(int, const JobCheck*, JobsState, cudaStream_t);
+template cudaError_t launch_jobs_check<float>(int, const JobCheck*, JobsState, int, cudaStream_t);
+template cudaError_t launch_jobs_check<double>(int, const JobCheck*, JobsState, int, cudaStream_t);
+
 template cudaError_t launch_fp_check<float>(const void*, FpCtl*, double, int, unsigned long long, cudaStream_t);
 template cudaError_t launch_fp_check<double>(const void*, FpCtl*, double, int, unsigned long long, cudaStream_t);
 

@@ -97,7 +97,7 @@ void set_smem(K kernel, size_t bytes) {
 // forward row pass: T_in along s1 (from staged nodes) + packed R2C
 // ---------------------------------------------------------------------------
 template <typename R, int P>
-PIDE_FFT_KERNEL(R, P) k_row_forward(FwdArgs<R> a) {
+__device__ __forceinline__ void row_forward_body(const FwdArgs<R>& a) {
     using C = cpx<R>;
     using CF = Cfg<R, P>;
     constexpr int NT = CF::NT, N = P / 2;
@@ -167,13 +167,20 @@ PIDE_FFT_KERNEL(R, P) k_row_forward(FwdArgs<R> a) {
         }
     }
 }
+template <typename R, int P>
+PIDE_FFT_KERNEL(R, P) k_row_forward(const __grid_constant__ FwdArgs<R> a) { row_forward_body<R, P>(a); }
+template <typename R, int P>
+PIDE_FFT_KERNEL(R, P) k_row_forward_jobs(const FwdArgs<R>* __restrict__ arr, JobsCtl jc) {
+    if (jc.skip(blockIdx.y)) return;
+    row_forward_body<R, P>(arr[blockIdx.y]);
+}
 
 // ---------------------------------------------------------------------------
 // column pass: staged column, T_in along s2 in the first stage, product with
 // conj(w^)/P^2 in the last forward stage, inverse FFT writing rows 1..N
 // ---------------------------------------------------------------------------
 template <typename R, int P>
-PIDE_FFT_KERNEL(R, P) k_col(ColArgs<R> a) {
+__device__ __forceinline__ void col_body(const ColArgs<R>& a) {
     using C = cpx<R>;
     using CF = Cfg<R, P>;
     constexpr int NT = CF::NT, N = P / 2;
@@ -214,6 +221,13 @@ PIDE_FFT_KERNEL(R, P) k_col(ColArgs<R> a) {
     };
     block_fft<R, +1, P>(buf, t, tw, SmemLoad<R>{buf}, store_out);
 }
+template <typename R, int P>
+PIDE_FFT_KERNEL(R, P) k_col(const __grid_constant__ ColArgs<R> a) { col_body<R, P>(a); }
+template <typename R, int P>
+PIDE_FFT_KERNEL(R, P) k_col_jobs(const ColArgs<R>* __restrict__ arr, JobsCtl jc) {
+    if (jc.skip(blockIdx.y)) return;
+    col_body<R, P>(arr[blockIdx.y]);
+}
 
 // ---------------------------------------------------------------------------
 // inverse row pass: Hermitian-extended packed spectrum in the first stage,
@@ -221,7 +235,7 @@ PIDE_FFT_KERNEL(R, P) k_col(ColArgs<R> a) {
 // also lays out the odd extension of the residual for the row DST
 // ---------------------------------------------------------------------------
 template <typename R, int P>
-PIDE_FFT_KERNEL(R, P) k_row_inverse(InvArgs<R> a) {
+__device__ __forceinline__ void row_inverse_body(const InvArgs<R>& a) {
     using C = cpx<R>;
     using S_ = St<R>;
     using CF = Cfg<R, P>;
@@ -297,7 +311,7 @@ PIDE_FFT_KERNEL(R, P) k_row_inverse(InvArgs<R> a) {
             buf[padi(P - m1)] = mk<R>(-rr[0], -rr[1]);
         }
     };
-    block_fft<R, +1, P>(buf, t, tw, load, epilogue);
+    block_fft<R, +1, P, false>(buf, t, tw, load, epilogue);
     if (!do_resid) return;   // uniform across the block
     constexpr int GE = rgroup<R>();
     auto store_e = [&](int k, C zz) {
@@ -310,12 +324,19 @@ PIDE_FFT_KERNEL(R, P) k_row_inverse(InvArgs<R> a) {
     };
     block_fft<R, -1, P>(buf, t, tw, SmemLoad<R>{buf}, store_e);
 }
+template <typename R, int P>
+PIDE_FFT_KERNEL(R, P) k_row_inverse(const __grid_constant__ InvArgs<R> a) { row_inverse_body<R, P>(a); }
+template <typename R, int P>
+PIDE_FFT_KERNEL(R, P) k_row_inverse_jobs(const InvArgs<R>* __restrict__ arr, JobsCtl jc) {
+    if (jc.skip(blockIdx.y)) return;
+    row_inverse_body<R, P>(arr[blockIdx.y]);
+}
 
 // ---------------------------------------------------------------------------
 // column DST pass with the eigenvalue division between the two transforms
 // ---------------------------------------------------------------------------
 template <typename R, int P>
-PIDE_FFT_KERNEL(R, P) k_dst_col(DstColArgs<R> a) {
+__device__ __forceinline__ void dst_col_body(const DstColArgs<R>& a) {
     using C = cpx<R>;
     using CF = Cfg<R, P>;
     constexpr int NT = CF::NT, N = P / 2;
@@ -364,13 +385,20 @@ PIDE_FFT_KERNEL(R, P) k_dst_col(DstColArgs<R> a) {
     };
     block_fft<R, -1, P>(buf, t, tw, SmemLoad<R>{buf}, store);
 }
+template <typename R, int P>
+PIDE_FFT_KERNEL(R, P) k_dst_col(const __grid_constant__ DstColArgs<R> a) { dst_col_body<R, P>(a); }
+template <typename R, int P>
+PIDE_FFT_KERNEL(R, P) k_dst_col_jobs(const DstColArgs<R>* __restrict__ arr, JobsCtl jc) {
+    if (jc.skip(blockIdx.y)) return;
+    dst_col_body<R, P>(arr[blockIdx.y]);
+}
 
 // ---------------------------------------------------------------------------
 // row DST back to nodes: increment, state update, eq. 3.25 maximum, and the
 // row pass of the increment's B_w sweep (packed R2C) in the same block
 // ---------------------------------------------------------------------------
 template <typename R, int P>
-PIDE_FFT_KERNEL(R, P) k_dst_row(DstRowArgs<R> a) {
+__device__ __forceinline__ void dst_row_body(const DstRowArgs<R>& a) {
     using C = cpx<R>;
     using CF = Cfg<R, P>;
     constexpr int NT = CF::NT, N = P / 2;
@@ -460,6 +488,13 @@ PIDE_FFT_KERNEL(R, P) k_dst_row(DstRowArgs<R> a) {
         ResidAtomic<R>::max(a.resid, m);
     }
 }
+template <typename R, int P>
+PIDE_FFT_KERNEL(R, P) k_dst_row(const __grid_constant__ DstRowArgs<R> a) { dst_row_body<R, P>(a); }
+template <typename R, int P>
+PIDE_FFT_KERNEL(R, P) k_dst_row_jobs(const DstRowArgs<R>* __restrict__ arr, JobsCtl jc) {
+    if (jc.skip(blockIdx.y)) return;
+    dst_row_body<R, P>(arr[blockIdx.y]);
+}
 
 // ---------------------------------------------------------------------------
 // per-step preparation: W = T_SL[Z] (Algorithm 1 step 2), Y^{n,0} (eq. 3.26),
@@ -474,7 +509,7 @@ __device__ __forceinline__ double far_dbl(const PrepArgs<R>& a, int q1, int q2, 
 
 // cz = h_t (1-theta) (D V - r_w V + B V) at interior nodes (Z - V of Algorithm 1 step 2)
 template <typename R>
-__global__ void k_explicit(PrepArgs<R> a) {
+__device__ __forceinline__ void explicit_body(const PrepArgs<R>& a) {
     const int N = a.g.N;
     const int m1 = blockIdx.x * blockDim.x + threadIdx.x;
     const int m2 = blockIdx.y * blockDim.y + threadIdx.y;
@@ -486,8 +521,15 @@ __global__ void k_explicit(PrepArgs<R> a) {
         a.htm * (diff_state(V, idx, ld, a.d11, a.d22, a.d12) - a.rw * st_r(V[idx]) + st_r(a.BV[idx]));
 }
 
+template <typename R>
+__global__ void k_explicit(const __grid_constant__ PrepArgs<R> a) { explicit_body<R>(a); }
+template <typename R>
+__global__ void k_explicit_jobs(const PrepArgs<R>* __restrict__ arr) {
+    explicit_body<R>(arr[blockIdx.z]);
+}
+
 template <typename R, int NTAP>
-__global__ void __launch_bounds__(256) k_prep(PrepArgs<R> a) {
+__device__ __forceinline__ void prep_body(const PrepArgs<R>& a) {
     const int N = a.g.N;
     const int m1 = blockIdx.x * blockDim.x + threadIdx.x;
     const int m2 = blockIdx.y * blockDim.y + threadIdx.y;
@@ -562,6 +604,13 @@ __global__ void __launch_bounds__(256) k_prep(PrepArgs<R> a) {
         e = R(-6) * st_diff(a.V[1][idx], v) + R(4) * st_diff(a.V[2][idx], v) - st_diff(a.V[3][idx], v);
     }
     a.Y[idx] = st_add(v, e);
+}
+
+template <typename R, int NTAP>
+__global__ void __launch_bounds__(256) k_prep(const __grid_constant__ PrepArgs<R> a) { prep_body<R, NTAP>(a); }
+template <typename R, int NTAP>
+__global__ void __launch_bounds__(256) k_prep_jobs(const PrepArgs<R>* __restrict__ arr) {
+    prep_body<R, NTAP>(arr[blockIdx.z]);
 }
 
 // ---------------------------------------------------------------------------
@@ -672,6 +721,69 @@ cudaError_t launch_fft_kernel(K kernel, const A& a, int work_units, size_t extra
     set_smem(kernel, smem);
     const int blocks = (work_units + CF::UNITS - 1) / CF::UNITS;
     kernel<<<blocks, CF::THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename R, int P, class K, class A>
+cudaError_t launch_fft_kernel_jobs(K kernel, const A* arr, int njobs, JobsCtl jc, int work_units, size_t extra_smem,
+                                   cudaStream_t s) {
+    using CF = Cfg<R, P>;
+    const size_t smem = CF::SMEM + extra_smem;
+    set_smem(kernel, smem);
+    const dim3 grid((work_units + CF::UNITS - 1) / CF::UNITS, njobs);
+    kernel<<<grid, CF::THREADS, smem, s>>>(arr, jc);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_row_forward_jobs(const FwdArgs<R>& a0, const FwdArgs<R>* arr, int K, JobsCtl jc, cudaStream_t s) {
+#define CASE(PP) return launch_fft_kernel_jobs<R, PP>(k_row_forward_jobs<R, PP>, arr, K, jc, a0.npairs, 0, s);
+    PIDE_SWITCH_P(a0.g.P, CASE)
+#undef CASE
+}
+template <typename R>
+cudaError_t launch_col_jobs(const ColArgs<R>& a0, const ColArgs<R>* arr, int K, JobsCtl jc, cudaStream_t s) {
+#define CASE(PP)                                                                                             \
+    if constexpr (LoopSize<R, PP>::ok) return launch_fft_kernel_jobs<R, PP>(k_col_jobs<R, PP>, arr, K, jc, PP / 2 + 1, 0, s); \
+    else return cudaErrorInvalidValue;
+    PIDE_SWITCH_P(a0.g.P, CASE)
+#undef CASE
+}
+template <typename R>
+cudaError_t launch_row_inverse_jobs(const InvArgs<R>& a0, const InvArgs<R>* arr, int K, JobsCtl jc, cudaStream_t s) {
+#define CASE(PP)                                                                                             \
+    if constexpr (LoopSize<R, PP>::ok) return launch_fft_kernel_jobs<R, PP>(k_row_inverse_jobs<R, PP>, arr, K, jc, PP / 4, 0, s); \
+    else return cudaErrorInvalidValue;
+    PIDE_SWITCH_P(a0.g.P, CASE)
+#undef CASE
+}
+template <typename R>
+cudaError_t launch_dst_col_jobs(const DstColArgs<R>& a0, const DstColArgs<R>* arr, int K, JobsCtl jc, cudaStream_t s) {
+#define CASE(PP)                                                                                             \
+    if constexpr (LoopSize<R, PP>::ok) return launch_fft_kernel_jobs<R, PP>(k_dst_col_jobs<R, PP>, arr, K, jc, PP / 4, 0, s); \
+    else return cudaErrorInvalidValue;
+    PIDE_SWITCH_P(a0.g.P, CASE)
+#undef CASE
+}
+template <typename R>
+cudaError_t launch_dst_row_jobs(const DstRowArgs<R>& a0, const DstRowArgs<R>* arr, int K, JobsCtl jc, cudaStream_t s) {
+#define CASE(PP)                                                                                             \
+    if constexpr (LoopSize<R, PP>::ok) return launch_fft_kernel_jobs<R, PP>(k_dst_row_jobs<R, PP>, arr, K, jc, PP / 4, 32 * sizeof(R), s); \
+    else return cudaErrorInvalidValue;
+    PIDE_SWITCH_P(a0.g.P, CASE)
+#undef CASE
+}
+template <typename R>
+cudaError_t launch_prep_jobs(const PrepArgs<R>& a0, const PrepArgs<R>* arr, int K, bool explicit_part, cudaStream_t s) {
+    const dim3 blk(32, 8);
+    const dim3 grd((a0.g.N + 1 + 31) / 32, (a0.g.N + 1 + 7) / 8, K);
+    if (explicit_part) {
+        k_explicit_jobs<R><<<grd, blk, 0, s>>>(arr);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (a0.nt == 2) k_prep_jobs<R, 2><<<grd, blk, 0, s>>>(arr);
+    else k_prep_jobs<R, 4><<<grd, blk, 0, s>>>(arr);
     return cudaGetLastError();
 }
 

@@ -1,8 +1,9 @@
 """pide2d_batch_solve: many independent pricings (uneven grids) on one GPU.
 
-Each job of a batch runs the same kernels as a single pide2d_solve, so the
-batch prices must equal the single-solve prices exactly; one small job is
-also checked against the oracle at the FP32-bulk tolerance.
+Jobs of one geometry run in lockstep through the multi-job kernels, which
+share their bodies with the single-solve kernels, so the batch prices must
+equal the single-solve prices exactly; one small job is also checked against
+the oracle at the FP32-bulk tolerance.
 """
 import pytest
 
@@ -17,7 +18,7 @@ def test_batch_workspace_bytes_and_arguments():
     jobs = [gpu_job(with_(w, n=n)) for w, n in zip(batch_draw(3), (64, 256, 128))]
     one = B.pide2d_workspace_bytes(jobs[1].grid)
     nb = B.pide2d_batch_workspace_bytes(jobs, 2)
-    assert nb >= 2 * one and nb < 2 * one + 512
+    assert nb >= 2 * one and nb < 2 * one + 64 * 1024      # two lanes + the multi-job argument arrays
     assert B.pide2d_batch_workspace_bytes(jobs, 8) == B.pide2d_batch_workspace_bytes(jobs, 3)
     with pytest.raises(B.PideError):
         B.pide2d_batch_workspace_bytes(jobs, 0)
@@ -30,7 +31,10 @@ def _small_batch(count=24):
     out = []
     for i, w in enumerate(batch_draw(count, seed=77)):
         n = (32, 64, 128)[i % 3]
-        out.append(with_(w, n=n, steps=n // 8))
+        w = with_(w, n=n, steps=n // 8)
+        if i % 4 == 0:
+            w = with_(w, sl_order=1)          # a second group of the same size
+        out.append(w)
     return out
 
 
@@ -67,3 +71,24 @@ def test_batch_job_matches_oracle():
     ref = O.Scheme(m, g, c, w.steps, theta=w.theta, tol=w.tol, sl_order=w.sl_order).solve().price
     assert sts == [0, 0]
     assert abs(prices[0] - ref) <= 1e-5 * abs(ref), (prices[0], ref)
+
+
+@pytest.mark.gpu
+def test_batch_reports_iteration_cap_per_job():
+    """kmax = 20 with an unreachable tolerance for half of the jobs: those
+    report NOT_CONVERGED (4) with the same prices as single solves under the
+    same cap; the others converge normally."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_02700_gb300 import binding as B
+    ws = [with_(w, n=32, steps=4, tol=(1e-30 if i % 2 else 1e-8)) for i, w in enumerate(batch_draw(6, seed=9))]
+    prices, sts, stats = B.solve_batch([gpu_job(w) for w in ws], lanes=4, kmax=20)
+    assert sts == [0, 4, 0, 4, 0, 4], sts
+    assert stats.failures == 3 and stats.jobs_done == 6
+    for w, p in zip(ws, prices):
+        s = gpu_solver(w, kmax=20, host_loop=True)
+        p1, _, _, st1 = s.solve()
+        s.close()
+        assert p == p1 and st1 == (4 if w.tol < 1e-20 else 0)
+
