@@ -27,6 +27,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -46,6 +48,7 @@ def args_parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batch", action="store_true", help="skip the 512-pricing batch measurement")
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
+    p.add_argument("--no-sweep", action="store_true", help="skip the FP32-bulk vs FP64 convergence sweep")
     p.add_argument("--host-loop", action="store_true",
                    help="drive the fixed-point loop from the host in the timed region too (one launch per "
                         "kernel, as the profilers see it)")
@@ -155,10 +158,11 @@ def measured_peak():
 
 
 def kernel_source_sha256():
-    """sha256 of the sources of the time-loop kernels (what the ncu counters depend on)."""
+    """sha256 of the sources the ncu counters depend on: the time-loop kernels
+    and the host code that sizes their launches."""
     csrc = os.path.join(ROOT, "paper_2511_02700_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("sweep_impl.cuh", "common.cuh", "state.cuh"):
+    for f in ("sweep_impl.cuh", "common.cuh", "state.cuh", "api.cu"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()
 
@@ -342,6 +346,7 @@ def run_ours(a):
         cb = oracle_sample(steps=6, warmup=1)
     batch = None if (a.no_batch or ws > 1) else run_batch(B, torch, dev)
     adjoint = None if (a.no_adjoint or ws > 1) else run_adjoint(B, torch, dev)
+    sweep = None if (a.no_sweep or ws > 1) else run_sweep(B, torch, dev)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": t_max / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -351,7 +356,7 @@ def run_ours(a):
                        "l2": "working set > L2 (inputs larger than the 129 MB L2, no flush)"},
             "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": gpu_launches,
             "clocks": ck, "fp_iters_per_step": iters, "create_s": create_s, "kernels": kernels,
-            "batch": batch, "adjoint": adjoint,
+            "batch": batch, "adjoint": adjoint, "convergence_sweep": sweep,
             "loop": "host-driven fixed-point loop" if a.host_loop else
                     "device-side fixed-point loop (CUDA graph while-node), one host sync per time step"}
     print(json.dumps(line), flush=True)
@@ -365,7 +370,7 @@ def _job(B, w, payoff=0):
     return grid, model, contract
 
 
-def run_batch(B, torch, dev, lanes=16, fp64_sample=16):
+def run_batch(B, torch, dev, lanes=256, fp64_sample=16):
     """The 512 seed-drawn pricings (N in {128, 256, 512}, FP32-bulk) through
     pide2d_batch_solve, wall time from the call to the prices on the host;
     then the first `fp64_sample` jobs again as plain FP64 GPU solves, for the
@@ -467,6 +472,49 @@ def run_adjoint(B, torch, dev):
                 "fp32_bulk_forward_with_checkpoints_s": t_fwd32, "fp32_bulk_adjoint_s": t_adj32,
                 "fp32_bulk_grad_max_abs_err_over_max_grad": max(abs(a_ - b_) for a_, b_ in zip(g32, grad)) / scale})
     return out
+
+
+def run_sweep(B, torch, dev):
+    """The convergence sweep: alpha in {0.25, 0.5, 0.75} x N in {256, 512,
+    1024}, N/4 steps, tol 1e-8, solved in FP64 and in FP32-bulk on the GPU.
+    Per case: the price at S0, the FP32-bulk error against FP64 at S0 and in
+    max-norm over the region of interest (S_i <= 3K), and the wall times;
+    per alpha the observed order of the FP64 price from the three grids."""
+    import math
+    from paper_2511_02700_gb300.workloads import convergence_sweep
+    cases = []
+    by_alpha = {}
+    for w64, w32 in zip(convergence_sweep("fp64"), convergence_sweep("fp32")):
+        out = {}
+        for tag, w in (("fp64", w64), ("fp32", w32)):
+            g, m, c = _job(B, w)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            s = B.Solver(g, m, c, w.steps, theta=w.theta, tol=w.tol, device=dev)
+            price, V, st, _ = s.solve(values=True)
+            torch.cuda.synchronize(dev)
+            out[tag] = (price, V.cpu().numpy(), time.perf_counter() - t0, st.cell_iters)
+            s.close()
+        n = w64.n
+        h = 2 * w64.half_width / n
+        sg = math.log(w64.strike) - w64.half_width + h * np.arange(n + 1)
+        roi1 = np.exp(sg) <= 3 * w64.strike
+        roi = np.outer(roi1, roi1)
+        roi[0, :] = roi[-1, :] = roi[:, 0] = roi[:, -1] = False
+        p64, V64, t64, c64 = out["fp64"]
+        p32, V32, t32, c32 = out["fp32"]
+        cases.append({"alpha": w64.alpha, "n": n, "steps": w64.steps, "price_fp64": p64, "price_fp32": p32,
+                      "price_rel_err": abs(p32 - p64) / abs(p64),
+                      "roi_maxnorm_rel_err": float(np.abs(V32 - V64)[roi].max() / np.abs(V64[roi]).max()),
+                      "fp64_s": t64, "fp32_s": t32, "fp64_value": c64 / t64, "fp32_value": c32 / t32})
+        by_alpha.setdefault(w64.alpha, []).append(p64)
+    orders = {}
+    for a_, ps in by_alpha.items():
+        d1, d2 = ps[1] - ps[0], ps[2] - ps[1]
+        orders[str(a_)] = math.log2(abs(d1 / d2)) if d2 != 0 else None
+    return {"cases": cases, "fp64_observed_order_256_512_1024": orders,
+            "max_price_rel_err": max(c["price_rel_err"] for c in cases),
+            "max_roi_maxnorm_rel_err": max(c["roi_maxnorm_rel_err"] for c in cases)}
 
 
 def run_e2e(B, torch, dev, grid, model, contract, w, steps):

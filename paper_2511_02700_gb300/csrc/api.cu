@@ -565,6 +565,23 @@ static void build_solve_args(pide2d* H, const SolveSpec<R>& sp, SolveArgs<R>* ou
     ca.rlo = 0;
     ca.rhi = g.P + 2;
     ca.tw = tw;
+    if (sp.far && H->contract.payoff == PIDE2D_PUT_AVG) {
+        // halo rows above the domain where the put's far field vanishes for every
+        // staged s1, i.e. (e^{s1,min} + e^{s2}) / 2 >= K e^{-r tau}: their transforms
+        // are zero, so the row pass stops before them and the column pass treats
+        // them as zero (a relative margin of 1e-6 covers the FP32 evaluation)
+        const double e1min = std::exp(H->s_lo1 + (-N / 2 - 1) * hg);
+        int m2z = 3 * N / 2 + 1;
+        for (int m2 = N; m2 <= 3 * N / 2; ++m2) {
+            if (0.5 * (e1min + std::exp(H->s_lo2 + m2 * hg)) >= sp.Kd * (1.0 + 1e-6)) {
+                m2z = m2;
+                break;
+            }
+        }
+        const int rho_z = m2z + N / 2 + 1;          // first zero row of the staged layout
+        fa.npairs = (rho_z + 1) / 2;
+        ca.rhi = 2 * fa.npairs;                     // rows written by the row pass
+    }
     InvArgs<R>& ia = out->iaf;
     ia.g = g;
     ia.mode = INV_FULL;
@@ -1240,6 +1257,8 @@ static pide2d_status group_solve(pide2d* const* hs, int K, char* scratch, std::s
                     pa0 = pa;
                     A0 = A;
                 }
+                // the launch covers the longest row range of the chunk (each job stops at its own)
+                A0.fa.npairs = std::max(A0.fa.npairs, A.fa.npairs);
             }
             pide2d* H = H0;
             auto arr = [&](size_t off) { return scratch + off; };

@@ -325,7 +325,97 @@ __device__ __forceinline__ void row_inverse_body(const InvArgs<R>& a) {
     block_fft<R, -1, P>(buf, t, tw, SmemLoad<R>{buf}, store_e);
 }
 template <typename R, int P>
-PIDE_FFT_KERNEL(R, P) k_row_inverse(const __grid_constant__ InvArgs<R> a) { row_inverse_body<R, P>(a); }
+// the single-job kernel keeps its own copy of the body: inlined from a
+// reference to the parameter block, this FFT kernel spilled three times more
+PIDE_FFT_KERNEL(R, P) k_row_inverse(InvArgs<R> a) {
+    using C = cpx<R>;
+    using S_ = St<R>;
+    using CF = Cfg<R, P>;
+    constexpr int NT = CF::NT, N = P / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int unit = threadIdx.x / NT, t = threadIdx.x - unit * NT;
+    C* buf = reinterpret_cast<C*>(smem_raw) + (size_t)unit * CF::ULEN;
+    const int p = blockIdx.x * CF::UNITS + unit;
+    const int m2 = 2 * p + 1;
+    const bool valid = m2 <= N - 1;
+    const bool hasb = valid && (m2 + 1 <= N - 1);
+    constexpr int Gc = cgroup<R>();
+    const C* S = (const C*)a.S;
+    const int rows = a.g.rows;
+    const C* tw = (const C*)a.tw;
+    // the device-side fixed-point loop decides on the device whether a residual is needed
+    const bool do_resid = a.conv_flag ? (*a.conv_flag == 0) : (a.do_resid != 0);
+    auto load = [&](int pos) -> C {
+        const bool hi = pos > P / 2;
+        const int k = hi ? P - pos : pos;
+        C xa = mk<R>(0, 0), xb = mk<R>(0, 0);
+        if (valid) {
+            const int g = k / Gc, c = k - g * Gc;
+            xa = S[((size_t)g * rows + (m2 - 1)) * Gc + c];
+            xb = S[((size_t)g * rows + m2) * Gc + c];
+        }
+        if (k == 0 || k == P / 2) { xa.y = 0; xb.y = 0; }
+        if (hi) { xa.y = -xa.y; xb.y = -xb.y; }
+        return mk<R>(xa.x - xb.y, xa.y + xb.x);
+    };
+    const int ld = a.g.ldS, ldR = a.g.ldR;
+    S_* const BYv = a.BYind ? *a.BYind : a.BY;
+    auto epilogue = [&](int m1, C zz) {
+        if (m1 == 0) {
+            if (do_resid) {
+                buf[padi(0)] = mk<R>(0, 0);
+                buf[padi(N)] = mk<R>(0, 0);
+            }
+            return;
+        }
+        if (m1 >= N) return;
+        R rr[2] = {R(0), R(0)};
+        if (valid) {
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                if (half == 1 && !hasb) break;
+                const int row = m2 + half;
+                const R zv = half == 0 ? zz.x : zz.y;
+                const size_t idx = (size_t)row * ld + m1;
+                const size_t idr = (size_t)row * ldR + m1;
+                if (a.mode == INV_OUT) {
+                    a.out[idx] = (double)zv;
+                } else if (a.mode == INV_FULL) {
+                    BYv[idx] = st_from_r<S_, R>(zv);
+                    if (do_resid) {
+                        const S_ y = a.Y[idx];
+                        rr[half] = st_diff(a.W[idx], y) + a.htt * zv - a.htt * a.rw * st_r(y)
+                                   + a.htt * diff_state(a.Y, idx, ld, a.d11, a.d22, a.d12);
+                    }
+                } else {  // INV_INCR
+                    BYv[idx] = st_add(BYv[idx], zv);
+                    if (do_resid) {
+                        const R d = a.D[idr];
+                        rr[half] = a.r[idr] + a.htt * zv
+                                   - (a.cid * d - a.htt * diff_plain(a.D, idr, ldR, a.d11, a.d22, a.d12));
+                    }
+                }
+                if (do_resid) a.r[idr] = rr[half];
+            }
+        }
+        if (do_resid) {
+            buf[padi(m1)] = mk<R>(rr[0], rr[1]);
+            buf[padi(P - m1)] = mk<R>(-rr[0], -rr[1]);
+        }
+    };
+    block_fft<R, +1, P, false>(buf, t, tw, load, epilogue);
+    if (!do_resid) return;   // uniform across the block
+    constexpr int GE = rgroup<R>();
+    auto store_e = [&](int k, C zz) {
+        if (k >= N) return;
+        const int gE = k / GE, c = k - gE * GE;
+        const R va = k >= 1 ? R(-0.5) * zz.y : R(0);
+        const R vb = k >= 1 ? R(0.5) * zz.x : R(0);
+        if (valid) a.E[((size_t)gE * N + m2) * GE + c] = va;
+        if (hasb) a.E[((size_t)gE * N + m2 + 1) * GE + c] = vb;
+    };
+    block_fft<R, -1, P>(buf, t, tw, SmemLoad<R>{buf}, store_e);
+}
 template <typename R, int P>
 PIDE_FFT_KERNEL(R, P) k_row_inverse_jobs(const InvArgs<R>* __restrict__ arr, JobsCtl jc) {
     if (jc.skip(blockIdx.y)) return;
