@@ -13,3 +13,4 @@ from .scheme import (CALL_AVG, PUT_ASSET1, PUT_AVG, Contract, Grid, Precomputed,
                      far_field, greeks, initial_values, jump_direct, jump_fft, midpoints, precompute,
                      r1_moment, sl_interpolate, sl_weights, zones)
 from .sensitivities import PARAMS as SENSITIVITY_PARAMS, price_gradient_fd
+from .price_space import PriceGrid, PriceScheme, PriceSpaceOperators
