@@ -290,6 +290,69 @@ pide2d_status pide2d_batch_solve(const pide2d_job* jobs, int count, const pide2d
                                  void* workspace, size_t workspace_bytes, double* prices, int* statuses,
                                  pide2d_batch_stats* stats);
 
+/* ------------------------------------------------------------------------
+ * The paper's price-space jump operator (Secs. 3.2.2, 4): on a non-uniform
+ * price grid x_0 = 0 < x_1 < ... < x_nx (for example the paper's sinh grid),
+ *   B_w V = T_out I~ C T_in V       (eqs. 3.12-3.17),
+ * with T_in cubic Lagrange in price from the x-grid to the log lattice
+ * y_in_m = e^{(m + 1/2) h_z}, m = -n_z - ny_minus .. n_z + ny_plus - 1 (v = 0
+ * beyond x_nx), C the cross-correlation with the weights w on the z-lattice
+ * of N_z = n_z cells of width h_z (eq. 3.5), I~ keeping
+ * y_out_m = e^{m h_z}, m = -ny_minus .. ny_plus, and T_out cubic Lagrange in
+ * price from y_out back to the x-grid (linear extrapolation for nodes below
+ * y_out_{-ny_minus}).  The correlation is a zero-padded FFT of length
+ * P = the least power of two >= max(#in, 4 n_z); the kept outputs equal
+ * the paper's circulant of size #in (no wrap-around reaches them).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int nx;               /* the grid has nx + 1 nodes per axis, 4 <= nx <= 8192 */
+    const double* x;      /* host: nx + 1 increasing nodes, x[0] = 0            */
+    int n_z;              /* N_z >= 2                                           */
+    double h_z;           /* z- and y-lattice spacing > 0                       */
+    int ny_minus, ny_plus;/* y_out index range (either may be negative)         */
+    int precision;        /* PIDE2D_FP64 (P <= 4096) or PIDE2D_FP32_BULK (FP32  */
+                          /* transforms, P <= 8192); the tables are FP64        */
+} pide2d_price_grid;
+
+typedef struct pide2d_price pide2d_price_t;
+
+/* Workspace bytes for this grid.  Errors: ERR_ARG, ERR_UNSUPPORTED (P too large). */
+pide2d_status pide2d_price_workspace_bytes(const pide2d_price_grid* grid, size_t* bytes);
+
+/* Builds the interpolation tables (host, FP64), the weights w, sigma_w sigma_w^T
+ * and the rates of `model` on the z-lattice (device, FP64) and the weight
+ * spectrum.  workspace: device, 256-byte aligned, >= the bytes above,
+ * caller-owned.  Blocks until done.  Errors: ERR_ARG, ERR_WORKSPACE, ERR_CUDA,
+ * ERR_UNSUPPORTED. */
+pide2d_status pide2d_price_create(const pide2d_price_grid* grid, const pide2d_model* model, void* workspace,
+                                  size_t workspace_bytes, void* cuda_stream, pide2d_price_t** out);
+
+/* out = B_w V on the (nx+1)^2 price grid; V and out: device, (nx+1)^2 doubles,
+ * [m2][m1].  Blocks until done.  Errors: ERR_ARG, ERR_STATE, ERR_CUDA. */
+pide2d_status pide2d_price_apply_jump(pide2d_price_t* h, const double* V, double* out);
+
+/* Algorithm 1 in price space on this grid (Sec. 3.3): V^0 the payoff of
+ * `contract` (put or call on the average) cell-averaged near the kink, then
+ * n_steps theta steps (the first damped unless opts->damping = 0), each
+ *   (I - h_t theta (D + B_w - r_w I)) V^n = T_SL (I + h_t (1-theta)(D + B_w - r_w I)) V^{n-1}
+ * with D the central differences on the non-uniform grid (rows at x = 0
+ * zero, second difference zero and first difference backward at x_max),
+ * T_SL cubic Lagrange at x e^{kappa_w h_t} (linear beyond x_max), and the
+ * fixed-point iteration (3.24)-(3.25) to fp_tol, each implicit system
+ * solved by Jacobi-preconditioned BiCGSTAB to a relative residual of 1e-13.
+ * FP64 fields; the jump operator in the handle's precision.
+ * values_out: device or host, (nx+1)^2 doubles [m2][m1].  Blocks.
+ * Errors: ERR_ARG, ERR_NOT_CONVERGED, ERR_CUDA. */
+pide2d_status pide2d_price_solve(pide2d_price_t* h, const pide2d_contract* contract, double theta, int n_steps,
+                                 double fp_tol, const pide2d_options* opts, double* values_out, pide2d_stats* stats);
+
+/* The weights (2 n_z)^2 as [l2 + n_z][l1 + n_z] (omega_out, device or host) and
+ * the 9 rates of pide2d_get_weights (rates_out, host).  Either may be NULL. */
+pide2d_status pide2d_price_get_weights(pide2d_price_t* h, double* omega_out, double* rates_out);
+
+const char* pide2d_price_last_error(const pide2d_price_t* h);
+void pide2d_price_destroy(pide2d_price_t* h);
+
 /* B_w U (eq. 3.17 sweep) computed without any device allocation.  The paper
  * has no counterpart: this entry point exists for callers that cannot
  * allocate device memory -- e.g. a plugin in a host process whose memory

@@ -11,7 +11,7 @@ from __future__ import annotations
 import ctypes
 import math
 import os
-from ctypes import POINTER, byref, c_double, c_int, c_size_t, c_void_p
+from ctypes import POINTER, byref, c_char_p, c_double, c_int, c_size_t, c_void_p
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpide2d.so")
@@ -59,6 +59,11 @@ class pide2d_batch_stats(ctypes.Structure):
     _fields_ = [("jobs_done", c_int), ("failures", c_int), ("fp_iters_total", c_int), ("cell_iters", c_double)]
 
 
+class pide2d_price_grid(ctypes.Structure):
+    _fields_ = [("nx", c_int), ("x", c_void_p), ("n_z", c_int), ("h_z", c_double), ("ny_minus", c_int),
+                ("ny_plus", c_int), ("precision", c_int)]
+
+
 class PideError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -94,6 +99,17 @@ def lib():
         L.pide2d_tape_bytes.argtypes = [c_void_p, c_int, c_int, POINTER(c_size_t)]
         L.pide2d_record.argtypes = [c_void_p, c_void_p, c_size_t, c_int, c_int]
         L.pide2d_adjoint.argtypes = [c_void_p, POINTER(pide2d_model), c_int, POINTER(c_double)]
+        L.pide2d_price_workspace_bytes.argtypes = [POINTER(pide2d_price_grid), POINTER(c_size_t)]
+        L.pide2d_price_create.argtypes = [POINTER(pide2d_price_grid), POINTER(pide2d_model), c_void_p, c_size_t,
+                                          c_void_p, POINTER(c_void_p)]
+        L.pide2d_price_apply_jump.argtypes = [c_void_p, c_void_p, c_void_p]
+        L.pide2d_price_get_weights.argtypes = [c_void_p, c_void_p, c_void_p]
+        L.pide2d_price_solve.argtypes = [c_void_p, POINTER(pide2d_contract), c_double, c_int, c_double,
+                                         POINTER(pide2d_options), c_void_p, POINTER(pide2d_stats)]
+        L.pide2d_price_last_error.argtypes = [c_void_p]
+        L.pide2d_price_last_error.restype = c_char_p
+        L.pide2d_price_destroy.argtypes = [c_void_p]
+        L.pide2d_price_destroy.restype = None
         L.pide2d_batch_workspace_bytes.argtypes = [POINTER(pide2d_job), c_int, c_int, POINTER(c_size_t)]
         L.pide2d_batch_solve.argtypes = [POINTER(pide2d_job), c_int, POINTER(pide2d_options), c_int, c_void_p,
                                          c_size_t, POINTER(c_double), POINTER(c_int), POINTER(pide2d_batch_stats)]
@@ -102,7 +118,9 @@ def lib():
         for name in ("pide2d_workspace_bytes", "pide2d_create", "pide2d_step", "pide2d_solve",
                      "pide2d_get_values", "pide2d_get_weights", "pide2d_apply_jump", "pide2d_profile",
                      "pide2d_profile_read", "pide2d_jump_static", "pide2d_greeks", "pide2d_batch_workspace_bytes",
-                     "pide2d_batch_solve", "pide2d_tape_bytes", "pide2d_record", "pide2d_adjoint"):
+                     "pide2d_batch_solve", "pide2d_tape_bytes", "pide2d_record", "pide2d_adjoint",
+                     "pide2d_price_workspace_bytes", "pide2d_price_create", "pide2d_price_apply_jump",
+                     "pide2d_price_get_weights", "pide2d_price_solve"):
             getattr(L, name).restype = c_int
         _LIB = L
     return _LIB
@@ -418,4 +436,75 @@ def price_function():
             return (grad_out * g, None, None, None, None, None, None, None, None)
 
     return _Price
+
+
+class PriceJump:
+    """The price-space jump operator B_w = T_out I~ C T_in on a non-uniform
+    price grid (pide2d_price_*); workspace from PyTorch."""
+
+    def __init__(self, x, n_z, h_z, ny_minus, ny_plus, model, precision=PIDE2D_FP64, device="cuda", stream=None):
+        import numpy as np
+        import torch
+        self.torch = torch
+        self._x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+        g = pide2d_price_grid()
+        g.nx = self._x.size - 1
+        g.x = self._x.ctypes.data
+        g.n_z, g.h_z, g.ny_minus, g.ny_plus, g.precision = n_z, h_z, ny_minus, ny_plus, precision
+        self.grid = g
+        n = c_size_t(0)
+        _check(lib().pide2d_price_workspace_bytes(byref(g), byref(n)))
+        self.ws = torch.empty(n.value + 256, dtype=torch.uint8, device=device)
+        base = (self.ws.data_ptr() + 255) & ~255
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        h = c_void_p()
+        st = lib().pide2d_price_create(byref(g), byref(model), c_void_p(base), n.value,
+                                       c_void_p(self.stream.cuda_stream), byref(h))
+        if st != PIDE2D_OK:
+            raise PideError(st, lib().pide2d_last_error(None).decode())
+        self.h = h
+        self.nx1 = g.nx + 1
+
+    def apply(self, V):
+        torch = self.torch
+        V = V.to(device=self.ws.device, dtype=torch.float64).contiguous()
+        out = torch.empty_like(V)
+        st = lib().pide2d_price_apply_jump(self.h, c_void_p(V.data_ptr()), c_void_p(out.data_ptr()))
+        if st != PIDE2D_OK:
+            raise PideError(st, lib().pide2d_price_last_error(self.h).decode())
+        return out
+
+    def solve(self, contract, n_steps, theta=0.5, tol=1e-7, kmax=100, damping=True):
+        """Algorithm 1 in price space on this grid; returns (V device tensor, stats, status)."""
+        torch = self.torch
+        V = torch.empty((self.nx1, self.nx1), dtype=torch.float64, device=self.ws.device)
+        opts = pide2d_options()
+        opts.kmax, opts.damping = kmax, 1 if damping else 0
+        stats = pide2d_stats()
+        st = lib().pide2d_price_solve(self.h, byref(contract), theta, n_steps, tol, byref(opts),
+                                      c_void_p(V.data_ptr()), byref(stats))
+        if st not in (PIDE2D_OK, 4):
+            raise PideError(st, lib().pide2d_price_last_error(self.h).decode())
+        return V, stats, st
+
+    def weights(self):
+        torch = self.torch
+        nzz = 2 * self.grid.n_z
+        om = torch.empty((nzz, nzz), dtype=torch.float64, device=self.ws.device)
+        rates = (c_double * 9)()
+        st = lib().pide2d_price_get_weights(self.h, c_void_p(om.data_ptr()), rates)
+        if st != PIDE2D_OK:
+            raise PideError(st, lib().pide2d_price_last_error(self.h).decode())
+        return om, list(rates)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pide2d_price_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libpide2d.so")
-SOURCES = ["sweep_f32.cu", "sweep_f64.cu", "precompute.cu", "api.cu", "static_jump.cu", "loop_ctl.cu", "adjoint.cu", "batch.cpp"]
+SOURCES = ["sweep_f32.cu", "sweep_f64.cu", "precompute.cu", "api.cu", "static_jump.cu", "loop_ctl.cu", "adjoint.cu", "price_space.cu", "batch.cpp"]
 HEADERS = ["common.cuh", "state.cuh", "internal.h", "sweep_impl.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]

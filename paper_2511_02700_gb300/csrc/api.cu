@@ -855,13 +855,23 @@ static pide2d_status do_step(pide2d* H, int* iters, double* resid) {
     return st;
 }
 
-// weights w (eq. 3.5), the R_I moment (eq. 3.3) and the rates (eq. 3.6) of a
-// model, into the given device buffers (params: the 9 values of pide2d_get_weights)
-static pide2d_status run_precompute(pide2d* H, const pide2d_model& m, double* omega, double* part, double* moment,
-                                    double* params) {
-    const int N = H->L.g.N;
-    cudaStream_t s = H->stream;
-    const double* dgl = H->at<double>(R_GL);
+// Gauss-Legendre nodes and weights of the device precompute, in the order
+// the kernels expect: near, far, edge, payoff, very far
+static std::vector<double> quadrature_nodes() {
+    std::vector<double> gl(kGlTotal);
+    double* p = gl.data();
+    gauss_legendre(kGlNear, p, p + kGlNear);
+    gauss_legendre(kGlFar, p + 2 * kGlNear, p + 2 * kGlNear + kGlFar);
+    gauss_legendre(kGlEdge, p + 2 * (kGlNear + kGlFar), p + 2 * (kGlNear + kGlFar) + kGlEdge);
+    gauss_legendre(kGlPay, p + 2 * (kGlNear + kGlFar + kGlEdge), p + 2 * (kGlNear + kGlFar + kGlEdge) + kGlPay);
+    double* pv = p + 2 * (kGlNear + kGlFar + kGlEdge + kGlPay);
+    gauss_legendre(kGlVfar, pv, pv + kGlVfar);
+    return gl;
+}
+
+// the precompute on a z-lattice of N x N cells of width hz (N_z = N/2)
+static cudaError_t precompute_core(int N, double hz, const double* dgl, const pide2d_model& m, double* omega,
+                                   double* part, double* moment, double* params, cudaStream_t s) {
     // Levy density constants (Sec. 4)
     const double r11 = m.rho[0], r12 = m.rho[1], r22 = m.rho[2];
     const double det = r11 * r22 - r12 * r12;
@@ -881,7 +891,7 @@ static pide2d_status run_precompute(pide2d* H, const pide2d_model& m, double* om
 
     WeightJob j{};
     j.N = N;
-    j.h = H->h;
+    j.h = hz;
     j.M2 = (int)std::ceil(std::sqrt(0.1) * (N / 2) - 0.5);
     j.gl_near_x = dgl;
     j.gl_near_w = dgl + kGlNear;
@@ -893,10 +903,19 @@ static pide2d_status run_precompute(pide2d* H, const pide2d_model& m, double* om
     j.gl_vfar_w = j.gl_vfar_x + kGlVfar;
     j.n_vfar = kGlVfar;
     int nblocks = 0;
-    PIDE_CUDA(launch_weights(L, j, omega, part, &nblocks, s));
+    cudaError_t e = launch_weights(L, j, omega, part, &nblocks, s);
+    if (e != cudaSuccess) return e;
     const double* edge = dgl + 2 * (kGlNear + kGlFar);
-    PIDE_CUDA(launch_moment(L, 2.0 * H->h, edge, edge + kGlEdge, kGlEdge, kTanhSinhStep, moment, s));
-    PIDE_CUDA(launch_finalize(part, nblocks, moment, m.r, m.sigma_cov, params, s));
+    e = launch_moment(L, 2.0 * hz, edge, edge + kGlEdge, kGlEdge, kTanhSinhStep, moment, s);
+    if (e != cudaSuccess) return e;
+    return launch_finalize(part, nblocks, moment, m.r, m.sigma_cov, params, s);
+}
+
+// weights w (eq. 3.5), the R_I moment (eq. 3.3) and the rates (eq. 3.6) of a
+// model, into the given device buffers (params: the 9 values of pide2d_get_weights)
+static pide2d_status run_precompute(pide2d* H, const pide2d_model& m, double* omega, double* part, double* moment,
+                                    double* params) {
+    PIDE_CUDA(precompute_core(H->L.g.N, H->h, H->at<double>(R_GL), m, omega, part, moment, params, H->stream));
     return PIDE2D_OK;
 }
 
@@ -928,14 +947,7 @@ static pide2d_status do_create(pide2d* H) {
     const int N = g.N;
     cudaStream_t s = H->stream;
     // quadrature nodes
-    std::vector<double> gl(kGlTotal);
-    double* p = gl.data();
-    gauss_legendre(kGlNear, p, p + kGlNear);
-    gauss_legendre(kGlFar, p + 2 * kGlNear, p + 2 * kGlNear + kGlFar);
-    gauss_legendre(kGlEdge, p + 2 * (kGlNear + kGlFar), p + 2 * (kGlNear + kGlFar) + kGlEdge);
-    gauss_legendre(kGlPay, p + 2 * (kGlNear + kGlFar + kGlEdge), p + 2 * (kGlNear + kGlFar + kGlEdge) + kGlPay);
-    double* pv = p + 2 * (kGlNear + kGlFar + kGlEdge + kGlPay);
-    gauss_legendre(kGlVfar, pv, pv + kGlVfar);
+    const std::vector<double> gl = quadrature_nodes();
     double* dgl = H->at<double>(R_GL);
     PIDE_CUDA(cudaMemsetAsync(H->ws, 0, H->L.total, s));
     PIDE_CUDA(cudaMemcpyAsync(dgl, gl.data(), gl.size() * 8, cudaMemcpyHostToDevice, s));
@@ -1633,6 +1645,513 @@ static pide2d_status do_adjoint(pide2d* H, const pide2d_model* dirs, int ndirs, 
 }
 
 // ---------------------------------------------------------------------------
+// price-space jump operator on the paper's non-uniform price grid
+// (B_w = T_out I~ C T_in, eqs. 3.12-3.17): tables, weights and spectrum at
+// creation, five kernels per application
+// ---------------------------------------------------------------------------
+struct pide2d_price {
+    pide2d_model model;
+    int precision;
+    int nx1, nz, nin, nout, P;
+    double hz;
+    int ny_minus, ny_plus;
+    cudaStream_t stream;
+    char* ws;
+    size_t off_gl, off_omega, off_pad, off_part, off_moment, off_params, off_rows, off_wh, off_twr, off_twd,
+        off_tin_s, off_tin_w, off_tout_t, off_tout_u, off_A, off_S, off_By, off_loop, total;
+    std::vector<double> x;         // the price nodes
+    double par[9];
+    std::string err;
+    bool broken = false;
+    template <typename T> T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
+};
+
+namespace {
+
+int pow2_at_least(int n) {
+    int p = 16;
+    while (p < n) p *= 2;
+    return p;
+}
+
+// cubic Lagrange weights at t over the four nodes starting at s0
+void lagrange4(const double* nodes, int s0, double t, double w[4]) {
+    for (int q = 0; q < 4; ++q) {
+        double v = 1.0;
+        for (int r = 0; r < 4; ++r)
+            if (r != q) v *= (t - nodes[s0 + r]) / (nodes[s0 + q] - nodes[s0 + r]);
+        w[q] = v;
+    }
+}
+
+// first index k with nodes[k] <= t < nodes[k+1] (clamped to [0, n-2])
+int bracket(const std::vector<double>& nodes, double t) {
+    int lo = 0, hi = (int)nodes.size() - 1;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        if (nodes[mid] <= t) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+std::string check_price_grid(const pide2d_price_grid* g) {
+    if (!g || !g->x) return "price grid or its nodes are NULL";
+    if (g->nx < 4 || g->nx > 8192) return "price grid: 4 <= nx <= 8192";
+    if (g->x[0] != 0.0) return "price grid: x[0] must be 0";
+    for (int i = 0; i < g->nx; ++i)
+        if (!(g->x[i + 1] > g->x[i]) || !std::isfinite(g->x[i + 1])) return "price grid: nodes must increase";
+    if (g->n_z < 2 || !(g->h_z > 0.0) || !std::isfinite(g->h_z)) return "price grid: n_z >= 2 and h_z > 0";
+    if (g->ny_minus + g->ny_plus + 1 < 4) return "price grid: at least four y_out points";
+    if (g->precision != PIDE2D_FP64 && g->precision != PIDE2D_FP32_BULK) return "price grid: precision invalid";
+    return "";
+}
+
+struct PriceSizes {
+    int nx1, nz, nin, nout, P;
+};
+
+PriceSizes price_sizes(const pide2d_price_grid* g) {
+    PriceSizes z{};
+    z.nx1 = g->nx + 1;
+    z.nz = g->n_z;
+    z.nin = g->ny_minus + g->ny_plus + 2 * g->n_z;
+    z.nout = g->ny_minus + g->ny_plus + 1;
+    z.P = pow2_at_least(std::max(z.nin, 4 * z.nz));   // Omega must fit the top-left quarter
+    return z;
+}
+
+template <typename R>
+void price_layout(pide2d_price* H) {
+    const int P = H->P;
+    const int ng = (P / 2 + 1 + cgroup<R>() - 1) / cgroup<R>();
+    const int nzz = 2 * H->nz;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o += align256(bytes);
+        return at;
+    };
+    H->off_gl = take((size_t)kGlTotal * 8);
+    H->off_omega = take((size_t)nzz * nzz * 8);
+    H->off_pad = take((size_t)(P / 2) * (P / 2) * 8);
+    H->off_part = take((size_t)((nzz * nzz + 255) / 256) * 3 * 8);
+    H->off_moment = take(4 * 8);
+    H->off_params = take(16 * 8);
+    H->off_rows = take((size_t)(P / 2 + 1) * P * 16);
+    H->off_wh = take((size_t)ng * P * 16);
+    H->off_twr = take((size_t)P * 2 * sizeof(R));
+    H->off_twd = take((size_t)P * 16);
+    H->off_tin_s = take((size_t)H->nin * 4);
+    H->off_tin_w = take((size_t)H->nin * 4 * 8);
+    H->off_tout_t = take((size_t)H->nx1 * 4);
+    H->off_tout_u = take((size_t)H->nx1 * 4 * 8);
+    H->off_A = take((size_t)P * P * sizeof(R));
+    H->off_S = take((size_t)ng * P * 16);
+    H->off_By = take((size_t)H->nout * H->nout * 8);
+    H->off_loop = o;                // the time-loop fields follow (ps_loop_bytes)
+    H->total = o;
+}
+
+}  // namespace
+
+#define PIDE_PCUDA(call)                                                                  \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            H->err = std::string(#call) + ": " + cudaGetErrorString(e_);                  \
+            H->broken = true;                                                             \
+            return PIDE2D_ERR_CUDA;                                                       \
+        }                                                                                 \
+    } while (0)
+
+template <typename R>
+static pide2d_status price_create(pide2d_price* H, const pide2d_price_grid* g) {
+    cudaStream_t s = H->stream;
+    const int P = H->P, nin = H->nin, nout = H->nout, nx1 = H->nx1;
+    std::vector<double> x(g->x, g->x + nx1);
+    // T_in: x-grid -> y_in (v = 0 beyond x_max); T_out: y_out -> x-grid (linear below y_out)
+    std::vector<int> ts(nin), tt(nx1);
+    std::vector<double> tw(4 * (size_t)nin, 0.0), tu(4 * (size_t)nx1, 0.0);
+    for (int j = 0; j < nin; ++j) {
+        const double y = std::exp((j - H->nz - H->ny_minus + 0.5) * H->hz);
+        if (y > x[nx1 - 1]) {
+            ts[j] = -1;
+            continue;
+        }
+        const int k = bracket(x, y);
+        const int s0 = std::min(std::max(k - 1, 0), nx1 - 4);
+        ts[j] = s0;
+        lagrange4(x.data(), s0, y, &tw[4 * (size_t)j]);
+    }
+    std::vector<double> yo(nout);
+    for (int i = 0; i < nout; ++i) yo[i] = std::exp((i - H->ny_minus) * H->hz);
+    for (int m = 0; m < nx1; ++m) {
+        const double t = x[m];
+        double* u = &tu[4 * (size_t)m];
+        if (t < yo[0] || t > yo[nout - 1]) {
+            const int j = t < yo[0] ? 0 : nout - 2;
+            tt[m] = j;
+            u[0] = (yo[j + 1] - t) / (yo[j + 1] - yo[j]);
+            u[1] = (t - yo[j]) / (yo[j + 1] - yo[j]);
+            continue;
+        }
+        const int k = bracket(yo, t);
+        const int s0 = std::min(std::max(k - 1, 0), nout - 4);
+        tt[m] = s0;
+        lagrange4(yo.data(), s0, t, u);
+    }
+    const std::vector<double> gl = quadrature_nodes();
+    PIDE_PCUDA(cudaMemsetAsync(H->ws, 0, H->total, s));
+    PIDE_PCUDA(cudaMemcpyAsync(H->at<double>(H->off_gl), gl.data(), gl.size() * 8, cudaMemcpyHostToDevice, s));
+    PIDE_PCUDA(cudaMemcpyAsync(H->at<int>(H->off_tin_s), ts.data(), ts.size() * 4, cudaMemcpyHostToDevice, s));
+    PIDE_PCUDA(cudaMemcpyAsync(H->at<double>(H->off_tin_w), tw.data(), tw.size() * 8, cudaMemcpyHostToDevice, s));
+    PIDE_PCUDA(cudaMemcpyAsync(H->at<int>(H->off_tout_t), tt.data(), tt.size() * 4, cudaMemcpyHostToDevice, s));
+    PIDE_PCUDA(cudaMemcpyAsync(H->at<double>(H->off_tout_u), tu.data(), tu.size() * 8, cudaMemcpyHostToDevice, s));
+    PIDE_PCUDA(launch_twiddles<R>(P, H->at<void>(H->off_twr), s));
+    PIDE_PCUDA(launch_twiddles<double>(P, H->at<void>(H->off_twd), s));
+    // weights on the z-lattice (N_z = nz, width hz), then conj(fft2(Omega padded))/P^2
+    const int nzz = 2 * H->nz;
+    PIDE_PCUDA(precompute_core(nzz, H->hz, H->at<double>(H->off_gl), H->model, H->at<double>(H->off_omega),
+                               H->at<double>(H->off_part), H->at<double>(H->off_moment),
+                               H->at<double>(H->off_params), s));
+    PIDE_PCUDA(cudaMemcpy2DAsync(H->at<double>(H->off_pad), (size_t)(P / 2) * 8, H->at<double>(H->off_omega),
+                                 (size_t)nzz * 8, (size_t)nzz * 8, nzz, cudaMemcpyDeviceToDevice, s));
+    Geometry gd{};
+    gd.N = P / 2;
+    gd.P = P;
+    gd.rows = P;
+    gd.ng = P / 2 + 1;
+    FwdArgs<double> wa{};
+    wa.g = gd;
+    wa.mode = FWD_WEIGHTS;
+    wa.omega = H->at<double>(H->off_pad);
+    wa.S = H->at<void>(H->off_rows);
+    wa.pair0 = 0;
+    wa.npairs = P / 4;
+    wa.tw = H->at<void>(H->off_twd);
+    PIDE_PCUDA(launch_row_forward<double>(wa, s));
+    PIDE_PCUDA(launch_weights_col<R>(gd, H->at<void>(H->off_rows), H->at<void>(H->off_wh), nullptr,
+                                     H->at<void>(H->off_twd), s));
+    PIDE_PCUDA(cudaMemcpyAsync(H->par, H->at<double>(H->off_params), 9 * 8, cudaMemcpyDeviceToHost, s));
+    PIDE_PCUDA(cudaStreamSynchronize(s));
+    for (double v : H->par)
+        if (!std::isfinite(v)) {
+            H->err = "price-space precompute: rates are not finite";
+            return PIDE2D_ERR_ARG;
+        }
+    return PIDE2D_OK;
+}
+
+template <typename R>
+static pide2d_status price_apply(pide2d_price* H, const double* V, double* out) {
+    cudaStream_t s = H->stream;
+    const int P = H->P;
+    R* A = H->at<R>(H->off_A);
+    void* S = H->at<void>(H->off_S);
+    const void* tw = H->at<void>(H->off_twr);
+    PIDE_PCUDA(launch_ps_tin<R>(P, H->nin, H->nx1, H->at<int>(H->off_tin_s), H->at<double>(H->off_tin_w), V, A, s));
+    PIDE_PCUDA(launch_ps_rows_fwd<R>(P, A, H->nin, S, tw, s));
+    PIDE_PCUDA(launch_ps_col<R>(P, S, H->at<void>(H->off_wh), H->nin, H->nout, tw, s));
+    PIDE_PCUDA(launch_ps_rows_inv<R>(P, S, H->nout, H->at<double>(H->off_By), H->nout, tw, s));
+    PIDE_PCUDA(launch_ps_tout(H->nx1, H->nout, H->at<int>(H->off_tout_t), H->at<double>(H->off_tout_u),
+                              H->at<double>(H->off_By), H->nout, out, s));
+    PIDE_PCUDA(cudaStreamSynchronize(s));
+    return PIDE2D_OK;
+}
+
+// ---------------------------------------------------------------------------
+// the price-space time loop (Sec. 3.3 on the paper's grid), FP64 fields:
+// explicit part, T_SL, fixed-point iteration with the price-space jump
+// operator, each implicit system solved by Jacobi-preconditioned BiCGSTAB
+// ---------------------------------------------------------------------------
+namespace {
+enum PsField { F_V0, F_V1, F_V2, F_V3, F_V4, F_BV, F_W, F_Z, F_Y, F_YN, F_BY, F_B, F_R, F_RH, F_P, F_VV, F_YY,
+               F_S, F_ZZ, F_T, F_DINV, F_COUNT };
+
+double ps_H(double t) { return t > 0.0 ? t * t * t / 6.0 : 0.0; }
+
+// int_{a1}^{b1} int_{a2}^{b2} max(K - (x1 + x2)/2, 0): the positive part of an affine function
+// integrated twice in closed form
+double ps_put_cell(double K, double a1, double b1, double a2, double b2) {
+    return 4.0 * (ps_H(K - 0.5 * a1 - 0.5 * a2) - ps_H(K - 0.5 * a1 - 0.5 * b2) - ps_H(K - 0.5 * b1 - 0.5 * a2) +
+                  ps_H(K - 0.5 * b1 - 0.5 * b2));
+}
+
+// departure-point tables of one axis: x e^{k ht}, cubic Lagrange, linear beyond x_max
+void ps_sl_table(const std::vector<double>& x, double kappa, double ht, std::vector<int>& s, std::vector<double>& w) {
+    const int n1 = (int)x.size();
+    s.assign(n1, 0);
+    w.assign(4 * (size_t)n1, 0.0);
+    const double f = std::exp(kappa * ht);
+    for (int m = 0; m < n1; ++m) {
+        const double t = x[m] * f;
+        double* u = &w[4 * (size_t)m];
+        if (t > x[n1 - 1]) {
+            s[m] = n1 - 4;
+            u[2] = (x[n1 - 1] - t) / (x[n1 - 1] - x[n1 - 2]);
+            u[3] = (t - x[n1 - 2]) / (x[n1 - 1] - x[n1 - 2]);
+            continue;
+        }
+        const int k = bracket(x, t);
+        const int s0 = std::min(std::max(k - 1, 0), n1 - 4);
+        s[m] = s0;
+        lagrange4(x.data(), s0, t, u);
+    }
+}
+}  // namespace
+
+static size_t ps_field_bytes(int nx1) { return align256((size_t)nx1 * nx1 * 8); }
+
+static size_t ps_loop_bytes(int nx1) {
+    return (size_t)F_COUNT * ps_field_bytes(nx1) + 3 * align256((size_t)nx1 * 3 * 8) + 2 * align256((size_t)nx1 * 4) +
+           2 * align256((size_t)nx1 * 4 * 8) + align256((size_t)ps_reduction_blocks() * 3 * 8) + 256;
+}
+
+static pide2d_status price_solve(pide2d_price* H, const pide2d_contract* c, double theta, int n_steps, double tol,
+                                 int damping, int kmax, double* values_out, pide2d_stats* stats) {
+    cudaStream_t s = H->stream;
+    const int n1 = H->nx1;
+    const size_t n = (size_t)n1 * n1;
+    char* base = H->ws + H->off_loop;
+    auto fld = [&](int i) { return reinterpret_cast<double*>(base + (size_t)i * ps_field_bytes(n1)); };
+    char* q = base + (size_t)F_COUNT * ps_field_bytes(n1);
+    auto take = [&](size_t bytes) {
+        char* at = q;
+        q += align256(bytes);
+        return at;
+    };
+    double* dx = reinterpret_cast<double*>(take((size_t)n1 * 3 * 8));
+    double* da1 = reinterpret_cast<double*>(take((size_t)n1 * 3 * 8));
+    double* db2 = reinterpret_cast<double*>(take((size_t)n1 * 3 * 8));
+    int* ds1 = reinterpret_cast<int*>(take((size_t)n1 * 4));
+    int* ds2 = reinterpret_cast<int*>(take((size_t)n1 * 4));
+    double* dw1 = reinterpret_cast<double*>(take((size_t)n1 * 4 * 8));
+    double* dw2 = reinterpret_cast<double*>(take((size_t)n1 * 4 * 8));
+    double* part = reinterpret_cast<double*>(take((size_t)ps_reduction_blocks() * 3 * 8));
+    double* res = reinterpret_cast<double*>(q);
+    const std::vector<double>& x = H->x;
+    // central differences on the non-uniform grid (Sec. 3.2.1); row 0 zero, last row:
+    // second difference zero, first difference backward
+    std::vector<double> a1(3 * (size_t)n1, 0.0), b2(3 * (size_t)n1, 0.0);
+    for (int m = 1; m < n1 - 1; ++m) {
+        const double hm = x[m] - x[m - 1], hp = x[m + 1] - x[m];
+        a1[3 * m + 0] = -hp / (hm * (hm + hp));
+        a1[3 * m + 1] = (hp - hm) / (hm * hp);
+        a1[3 * m + 2] = hm / (hp * (hm + hp));
+        b2[3 * m + 0] = 2.0 / (hm * (hm + hp));
+        b2[3 * m + 1] = -2.0 / (hm * hp);
+        b2[3 * m + 2] = 2.0 / (hp * (hm + hp));
+    }
+    const double hN = x[n1 - 1] - x[n1 - 2];
+    a1[3 * (n1 - 1) + 0] = -1.0 / hN;
+    a1[3 * (n1 - 1) + 1] = 1.0 / hN;
+    PIDE_PCUDA(cudaMemcpyAsync(dx, x.data(), n1 * 8, cudaMemcpyHostToDevice, s));
+    PIDE_PCUDA(cudaMemcpyAsync(da1, a1.data(), a1.size() * 8, cudaMemcpyHostToDevice, s));
+    PIDE_PCUDA(cudaMemcpyAsync(db2, b2.data(), b2.size() * 8, cudaMemcpyHostToDevice, s));
+    PsDiff d{n1, dx, da1, db2, H->par[4], H->par[5], H->par[6]};
+    const double rw = H->par[1], k1 = H->par[2], k2 = H->par[3];
+
+    // V^0: the payoff, cell-averaged on cells that meet the kink (Sec. 3.2.3)
+    {
+        const double K = c->strike;
+        std::vector<double> lo(n1), hi(n1), v0(n);
+        for (int m = 0; m < n1; ++m) {
+            lo[m] = m == 0 ? -0.5 * (x[0] + x[1]) : 0.5 * (x[m - 1] + x[m]);
+            hi[m] = m == n1 - 1 ? 2.0 * x[n1 - 1] - 0.5 * (x[n1 - 2] + x[n1 - 1]) : 0.5 * (x[m] + x[m + 1]);
+        }
+        for (int m2 = 0; m2 < n1; ++m2)
+            for (int m1 = 0; m1 < n1; ++m1) {
+                const bool kink = lo[m1] + lo[m2] < 2 * K && hi[m1] + hi[m2] > 2 * K;
+                double put = std::max(K - 0.5 * (x[m1] + x[m2]), 0.0);
+                double lin = 0.5 * (x[m1] + x[m2]) - K;
+                if (kink) {
+                    const double area = (hi[m1] - lo[m1]) * (hi[m2] - lo[m2]);
+                    put = ps_put_cell(K, lo[m1], hi[m1], lo[m2], hi[m2]) / area;
+                    lin = 0.25 * (lo[m1] + hi[m1] + lo[m2] + hi[m2]) - K;
+                }
+                v0[(size_t)m2 * n1 + m1] = c->payoff == PIDE2D_CALL_AVG ? put + lin : put;
+            }
+        PIDE_PCUDA(cudaMemcpyAsync(fld(F_V0), v0.data(), n * 8, cudaMemcpyHostToDevice, s));
+        PIDE_PCUDA(cudaStreamSynchronize(s));
+    }
+    auto apply_jump = [&](const double* V, double* out) -> pide2d_status {
+        return H->precision == PIDE2D_FP64 ? price_apply<double>(H, V, out) : price_apply<float>(H, V, out);
+    };
+    auto dots = [&](int nd, PsDots dp, double* out) -> pide2d_status {
+        PIDE_PCUDA(launch_ps_dots(n, nd, dp, part, res, s));
+        PIDE_PCUDA(cudaMemcpyAsync(out, res, nd * 8, cudaMemcpyDeviceToHost, s));
+        PIDE_PCUDA(cudaStreamSynchronize(s));
+        return PIDE2D_OK;
+    };
+    // BiCGSTAB with Jacobi preconditioning for (c0 I - c1 D) X = B, X holding the start
+    auto bicgstab = [&](double c0, double c1, const double* Bv, double* X, int* its) -> pide2d_status {
+        double* r = fld(F_R);
+        double* rh = fld(F_RH);
+        double* p = fld(F_P);
+        double* v = fld(F_VV);
+        double* y = fld(F_YY);
+        double* sv = fld(F_S);
+        double* z = fld(F_ZZ);
+        double* t = fld(F_T);
+        const double* dinv = fld(F_DINV);
+        PIDE_PCUDA(launch_ps_diff(d, X, c0, -c1, nullptr, 0.0, r, s));
+        PIDE_PCUDA(launch_ps_axpy(n, 1.0, Bv, -1.0, r, 0.0, nullptr, nullptr, r, s));
+        PIDE_PCUDA(cudaMemcpyAsync(rh, r, n * 8, cudaMemcpyDeviceToDevice, s));
+        double h2[2];
+        pide2d_status st = dots(2, PsDots{{Bv, r, nullptr}, {Bv, r, nullptr}}, h2);
+        if (st != PIDE2D_OK) return st;
+        const double bn = std::sqrt(h2[0]);
+        double rn = std::sqrt(h2[1]);
+        const double lim = 1e-13 * (bn > 0.0 ? bn : 1.0);
+        double rho = 1.0, alpha = 1.0, omega = 1.0, rho_new = h2[1];
+        *its = 0;
+        for (int it = 0; it < 20000 && rn > lim; ++it) {
+            if (it == 0) {
+                PIDE_PCUDA(cudaMemcpyAsync(p, r, n * 8, cudaMemcpyDeviceToDevice, s));
+            } else {
+                const double beta = (rho_new / rho) * (alpha / omega);
+                PIDE_PCUDA(launch_ps_axpy(n, 1.0, r, beta, p, -beta * omega, v, nullptr, p, s));
+            }
+            PIDE_PCUDA(launch_ps_axpy(n, 1.0, p, 0.0, nullptr, 0.0, nullptr, dinv, y, s));
+            PIDE_PCUDA(launch_ps_diff(d, y, c0, -c1, nullptr, 0.0, v, s));
+            double rv;
+            st = dots(1, PsDots{{rh, nullptr, nullptr}, {v, nullptr, nullptr}}, &rv);
+            if (st != PIDE2D_OK) return st;
+            alpha = rho_new / rv;
+            PIDE_PCUDA(launch_ps_axpy(n, 1.0, r, -alpha, v, 0.0, nullptr, nullptr, sv, s));
+            PIDE_PCUDA(launch_ps_axpy(n, 1.0, sv, 0.0, nullptr, 0.0, nullptr, dinv, z, s));
+            PIDE_PCUDA(launch_ps_diff(d, z, c0, -c1, nullptr, 0.0, t, s));
+            double ts3[3];
+            st = dots(3, PsDots{{t, t, sv}, {sv, t, sv}}, ts3);
+            if (st != PIDE2D_OK) return st;
+            *its = it + 1;
+            if (std::sqrt(ts3[2]) <= lim) {
+                PIDE_PCUDA(launch_ps_axpy(n, 1.0, X, alpha, y, 0.0, nullptr, nullptr, X, s));
+                rn = std::sqrt(ts3[2]);
+                break;
+            }
+            omega = ts3[0] / ts3[1];
+            PIDE_PCUDA(launch_ps_axpy(n, 1.0, X, alpha, y, omega, z, nullptr, X, s));
+            PIDE_PCUDA(launch_ps_axpy(n, 1.0, sv, -omega, t, 0.0, nullptr, nullptr, r, s));
+            rho = rho_new;
+            double rr2[2];
+            st = dots(2, PsDots{{r, rh, nullptr}, {r, r, nullptr}}, rr2);
+            if (st != PIDE2D_OK) return st;
+            rn = std::sqrt(rr2[0]);
+            rho_new = rr2[1];
+        }
+        if (rn > lim) {
+            H->err = "price-space BiCGSTAB did not reach its tolerance";
+            return PIDE2D_ERR_NOT_CONVERGED;
+        }
+        return PIDE2D_OK;
+    };
+
+    std::vector<int> hist{F_V0};
+    std::vector<int> freel{F_V4, F_V3, F_V2, F_V1};
+    int cur = F_V0;
+    pide2d_status st = apply_jump(fld(F_V0), fld(F_BV));
+    if (st != PIDE2D_OK) return st;
+    pide2d_stats S{};
+    const double T = c->maturity, ht_full = T / n_steps;
+    std::vector<int> sl1, sl2;
+    std::vector<double> wl1, wl2;
+    // one theta step from V (field cur) with B_w V in F_BV; start in F_Y; result into `out_field`
+    auto theta_step = [&](int out_field, double ht, double th) -> pide2d_status {
+        const double htm = ht * (1.0 - th), htt = ht * th;
+        double* V = fld(cur);
+        PIDE_PCUDA(launch_ps_diff(d, V, 1.0 - htm * rw, htm, fld(F_BV), htm, fld(F_Z), s));
+        ps_sl_table(x, k1, ht, sl1, wl1);
+        ps_sl_table(x, k2, ht, sl2, wl2);
+        PIDE_PCUDA(cudaMemcpyAsync(ds1, sl1.data(), n1 * 4, cudaMemcpyHostToDevice, s));
+        PIDE_PCUDA(cudaMemcpyAsync(ds2, sl2.data(), n1 * 4, cudaMemcpyHostToDevice, s));
+        PIDE_PCUDA(cudaMemcpyAsync(dw1, wl1.data(), wl1.size() * 8, cudaMemcpyHostToDevice, s));
+        PIDE_PCUDA(cudaMemcpyAsync(dw2, wl2.data(), wl2.size() * 8, cudaMemcpyHostToDevice, s));
+        PIDE_PCUDA(launch_ps_sl(n1, ds1, dw1, ds2, dw2, fld(F_Z), fld(F_W), s));
+        const double c0 = 1.0 + htt * rw, c1 = htt;
+        PIDE_PCUDA(launch_ps_diag_inv(d, c0, c1, fld(F_DINV), s));
+        double err = 0.0;
+        int k = 0;
+        for (k = 1; k <= kmax; ++k) {
+            // B_w Y^{k-1} = B_w Y^{k-2} + B_w (Y^{k-1} - Y^{k-2}) after the first iteration: in
+            // FP32-bulk the rounding then shrinks with the increment and the test (3.25) can
+            // reach tolerances far below FP32's unit roundoff; F_T holds the increment
+            if (k == 1) {
+                pide2d_status js = apply_jump(fld(F_Y), fld(F_BY));
+                if (js != PIDE2D_OK) return js;
+            } else {
+                pide2d_status js = apply_jump(fld(F_T), fld(F_ZZ));
+                if (js != PIDE2D_OK) return js;
+                PIDE_PCUDA(launch_ps_axpy(n, 1.0, fld(F_BY), 1.0, fld(F_ZZ), 0.0, nullptr, nullptr, fld(F_BY), s));
+            }
+            PIDE_PCUDA(launch_ps_axpy(n, htt, fld(F_BY), 1.0, fld(F_W), 0.0, nullptr, nullptr, fld(F_B), s));
+            PIDE_PCUDA(cudaMemcpyAsync(fld(F_YN), fld(F_Y), n * 8, cudaMemcpyDeviceToDevice, s));
+            int its = 0;
+            const pide2d_status js = bicgstab(c0, c1, fld(F_B), fld(F_YN), &its);
+            if (js != PIDE2D_OK) return js;
+            PIDE_PCUDA(launch_ps_maxrel(n, fld(F_YN), fld(F_Y), part, res, s));
+            PIDE_PCUDA(cudaMemcpyAsync(&err, res, 8, cudaMemcpyDeviceToHost, s));
+            PIDE_PCUDA(launch_ps_axpy(n, 1.0, fld(F_YN), -1.0, fld(F_Y), 0.0, nullptr, nullptr, fld(F_T), s));
+            PIDE_PCUDA(cudaMemcpyAsync(fld(F_Y), fld(F_YN), n * 8, cudaMemcpyDeviceToDevice, s));
+            PIDE_PCUDA(cudaStreamSynchronize(s));
+            if (err < tol) break;
+        }
+        if (k > kmax) {
+            H->err = "price-space fixed-point iteration not converged";
+            return PIDE2D_ERR_NOT_CONVERGED;
+        }
+        PIDE_PCUDA(cudaMemcpyAsync(fld(out_field), fld(F_Y), n * 8, cudaMemcpyDeviceToDevice, s));
+        pide2d_status js = apply_jump(fld(out_field), fld(F_BV));
+        if (js != PIDE2D_OK) return js;
+        S.fp_iters_total += k;
+        S.cell_iters += (double)n * (k + 1);
+        return PIDE2D_OK;
+    };
+    int first = 1;
+    if (damping) {
+        const int v0 = cur;
+        for (int j = 0; j < 4; ++j) {
+            const int res = freel.back();
+            freel.pop_back();
+            PIDE_PCUDA(cudaMemcpyAsync(fld(F_Y), fld(cur), n * 8, cudaMemcpyDeviceToDevice, s));
+            st = theta_step(res, ht_full / 4.0, 1.0);
+            if (st != PIDE2D_OK) return st;
+            if (cur != v0) freel.push_back(cur);
+            cur = res;
+        }
+        hist = {cur, v0};
+        first = 2;
+        S.steps_done = 1;
+    }
+    for (int step = first; step <= n_steps; ++step) {
+        // Y^{n,0}: polynomial extrapolation of the history (eq. 3.26)
+        const int cnt = (int)hist.size() < 4 ? (int)hist.size() : 4;
+        static const double coef[4][4] = {{1, 0, 0, 0}, {2, -1, 0, 0}, {3, -3, 1, 0}, {4, -6, 4, -1}};
+        const double* cf = coef[cnt - 1];
+        PIDE_PCUDA(launch_ps_axpy(n, cf[0], fld(hist[0]), cf[1], cnt > 1 ? fld(hist[1]) : nullptr, cf[2],
+                                  cnt > 2 ? fld(hist[2]) : nullptr, nullptr, fld(F_Y), s));
+        if (cnt > 3) PIDE_PCUDA(launch_ps_axpy(n, 1.0, fld(F_Y), cf[3], fld(hist[3]), 0.0, nullptr, nullptr, fld(F_Y), s));
+        const int res = freel.back();
+        freel.pop_back();
+        cur = hist[0];
+        st = theta_step(res, ht_full, theta);
+        if (st != PIDE2D_OK) return st;
+        hist.insert(hist.begin(), res);
+        if (hist.size() > 4) {
+            freel.push_back(hist.back());
+            hist.pop_back();
+        }
+        cur = res;
+        S.steps_done = step;
+    }
+    if (values_out) PIDE_PCUDA(cudaMemcpyAsync(values_out, fld(hist[0]), n * 8, cudaMemcpyDefault, s));
+    PIDE_PCUDA(cudaStreamSynchronize(s));
+    if (stats) *stats = S;
+    return PIDE2D_OK;
+}
+
+// ---------------------------------------------------------------------------
 // public entry points
 // ---------------------------------------------------------------------------
 extern "C" {
@@ -1886,6 +2405,114 @@ pide2d_status pide2d_adjoint(pide2d_t* H, const pide2d_model* dirs, int ndirs, d
     return H->grid.precision == PIDE2D_FP64 ? do_adjoint<double>(H, dirs, ndirs, grad)
                                             : do_adjoint<float>(H, dirs, ndirs, grad);
 }
+
+pide2d_status pide2d_price_workspace_bytes(const pide2d_price_grid* g, size_t* bytes) {
+    const std::string e = check_price_grid(g);
+    if (!e.empty() || !bytes) {
+        g_create_error = e.empty() ? "bytes is NULL" : e;
+        return PIDE2D_ERR_ARG;
+    }
+    const PriceSizes z = price_sizes(g);
+    if (z.P > (g->precision == PIDE2D_FP64 ? 4096 : 8192)) {
+        g_create_error = "price grid: the transform length exceeds 8192 (4096 in FP64)";
+        return PIDE2D_ERR_UNSUPPORTED;
+    }
+    pide2d_price tmp;
+    tmp.nx1 = z.nx1;
+    tmp.nz = z.nz;
+    tmp.nin = z.nin;
+    tmp.nout = z.nout;
+    tmp.P = z.P;
+    if (g->precision == PIDE2D_FP64) price_layout<double>(&tmp);
+    else price_layout<float>(&tmp);
+    *bytes = tmp.total + ps_loop_bytes(z.nx1);
+    return PIDE2D_OK;
+}
+
+pide2d_status pide2d_price_create(const pide2d_price_grid* g, const pide2d_model* model, void* workspace,
+                                  size_t workspace_bytes, void* cuda_stream, pide2d_price_t** out) {
+    if (out) *out = nullptr;
+    if (!out || !model) { g_create_error = "out or model is NULL"; return PIDE2D_ERR_ARG; }
+    size_t need = 0;
+    const pide2d_status st0 = pide2d_price_workspace_bytes(g, &need);
+    if (st0 != PIDE2D_OK) return st0;
+    const double det = model->rho[0] * model->rho[2] - model->rho[1] * model->rho[1];
+    if (!(model->alpha >= 0.0 && model->alpha < 1.0) || !(model->delta > 0.0) || !(model->lambda > 0.0) ||
+        !(model->rho[0] > 0.0) || !(det > 0.0)) {
+        g_create_error = "model invalid (alpha in [0,1), delta, lambda > 0, rho positive definite)";
+        return PIDE2D_ERR_ARG;
+    }
+    if (!workspace || ((uintptr_t)workspace & 255) != 0 || workspace_bytes < need) {
+        g_create_error = "workspace must be 256-byte aligned device memory of >= pide2d_price_workspace_bytes";
+        return PIDE2D_ERR_WORKSPACE;
+    }
+    pide2d_price* H = new (std::nothrow) pide2d_price();
+    if (!H) { g_create_error = "out of host memory"; return PIDE2D_ERR_ARG; }
+    const PriceSizes z = price_sizes(g);
+    H->model = *model;
+    H->precision = g->precision;
+    H->nx1 = z.nx1;
+    H->nz = z.nz;
+    H->nin = z.nin;
+    H->nout = z.nout;
+    H->P = z.P;
+    H->hz = g->h_z;
+    H->ny_minus = g->ny_minus;
+    H->ny_plus = g->ny_plus;
+    H->stream = (cudaStream_t)cuda_stream;
+    H->ws = (char*)workspace;
+    if (g->precision == PIDE2D_FP64) price_layout<double>(H);
+    else price_layout<float>(H);
+    H->x.assign(g->x, g->x + z.nx1);
+    const pide2d_status st = g->precision == PIDE2D_FP64 ? price_create<double>(H, g) : price_create<float>(H, g);
+    if (st != PIDE2D_OK) {
+        g_create_error = H->err;
+        delete H;
+        return st;
+    }
+    *out = H;
+    return PIDE2D_OK;
+}
+
+pide2d_status pide2d_price_apply_jump(pide2d_price_t* H, const double* V, double* out) {
+    if (!H || !V || !out) return PIDE2D_ERR_ARG;
+    if (H->broken) return PIDE2D_ERR_STATE;
+    return H->precision == PIDE2D_FP64 ? price_apply<double>(H, V, out) : price_apply<float>(H, V, out);
+}
+
+pide2d_status pide2d_price_solve(pide2d_price_t* H, const pide2d_contract* c, double theta, int n_steps,
+                                 double fp_tol, const pide2d_options* opts, double* values_out, pide2d_stats* stats) {
+    if (!H || !c) return PIDE2D_ERR_ARG;
+    if (H->broken) return PIDE2D_ERR_STATE;
+    if (c->payoff != PIDE2D_PUT_AVG && c->payoff != PIDE2D_CALL_AVG) {
+        H->err = "price-space solve: put or call on the average";
+        return PIDE2D_ERR_ARG;
+    }
+    if (!(c->strike > 0.0) || !(c->maturity > 0.0) || n_steps < 1 || !(theta >= 0.5 && theta <= 1.0) ||
+        !(fp_tol > 0.0)) {
+        H->err = "price-space solve: strike, maturity, fp_tol > 0, n_steps >= 1, theta in [0.5, 1]";
+        return PIDE2D_ERR_ARG;
+    }
+    const int kmax = (opts && opts->kmax > 0) ? opts->kmax : 100;
+    const int damping = opts ? (opts->damping != 0) : 1;
+    return price_solve(H, c, theta, n_steps, fp_tol, damping, kmax, values_out, stats);
+}
+
+pide2d_status pide2d_price_get_weights(pide2d_price_t* H, double* omega_out, double* rates_out) {
+    if (!H) return PIDE2D_ERR_ARG;
+    if (H->broken) return PIDE2D_ERR_STATE;
+    if (omega_out) {
+        const size_t n = (size_t)(2 * H->nz) * (2 * H->nz);
+        PIDE_PCUDA(cudaMemcpyAsync(omega_out, H->at<double>(H->off_omega), n * 8, cudaMemcpyDefault, H->stream));
+        PIDE_PCUDA(cudaStreamSynchronize(H->stream));
+    }
+    if (rates_out) std::memcpy(rates_out, H->par, 9 * 8);
+    return PIDE2D_OK;
+}
+
+const char* pide2d_price_last_error(const pide2d_price_t* H) { return H ? H->err.c_str() : g_create_error.c_str(); }
+
+void pide2d_price_destroy(pide2d_price_t* H) { delete H; }
 
 const char* pide2d_last_error(const pide2d_t* H) {
     if (!H) return g_create_error.c_str();

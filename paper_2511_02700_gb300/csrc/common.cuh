@@ -314,6 +314,15 @@ __device__ __forceinline__ void block_fft(cpx<R>* buf, int t, const cpx<R>* __re
     fft_from<R, DIR, P, 1, FUSE2>(buf, t, tw, load, store);
 }
 
+// Hint to the bulk-copy engine to bring [p, p + bytes) into L2 (no wait, no
+// completion event).  The range is narrowed to 16-byte boundaries inside it,
+// as the instruction requires, so it never reaches past the caller's range.
+__device__ __forceinline__ void l2_prefetch(const void* p, size_t bytes) {
+    const uintptr_t a = ((uintptr_t)p + 15) & ~(uintptr_t)15;
+    const uintptr_t e = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
+    if (e > a) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((unsigned)(e - a)) : "memory");
+}
+
 // order-preserving bit pattern of a non-negative double (for atomicMax)
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 

@@ -149,6 +149,39 @@ template <typename R> cudaError_t launch_dst_row_jobs(const DstRowArgs<R>& a0, c
                                                      JobsCtl jc, cudaStream_t s);
 template <typename R> cudaError_t launch_prep_jobs(const PrepArgs<R>& a0, const PrepArgs<R>* arr, int K,
                                                   bool explicit_part, cudaStream_t s);
+// price-space jump operator (eqs. 3.12-3.17 on the paper's price grid); P x P transforms
+template <typename R> cudaError_t launch_ps_tin(int P, int nin, int nx1, const int* s, const double* w,
+                                               const double* V, R* A, cudaStream_t st);
+template <typename R> cudaError_t launch_ps_rows_fwd(int P, const R* A, int nin, void* S, const void* tw,
+                                                    cudaStream_t st);
+template <typename R> cudaError_t launch_ps_col(int P, void* S, const void* Wh, int nin, int nout, const void* tw,
+                                               cudaStream_t st);
+template <typename R> cudaError_t launch_ps_rows_inv(int P, const void* S, int nout, double* By, int ldB,
+                                                    const void* tw, cudaStream_t st);
+cudaError_t launch_ps_tout(int nx1, int nout, const int* t, const double* u, const double* By, int ldB, double* out,
+                           cudaStream_t st);
+// price-space diffusion and the Krylov solve around it (price_space.cu), FP64
+struct PsDiff {
+    int n1;                  // nodes per axis
+    const double* x;         // [n1] price nodes
+    const double* a1;        // [n1][3] first-difference coefficients (row 0 zero, last row backward)
+    const double* b2;        // [n1][3] second-difference coefficients (first and last rows zero)
+    double A11, A12, A22;    // sigma_w sigma_w^T
+};
+cudaError_t launch_ps_diff(const PsDiff& d, const double* v, double alpha, double beta, const double* w, double gamma,
+                           double* out, cudaStream_t s);
+cudaError_t launch_ps_diag_inv(const PsDiff& d, double c0, double c1, double* dinv, cudaStream_t s);
+cudaError_t launch_ps_axpy(size_t n, double a, const double* x, double b, const double* y, double c, const double* z,
+                           const double* dinv, double* out, cudaStream_t s);
+int ps_reduction_blocks();
+struct PsDots {
+    const double* x[3];
+    const double* y[3];
+};
+cudaError_t launch_ps_dots(size_t n, int nd, const PsDots& dp, double* part, double* res, cudaStream_t s);
+cudaError_t launch_ps_maxrel(size_t n, const double* a, const double* b, double* part, double* res, cudaStream_t s);
+cudaError_t launch_ps_sl(int n1, const int* s1, const double* w1, const int* s2, const double* w2, const double* Z,
+                         double* W, cudaStream_t s);
 // omega-hat: forward column FFT of the FP64 row spectra, written as cpx<RO>
 template <typename RO> cudaError_t launch_weights_col(const Geometry& g, const void* Sd, void* Wh, void* Whi,
                                                        const void* twd, cudaStream_t s);

@@ -194,6 +194,9 @@ __device__ __forceinline__ void col_body(const ColArgs<R>& a) {
     C* col = (C*)a.S + (size_t)g * a.g.rows * Gc + c;
     const C* tw = (const C*)a.tw;
     const C* wh = (const C*)a.Wh + (size_t)g * P * Gc + c;
+    // the four blocks of a column group each bring a quarter of the group's
+    // weight spectrum into L2 while the forward transform runs
+    if (t == 0 && valid) l2_prefetch((const C*)a.Wh + ((size_t)g * P + (size_t)c * (P / Gc)) * Gc, (size_t)P * sizeof(C));
     auto store_mul = [&](int k2, C v) {
         const C w = valid ? __ldg(&wh[(size_t)k2 * Gc]) : mk<R>(0, 0);
         buf[padi(k2)] = cmul(v, w);
@@ -234,6 +237,27 @@ PIDE_FFT_KERNEL(R, P) k_col_jobs(const ColArgs<R>* __restrict__ arr, JobsCtl jc)
 // B_w at the interior nodes + state/residual update in the last stage, which
 // also lays out the odd extension of the residual for the row DST
 // ---------------------------------------------------------------------------
+// L2 prefetch of the field rows the inverse row pass's epilogue reads for
+// rows m2 (and m2 + 1): they arrive while the transform runs
+template <typename R>
+__device__ __forceinline__ void prefetch_inverse_rows(const InvArgs<R>& a, const St<R>* BYv, int m2, bool hasb,
+                                                      bool do_resid) {
+    using S_ = St<R>;
+    const int N = a.g.N, ld = a.g.ldS, ldR = a.g.ldR;
+    const int nr = hasb ? 2 : 1;
+    const int lo = m2 - 1, hi = m2 + 2 < N ? m2 + 2 : N;     // stencil rows, inside the N + 1 rows
+    if (a.mode == INV_INCR) {
+        l2_prefetch(BYv + (size_t)m2 * ld, (size_t)nr * ld * sizeof(S_));
+        if (do_resid) {
+            l2_prefetch(a.r + (size_t)m2 * ldR, (size_t)nr * ldR * sizeof(R));
+            l2_prefetch(a.D + (size_t)lo * ldR, (size_t)(hi - lo + 1) * ldR * sizeof(R));
+        }
+    } else if (a.mode == INV_FULL && do_resid) {
+        l2_prefetch(a.W + (size_t)m2 * ld, (size_t)nr * ld * sizeof(S_));
+        l2_prefetch(a.Y + (size_t)lo * ld, (size_t)(hi - lo + 1) * ld * sizeof(S_));
+    }
+}
+
 template <typename R, int P>
 __device__ __forceinline__ void row_inverse_body(const InvArgs<R>& a) {
     using C = cpx<R>;
@@ -268,6 +292,7 @@ __device__ __forceinline__ void row_inverse_body(const InvArgs<R>& a) {
     };
     const int ld = a.g.ldS, ldR = a.g.ldR;
     S_* const BYv = a.BYind ? *a.BYind : a.BY;
+    if (t == 0 && valid) prefetch_inverse_rows(a, BYv, m2, hasb, do_resid);
     auto epilogue = [&](int m1, C zz) {
         if (m1 == 0) {
             if (do_resid) {
@@ -360,6 +385,7 @@ PIDE_FFT_KERNEL(R, P) k_row_inverse(InvArgs<R> a) {
     };
     const int ld = a.g.ldS, ldR = a.g.ldR;
     S_* const BYv = a.BYind ? *a.BYind : a.BY;
+    if (t == 0 && valid) prefetch_inverse_rows(a, BYv, m2, hasb, do_resid);
     auto epilogue = [&](int m1, C zz) {
         if (m1 == 0) {
             if (do_resid) {
@@ -516,6 +542,8 @@ __device__ __forceinline__ void dst_row_body(const DstRowArgs<R>& a) {
     St<R>* const Yv = a.Yind ? *a.Yind : a.Y;
     R rmax = 0;
     const int ld = a.g.ldS, ldR = a.g.ldR;
+    // the state rows updated after the DST arrive in L2 while it runs
+    if (t == 0 && valid) l2_prefetch(Yv + (size_t)m2 * ld, (size_t)(hasb ? 2 : 1) * ld * sizeof(St<R>));
     // the increment also enters the next B_w sweep: it is laid out at its
     // R2C position p = m1 + N/2 + 1 (zero elsewhere) for the second transform
     auto update = [&](int m1, C zz) {
@@ -701,6 +729,144 @@ __global__ void __launch_bounds__(256) k_prep(const __grid_constant__ PrepArgs<R
 template <typename R, int NTAP>
 __global__ void __launch_bounds__(256) k_prep_jobs(const PrepArgs<R>* __restrict__ arr) {
     prep_body<R, NTAP>(arr[blockIdx.z]);
+}
+
+// ---------------------------------------------------------------------------
+// price-space jump operator B_w = T_out I~ C T_in (eqs. 3.12-3.17 on the
+// paper's non-uniform price grid): T_in into a P x P real array on the
+// y_in lattice, the zero-padded correlation with Omega by row R2C, column
+// (forward, * conj(w^)/P^2, inverse) and row C2R passes, T_out back
+// ---------------------------------------------------------------------------
+// A[j2][j1] = sum_{b,c} w[j2][b] w[j1][c] V[s[j2]+b][s[j1]+c] on j < nin (s = -1: beyond x_max, 0)
+template <typename R>
+__global__ void k_ps_tin(int P, int nin, int nx1, const int* __restrict__ s, const double* __restrict__ w,
+                         const double* __restrict__ V, R* __restrict__ A) {
+    const int j1 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j2 = blockIdx.y * blockDim.y + threadIdx.y;
+    if (j1 >= P || j2 >= P) return;
+    double acc = 0.0;
+    if (j1 < nin && j2 < nin) {
+        const int a1 = s[j1], a2 = s[j2];
+        if (a1 >= 0 && a2 >= 0) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const double* row = V + (size_t)(a2 + b) * nx1 + a1;
+                double r = 0.0;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) r += w[j1 * 4 + c] * row[c];
+                acc += w[j2 * 4 + b] * r;
+            }
+        }
+    }
+    A[(size_t)j2 * P + j1] = (R)acc;
+}
+
+// rows 2p, 2p+1 of A (rows and columns >= nin are zero): packed R2C into S [group][row][c]
+template <typename R, int P>
+PIDE_FFT_KERNEL(R, P) k_ps_rows_fwd(const R* __restrict__ A, int nin, void* Sv, int rows, int ng, const void* twv) {
+    using C = cpx<R>;
+    using CF = Cfg<R, P>;
+    constexpr int NT = CF::NT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int unit = threadIdx.x / NT, t = threadIdx.x - unit * NT;
+    C* buf = reinterpret_cast<C*>(smem_raw) + (size_t)unit * CF::ULEN;
+    const int p = blockIdx.x * CF::UNITS + unit;
+    const int rho = 2 * p;
+    const bool valid = rho < nin;
+    const C* tw = (const C*)twv;
+    auto load = [&](int i) -> C {
+        R xa = 0, xb = 0;
+        if (valid && i < nin) {
+            xa = A[(size_t)rho * P + i];
+            if (rho + 1 < nin) xb = A[(size_t)(rho + 1) * P + i];
+        }
+        return mk<R>(xa, xb);
+    };
+    block_fft<R, -1, P>(buf, t, tw, load, SmemStore<R>{buf});
+    constexpr int Gc = cgroup<R>();
+    C* S = (C*)Sv;
+    for (int g = t; g < ng; g += NT) {
+#pragma unroll
+        for (int c = 0; c < Gc; ++c) {
+            const int k = g * Gc + c;
+            C xa = mk<R>(0, 0), xb = mk<R>(0, 0);
+            if (k <= P / 2) {
+                const C zk = buf[padi(k)];
+                const C zm = buf[padi((P - k) & (P - 1))];
+                xa = mk<R>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
+                xb = mk<R>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
+            }
+            if (valid) {
+                S[((size_t)g * rows + rho) * Gc + c] = xa;
+                S[((size_t)g * rows + rho + 1) * Gc + c] = xb;
+            }
+        }
+    }
+}
+
+// column k1: rows < nin in, forward FFT, * Wh, inverse FFT, rows < nout out (in place)
+template <typename R, int P>
+PIDE_FFT_KERNEL(R, P) k_ps_col(void* Sv, const void* Whv, int rows, int nin, int nout, const void* twv) {
+    using C = cpx<R>;
+    using CF = Cfg<R, P>;
+    constexpr int NT = CF::NT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int unit = threadIdx.x / NT, t = threadIdx.x - unit * NT;
+    C* buf = reinterpret_cast<C*>(smem_raw) + (size_t)unit * CF::ULEN;
+    const int k1 = blockIdx.x * CF::UNITS + unit;
+    const bool valid = k1 <= P / 2;
+    constexpr int Gc = cgroup<R>();
+    const int g = k1 / Gc, c = k1 - g * Gc;
+    C* col = (C*)Sv + (size_t)g * rows * Gc + c;
+    const C* wh = (const C*)Whv + (size_t)g * P * Gc + c;
+    const C* tw = (const C*)twv;
+    auto load = [&](int rho) -> C { return (valid && rho < nin) ? col[(size_t)rho * Gc] : mk<R>(0, 0); };
+    auto store_mul = [&](int k2, C v) {
+        const C w = valid ? __ldg(&wh[(size_t)k2 * Gc]) : mk<R>(0, 0);
+        buf[padi(k2)] = cmul(v, w);
+    };
+    block_fft<R, -1, P>(buf, t, tw, load, store_mul);
+    auto store_out = [&](int m, C v) {
+        if (valid && m < nout) col[(size_t)m * Gc] = v;
+    };
+    block_fft<R, +1, P>(buf, t, tw, SmemLoad<R>{buf}, store_out);
+}
+
+// output rows 2p, 2p+1 (< nout): packed C2R of the Hermitian spectrum, By[row][m1] for m1 < nout
+template <typename R, int P>
+PIDE_FFT_KERNEL(R, P) k_ps_rows_inv(const void* Sv, int rows, int nout, double* __restrict__ By, int ldB,
+                                    const void* twv) {
+    using C = cpx<R>;
+    using CF = Cfg<R, P>;
+    constexpr int NT = CF::NT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int unit = threadIdx.x / NT, t = threadIdx.x - unit * NT;
+    C* buf = reinterpret_cast<C*>(smem_raw) + (size_t)unit * CF::ULEN;
+    const int p = blockIdx.x * CF::UNITS + unit;
+    const int r = 2 * p;
+    const bool valid = r < nout;
+    constexpr int Gc = cgroup<R>();
+    const C* S = (const C*)Sv;
+    const C* tw = (const C*)twv;
+    auto load = [&](int pos) -> C {
+        const bool hi = pos > P / 2;
+        const int k = hi ? P - pos : pos;
+        C xa = mk<R>(0, 0), xb = mk<R>(0, 0);
+        if (valid) {
+            const int g = k / Gc, c = k - g * Gc;
+            xa = S[((size_t)g * rows + r) * Gc + c];
+            xb = S[((size_t)g * rows + r + 1) * Gc + c];
+        }
+        if (k == 0 || k == P / 2) { xa.y = 0; xb.y = 0; }
+        if (hi) { xa.y = -xa.y; xb.y = -xb.y; }
+        return mk<R>(xa.x - xb.y, xa.y + xb.x);
+    };
+    auto store = [&](int m1, C z) {
+        if (!valid || m1 >= nout) return;
+        By[(size_t)r * ldB + m1] = (double)z.x;
+        if (r + 1 < nout) By[(size_t)(r + 1) * ldB + m1] = (double)z.y;
+    };
+    block_fft<R, +1, P>(buf, t, tw, load, store);
 }
 
 // ---------------------------------------------------------------------------
@@ -927,6 +1093,52 @@ cudaError_t launch_prep(const PrepArgs<R>& a, cudaStream_t s) {
     if (a.nt == 2) k_prep<R, 2><<<grd, blk, 0, s>>>(a);
     else k_prep<R, 4><<<grd, blk, 0, s>>>(a);
     return cudaGetLastError();
+}
+template <typename R>
+cudaError_t launch_ps_tin(int P, int nin, int nx1, const int* s, const double* w, const double* V, R* A,
+                          cudaStream_t st) {
+    const dim3 blk(32, 8), grd((P + 31) / 32, (P + 7) / 8);
+    k_ps_tin<R><<<grd, blk, 0, st>>>(P, nin, nx1, s, w, V, A);
+    return cudaGetLastError();
+}
+template <typename R>
+cudaError_t launch_ps_rows_fwd(int P, const R* A, int nin, void* S, const void* tw, cudaStream_t st) {
+    const int rows = P, ng = (P / 2 + 1 + cgroup<R>() - 1) / cgroup<R>();
+#define CASE(PP)                                                                                     \
+    if constexpr (LoopSize<R, PP>::ok) {                                                             \
+        using CF = Cfg<R, PP>;                                                                       \
+        set_smem(k_ps_rows_fwd<R, PP>, CF::SMEM);                                                    \
+        const int units = (nin + 1) / 2;                                                             \
+        k_ps_rows_fwd<R, PP><<<(units + CF::UNITS - 1) / CF::UNITS, CF::THREADS, CF::SMEM, st>>>(A, nin, S, rows, ng, tw); \
+        return cudaGetLastError();                                                                   \
+    } else return cudaErrorInvalidValue;
+    PIDE_SWITCH_P(P, CASE)
+#undef CASE
+}
+template <typename R>
+cudaError_t launch_ps_col(int P, void* S, const void* Wh, int nin, int nout, const void* tw, cudaStream_t st) {
+#define CASE(PP)                                                                                     \
+    if constexpr (LoopSize<R, PP>::ok) {                                                             \
+        using CF = Cfg<R, PP>;                                                                       \
+        set_smem(k_ps_col<R, PP>, CF::SMEM);                                                         \
+        k_ps_col<R, PP><<<(PP / 2 + 1 + CF::UNITS - 1) / CF::UNITS, CF::THREADS, CF::SMEM, st>>>(S, Wh, PP, nin, nout, tw); \
+        return cudaGetLastError();                                                                   \
+    } else return cudaErrorInvalidValue;
+    PIDE_SWITCH_P(P, CASE)
+#undef CASE
+}
+template <typename R>
+cudaError_t launch_ps_rows_inv(int P, const void* S, int nout, double* By, int ldB, const void* tw, cudaStream_t st) {
+#define CASE(PP)                                                                                     \
+    if constexpr (LoopSize<R, PP>::ok) {                                                             \
+        using CF = Cfg<R, PP>;                                                                       \
+        set_smem(k_ps_rows_inv<R, PP>, CF::SMEM);                                                    \
+        const int units = (nout + 1) / 2;                                                            \
+        k_ps_rows_inv<R, PP><<<(units + CF::UNITS - 1) / CF::UNITS, CF::THREADS, CF::SMEM, st>>>(S, PP, nout, By, ldB, tw); \
+        return cudaGetLastError();                                                                   \
+    } else return cudaErrorInvalidValue;
+    PIDE_SWITCH_P(P, CASE)
+#undef CASE
 }
 template <typename RO>
 cudaError_t launch_weights_col(const Geometry& g, const void* Sd, void* Wh, void* Whi, const void* twd,
