@@ -32,6 +32,9 @@ template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
     C c; c.x = a.x * b.x - a.y * b.y; c.y = a.x * b.y + a.y * b.x; return c;
 }
 template <typename C> __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
+template <typename C> __device__ __forceinline__ C csq(C a) {
+    C c; c.x = a.x * a.x - a.y * a.y; c.y = 2 * a.x * a.y; return c;
+}
 template <typename C, typename R> __device__ __forceinline__ C cscale(C a, R s) { a.x *= s; a.y *= s; return a; }
 
 // padded shared-memory index: one pad element per 16
@@ -68,6 +71,42 @@ __device__ __forceinline__ C mul_w16(C v) {
         const R c = (R)c16[m];
         const R s = (R)(DIR > 0 ? s16[m] : -s16[m]);
         C r; r.x = v.x * c - v.y * s; r.y = v.x * s + v.y * c; return r;
+    }
+}
+
+// v * e^{DIR 2 pi i m / 32} for a compile-time m in [0, 16)
+template <int DIR, int M, typename C>
+__device__ __forceinline__ C mul_w32(C v) {
+    using R = decltype(v.x);
+    static_assert(M >= 0 && M < 16, "m in [0, 16)");
+    // cos(2 pi m/32), sin(2 pi m/32) for m = 0..15
+    constexpr double c32[16] = {1.0, 0.98078528040323044, 0.92387953251128674, 0.83146961230254524,
+                                0.70710678118654752, 0.55557023301960218, 0.38268343236508977, 0.19509032201612826,
+                                0.0, -0.19509032201612826, -0.38268343236508977, -0.55557023301960218,
+                                -0.70710678118654752, -0.83146961230254524, -0.92387953251128674, -0.98078528040323044};
+    constexpr double s32[16] = {0.0, 0.19509032201612826, 0.38268343236508977, 0.55557023301960218,
+                                0.70710678118654752, 0.83146961230254524, 0.92387953251128674, 0.98078528040323044,
+                                1.0, 0.98078528040323044, 0.92387953251128674, 0.83146961230254524,
+                                0.70710678118654752, 0.55557023301960218, 0.38268343236508977, 0.19509032201612826};
+    if constexpr (M == 0) {
+        return v;
+    } else if constexpr (M == 8) {          // multiply by DIR*i
+        C r;
+        if constexpr (DIR > 0) { r.x = -v.y; r.y = v.x; } else { r.x = v.y; r.y = -v.x; }
+        return r;
+    } else {
+        const R c = (R)c32[M];
+        const R s = (R)(DIR > 0 ? s32[M] : -s32[M]);
+        C r; r.x = v.x * c - v.y * s; r.y = v.x * s + v.y * c; return r;
+    }
+}
+// v[q] *= e^{DIR 2 pi i q / 32} for q = Q..15 where `on`, unchanged elsewhere
+template <int DIR, int Q, typename C>
+__device__ __forceinline__ void mul_w32_sel(C* v, bool on) {
+    if constexpr (Q < 16) {
+        const C m = mul_w32<DIR, Q>(v[Q]);
+        if (on) v[Q] = m;
+        mul_w32_sel<DIR, Q + 1>(v, on);
     }
 }
 
@@ -167,15 +206,17 @@ __device__ __forceinline__ void fft_stage(int t, const cpx<R>* __restrict__ tw, 
         if constexpr (NS > 1) {
             const int k = j & (NS - 1);
             if constexpr (RAD == 16) {
-                // w^r = w^{4a} w^b (r = 4a + b): six table loads, nine products,
-                // each twiddle at most one rounding away from the table
+                // w^r = w^{4a} w^b (r = 4a + b) from two table loads, w and w^4:
+                // squares and products give w^2, w^3, w^8, w^12 (each twiddle
+                // within a few roundings of the table)
                 cpx<R> wb[4], wa[4];
-#pragma unroll
-                for (int q = 1; q < 4; ++q) {
-                    wb[q] = __ldg(&tw[k * (q * TWS)]);
-                    wa[q] = __ldg(&tw[k * (4 * q * TWS)]);
-                    if (DIR > 0) { wb[q].y = -wb[q].y; wa[q].y = -wa[q].y; }
-                }
+                wb[1] = __ldg(&tw[k * TWS]);
+                wa[1] = __ldg(&tw[k * (4 * TWS)]);
+                if (DIR > 0) { wb[1].y = -wb[1].y; wa[1].y = -wa[1].y; }
+                wb[2] = csq(wb[1]);
+                wb[3] = cmul(wb[2], wb[1]);
+                wa[2] = csq(wa[1]);
+                wa[3] = cmul(wa[2], wa[1]);
 #pragma unroll
                 for (int r = 1; r < 16; ++r) {
                     const int qa = r >> 2, qb = r & 3;
@@ -239,15 +280,16 @@ __device__ __forceinline__ void fft_stage_r32(int t, const cpx<R>* __restrict__ 
         for (int m = 0; m < 16; ++m) v[m] = load(j + (2 * m + h) * NS);
     }
     if constexpr (NS > 1) {
-        // w^{2km} = w^{2k(4a+b)}: six table loads, nine products
+        // w^{2km} = w^{2k(4a+b)} from two table loads (w^{2k}, w^{8k}), as in fft_stage
         const int e = 2 * k;
         cpx<R> wb[4], wa[4];
-#pragma unroll
-        for (int q = 1; q < 4; ++q) {
-            wb[q] = __ldg(&tw[e * q]);
-            wa[q] = __ldg(&tw[4 * e * q]);
-            if (DIR > 0) { wb[q].y = -wb[q].y; wa[q].y = -wa[q].y; }
-        }
+        wb[1] = __ldg(&tw[e]);
+        wa[1] = __ldg(&tw[4 * e]);
+        if (DIR > 0) { wb[1].y = -wb[1].y; wa[1].y = -wa[1].y; }
+        wb[2] = csq(wb[1]);
+        wb[3] = cmul(wb[2], wb[1]);
+        wa[2] = csq(wa[1]);
+        wa[3] = cmul(wa[2], wa[1]);
 #pragma unroll
         for (int m = 1; m < 16; ++m) {
             const int qa = m >> 2, qb = m & 3;
@@ -259,13 +301,15 @@ __device__ __forceinline__ void fft_stage_r32(int t, const cpx<R>* __restrict__ 
         }
     }
     dft_small<DIR, 16>(v);
-    // Z_h[q] = w^{h (k + q NS)} Y_h[q] (the identity for h = 0)
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-        cpx<R> w = __ldg(&tw[h * (k + q * NS)]);
+    // Z_h[q] = w^{h (k + q NS)} Y_h[q] = w^{hk} e^{DIR 2 pi i h q / 32} Y_h[q] (NS = P/32;
+    // the identity for h = 0): one table load and compile-time constants
+    if (h) {
+        cpx<R> w = __ldg(&tw[k]);
         if (DIR > 0) w.y = -w.y;
-        v[q] = cmul(v[q], w);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = cmul(v[q], w);
     }
+    mul_w32_sel<DIR, 0>(v, h != 0);
     __syncthreads();                        // every input of the stage is read before any store
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
