@@ -206,15 +206,15 @@ __device__ __forceinline__ void fft_stage(int t, const cpx<R>* __restrict__ tw, 
         if constexpr (NS > 1) {
             const int k = j & (NS - 1);
             if constexpr (RAD == 16) {
-                // w^r = w^{4a} w^b (r = 4a + b) from two table loads, w and w^4:
-                // squares and products give w^2, w^3, w^8, w^12 (each twiddle
-                // within a few roundings of the table)
+                // w^r = w^{4a} w^b (r = 4a + b) from one table load: squares and
+                // products give w^2, w^3, w^4, w^8, w^12 (each twiddle within a few
+                // roundings of the table)
                 cpx<R> wb[4], wa[4];
                 wb[1] = __ldg(&tw[k * TWS]);
-                wa[1] = __ldg(&tw[k * (4 * TWS)]);
-                if (DIR > 0) { wb[1].y = -wb[1].y; wa[1].y = -wa[1].y; }
+                if (DIR > 0) wb[1].y = -wb[1].y;
                 wb[2] = csq(wb[1]);
                 wb[3] = cmul(wb[2], wb[1]);
+                wa[1] = csq(wb[2]);
                 wa[2] = csq(wa[1]);
                 wa[3] = cmul(wa[2], wa[1]);
 #pragma unroll
@@ -279,13 +279,13 @@ __device__ __forceinline__ void fft_stage_r32(int t, const cpx<R>* __restrict__ 
 #pragma unroll
         for (int m = 0; m < 16; ++m) v[m] = load(j + (2 * m + h) * NS);
     }
+    cpx<R> wk = __ldg(&tw[k]);              // w^k, the one table load of the stage
+    if (DIR > 0) wk.y = -wk.y;
     if constexpr (NS > 1) {
-        // w^{2km} = w^{2k(4a+b)} from two table loads (w^{2k}, w^{8k}), as in fft_stage
-        const int e = 2 * k;
+        // w^{2km} = w^{2k(4a+b)}: w^{2k} and w^{8k} by squaring w^k, then as in fft_stage
         cpx<R> wb[4], wa[4];
-        wb[1] = __ldg(&tw[e]);
-        wa[1] = __ldg(&tw[4 * e]);
-        if (DIR > 0) { wb[1].y = -wb[1].y; wa[1].y = -wa[1].y; }
+        wb[1] = csq(wk);
+        wa[1] = csq(csq(wb[1]));
         wb[2] = csq(wb[1]);
         wb[3] = cmul(wb[2], wb[1]);
         wa[2] = csq(wa[1]);
@@ -304,10 +304,8 @@ __device__ __forceinline__ void fft_stage_r32(int t, const cpx<R>* __restrict__ 
     // Z_h[q] = w^{h (k + q NS)} Y_h[q] = w^{hk} e^{DIR 2 pi i h q / 32} Y_h[q] (NS = P/32;
     // the identity for h = 0): one table load and compile-time constants
     if (h) {
-        cpx<R> w = __ldg(&tw[k]);
-        if (DIR > 0) w.y = -w.y;
 #pragma unroll
-        for (int q = 0; q < 16; ++q) v[q] = cmul(v[q], w);
+        for (int q = 0; q < 16; ++q) v[q] = cmul(v[q], wk);
     }
     mul_w32_sel<DIR, 0>(v, h != 0);
     __syncthreads();                        // every input of the stage is read before any store

@@ -197,6 +197,17 @@ __device__ __forceinline__ void col_body(const ColArgs<R>& a) {
     // the four blocks of a column group each bring a quarter of the group's
     // weight spectrum into L2 while the forward transform runs
     if (t == 0 && valid) l2_prefetch((const C*)a.Wh + ((size_t)g * P + (size_t)c * (P / Gc)) * Gc, (size_t)P * sizeof(C));
+    // look ahead: the column a block resident one wave later (MINB blocks on each
+    // of 152 SMs) will transform; its group's input rows come into L2 now, a
+    // quarter from each of the group's blocks
+    if (t == 0) {
+        const int kn = k1 + CF::MINB * 152;
+        if (kn <= P / 2 && a.rhi > a.rlo) {
+            const int gn = kn / Gc, cn = kn - gn * Gc, len = a.rhi - a.rlo;
+            const int r0 = a.rlo + (cn * len) / Gc, r1 = a.rlo + ((cn + 1) * len) / Gc;
+            l2_prefetch((const C*)a.S + ((size_t)gn * a.g.rows + r0) * Gc, (size_t)(r1 - r0) * Gc * sizeof(C));
+        }
+    }
     auto store_mul = [&](int k2, C v) {
         const C w = valid ? __ldg(&wh[(size_t)k2 * Gc]) : mk<R>(0, 0);
         buf[padi(k2)] = cmul(v, w);
