@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/pide2d.h"
+#include "common.cuh"
 #include "internal.h"
 
 using namespace pide;
@@ -91,8 +92,8 @@ void fill_layout(int N, Layout& L) {
     L.size[R_S] = (size_t)g.ng * g.rows * 16;
     L.size[R_WH] = L.size[R_WHI] = (size_t)g.ng * g.P * 16;
     L.size[R_E] = (size_t)g.nge * N * 16;
-    L.size[R_TWR] = (size_t)g.P * 2 * sizeof(R);
-    L.size[R_TWD] = (size_t)g.P * 16;
+    L.size[R_TWR] = (size_t)tw_entries(g.P) * 2 * sizeof(R);   // base table + stage tables
+    L.size[R_TWD] = (size_t)tw_entries(g.P) * 16;
     const size_t tl = (size_t)(2 * N + 7);
     L.size[R_E1D] = L.size[R_E2D] = tl * 8;
     L.size[R_E1F] = L.size[R_E2F] = tl * 4;
@@ -1740,8 +1741,8 @@ void price_layout(pide2d_price* H) {
     H->off_params = take(16 * 8);
     H->off_rows = take((size_t)(P / 2 + 1) * P * 16);
     H->off_wh = take((size_t)ng * P * 16);
-    H->off_twr = take((size_t)P * 2 * sizeof(R));
-    H->off_twd = take((size_t)P * 16);
+    H->off_twr = take((size_t)tw_entries(P) * 2 * sizeof(R));
+    H->off_twd = take((size_t)tw_entries(P) * 16);
     H->off_tin_s = take((size_t)H->nin * 4);
     H->off_tin_w = take((size_t)H->nin * 4 * 8);
     H->off_tout_t = take((size_t)H->nx1 * 4);

@@ -32,14 +32,50 @@ template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
     C c; c.x = a.x * b.x - a.y * b.y; c.y = a.x * b.y + a.y * b.x; return c;
 }
 template <typename C> __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
-template <typename C> __device__ __forceinline__ C csq(C a) {
-    C c; c.x = a.x * a.x - a.y * a.y; c.y = 2 * a.x * a.y; return c;
-}
+
 template <typename C, typename R> __device__ __forceinline__ C cscale(C a, R s) { a.x *= s; a.y *= s; return a; }
 
 // padded shared-memory index: one pad element per 16
 __device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int padded_len(int P) { return P + (P >> 4); }
+
+// Twiddle tables (complex, transform precision; w = e^{-2 pi i / P}):
+//   [0, P)  w^k;
+//   then per radix-16 stage with span NS = 16, 256, ... (16 NS <= P): NS rows of 8
+//     entries, row k = w^{k TWS m} for m = 1, 2, 3, 4, 8, 12 (TWS = P / (16 NS)), 2 unused;
+//   then, when P = 32 NS for a span NS = 16^j, the radix-32 stage: NS rows,
+//     row k = w^{2 k m} for m = 1, 2, 3, 4, 8, 12, then w^k, 1 unused.
+// Every entry is an FP64 value rounded once, so the fifteen twiddles w^{4a} w^b of a
+// butterfly are at most two roundings from exact, and a row is three or four 16-byte loads.
+__host__ __device__ constexpr int tw16_offset(int P, int NS) {
+    int off = P;
+    for (int s = 16; s < NS; s *= 16) off += 8 * s;
+    return off;
+}
+__host__ __device__ constexpr int tw32_offset(int P) {
+    int off = P;
+    for (int s = 16; 16 * s <= P; s *= 16) off += 8 * s;
+    return off;
+}
+__host__ __device__ constexpr bool tw_has_r32(int P) {
+    int s = 1;
+    while (32 * s < P) s *= 16;
+    return 32 * s == P;
+}
+__host__ __device__ constexpr int tw_entries(int P) { return tw32_offset(P) + (tw_has_r32(P) ? 8 * (P / 32) : 0); }
+
+// two adjacent table entries with one 16-byte load (two 16-byte loads in FP64)
+template <typename R>
+__device__ __forceinline__ void tw_pair(const cpx<R>* p, cpx<R>& a, cpx<R>& b) {
+    if constexpr (sizeof(R) == 4) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+        a = mk<R>(q.x, q.y);
+        b = mk<R>(q.z, q.w);
+    } else {
+        a = __ldg(p);
+        b = __ldg(p + 1);
+    }
+}
 
 // v * e^{DIR 2 pi i m / 16} for a compile-time m in [0, 16)
 template <int DIR, int M, typename C>
@@ -206,17 +242,18 @@ __device__ __forceinline__ void fft_stage(int t, const cpx<R>* __restrict__ tw, 
         if constexpr (NS > 1) {
             const int k = j & (NS - 1);
             if constexpr (RAD == 16) {
-                // w^r = w^{4a} w^b (r = 4a + b) from one table load: squares and
-                // products give w^2, w^3, w^4, w^8, w^12 (each twiddle within a few
-                // roundings of the table)
+                // w^r = w^{4a} w^b (r = 4a + b): the row of the stage's table holds
+                // w^b and w^{4a}; nine products form the rest
+                static_assert(TWS * NS * 16 == P, "radix-16 table row");
+                const cpx<R>* T = tw + tw16_offset(P, NS) + 8 * k;
                 cpx<R> wb[4], wa[4];
-                wb[1] = __ldg(&tw[k * TWS]);
-                if (DIR > 0) wb[1].y = -wb[1].y;
-                wb[2] = csq(wb[1]);
-                wb[3] = cmul(wb[2], wb[1]);
-                wa[1] = csq(wb[2]);
-                wa[2] = csq(wa[1]);
-                wa[3] = cmul(wa[2], wa[1]);
+                tw_pair<R>(T, wb[1], wb[2]);
+                tw_pair<R>(T + 2, wb[3], wa[1]);
+                tw_pair<R>(T + 4, wa[2], wa[3]);
+                if (DIR > 0) {
+#pragma unroll
+                    for (int q = 1; q < 4; ++q) { wb[q].y = -wb[q].y; wa[q].y = -wa[q].y; }
+                }
 #pragma unroll
                 for (int r = 1; r < 16; ++r) {
                     const int qa = r >> 2, qb = r & 3;
@@ -279,17 +316,21 @@ __device__ __forceinline__ void fft_stage_r32(int t, const cpx<R>* __restrict__ 
 #pragma unroll
         for (int m = 0; m < 16; ++m) v[m] = load(j + (2 * m + h) * NS);
     }
-    cpx<R> wk = __ldg(&tw[k]);              // w^k, the one table load of the stage
+    // the stage's table row k: w^{2km} for m = 1, 2, 3, 4, 8, 12, then w^k
+    const cpx<R>* T = tw + tw32_offset(P) + 8 * k;
+    cpx<R> wk, unused;
+    tw_pair<R>(T + 6, wk, unused);
     if (DIR > 0) wk.y = -wk.y;
     if constexpr (NS > 1) {
-        // w^{2km} = w^{2k(4a+b)}: w^{2k} and w^{8k} by squaring w^k, then as in fft_stage
+        // w^{2km} = w^{2k(4a+b)} as in fft_stage
         cpx<R> wb[4], wa[4];
-        wb[1] = csq(wk);
-        wa[1] = csq(csq(wb[1]));
-        wb[2] = csq(wb[1]);
-        wb[3] = cmul(wb[2], wb[1]);
-        wa[2] = csq(wa[1]);
-        wa[3] = cmul(wa[2], wa[1]);
+        tw_pair<R>(T, wb[1], wb[2]);
+        tw_pair<R>(T + 2, wb[3], wa[1]);
+        tw_pair<R>(T + 4, wa[2], wa[3]);
+        if (DIR > 0) {
+#pragma unroll
+            for (int q = 1; q < 4; ++q) { wb[q].y = -wb[q].y; wa[q].y = -wa[q].y; }
+        }
 #pragma unroll
         for (int m = 1; m < 16; ++m) {
             const int qa = m >> 2, qb = m & 3;
@@ -346,7 +387,7 @@ __device__ __forceinline__ void fft_from(cpx<R>* buf, int t, const cpx<R>* __res
 
 // Unscaled length-P complex DFT (DIR = -1: e^{-2 pi i jk/P}, DIR = +1: e^{+...})
 // with input x[j] = load(j) and output X[k] handed to store(k, X[k]);
-// tw[k] = e^{-2 pi i k/P}.  FUSE2 = false keeps a remainder of 2 as its own
+// tw is the twiddle table laid out as tw_entries(P) above.  FUSE2 = false keeps a remainder of 2 as its own
 // stage (for store functors heavy enough that the radix-32 stage spills).  Every thread of the block must call it (it
 // synchronises the block); inputs read from `buf` must have been written and
 // synchronised before the call.

@@ -229,11 +229,33 @@ __global__ void k_tables(int N, double s1, double s2, double h, double* E1d, dou
 
 template <typename R>
 __global__ void k_twiddles(int P, cpx<R>* tw) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= P) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= tw_entries(P)) return;
+    // exponent of w = e^{-2 pi i / P} held by entry i (layout in common.cuh)
+    long long e = i;
+    if (i >= P) {
+        const int m16[8] = {1, 2, 3, 4, 8, 12, 0, 0};
+        const int m32[8] = {2, 4, 6, 8, 16, 24, 1, 0};
+        int off = P;
+        bool r16 = false;
+        for (int sp = 16; 16 * sp <= P; sp *= 16) {
+            if (i < off + 8 * sp) {
+                const int k = (i - off) / 8, slot = (i - off) % 8;
+                e = (long long)k * (P / (16 * sp)) * m16[slot];
+                r16 = true;
+                break;
+            }
+            off += 8 * sp;
+        }
+        if (!r16) {
+            const int k = (i - off) / 8, slot = (i - off) % 8;
+            e = (long long)k * m32[slot];
+        }
+        e %= P;
+    }
     double s, c;
-    sincospi(2.0 * k / P, &s, &c);
-    tw[k] = mk<R>((R)c, (R)(-s));
+    sincospi(2.0 * (double)e / P, &s, &c);
+    tw[i] = mk<R>((R)c, (R)(-s));
 }
 
 // ---------------------------------------------------------------------------
@@ -342,7 +364,7 @@ cudaError_t launch_tables(int N, double s_lo1, double s_lo2, double h, double* E
 }
 template <typename R>
 cudaError_t launch_twiddles(int P, void* tw, cudaStream_t s) {
-    k_twiddles<R><<<(P + 255) / 256, 256, 0, s>>>(P, (cpx<R>*)tw);
+    k_twiddles<R><<<(tw_entries(P) + 255) / 256, 256, 0, s>>>(P, (cpx<R>*)tw);
     return cudaGetLastError();
 }
 template <typename R>

@@ -19,6 +19,7 @@
 #include <string>
 
 #include "../../include/pide2d.h"
+#include "common.cuh"
 #include "internal.h"
 
 namespace pide {
@@ -39,7 +40,7 @@ constexpr size_t kOffS = 0;                                                 // s
 constexpr size_t kOffWt = kOffS + al256((size_t)kH * (kP + 2) * 16);        // FP64 row spectra of Omega
 constexpr size_t kOffWh = kOffWt + al256((size_t)kH * kP * 16);             // conj(omega-hat) / P^2
 constexpr size_t kOffTw = kOffWh + al256((size_t)kH * kP * 16);             // twiddles
-constexpr size_t kOffX = kOffTw + al256((size_t)kP * 16);                   // U as FP64 state field
+constexpr size_t kOffX = kOffTw + al256((size_t)tw_entries(kP) * 16);      // U as FP64 state field
 constexpr size_t kOffOut = kOffX + al256((size_t)(kStaticMaxN + 1) * kLd * 8);
 constexpr size_t kStaticBytes = kOffOut + al256((size_t)(kStaticMaxN + 1) * kLd * 8);
 

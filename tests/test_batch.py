@@ -92,3 +92,25 @@ def test_batch_reports_iteration_cap_per_job():
         s.close()
         assert p == p1 and st1 == (4 if w.tol < 1e-20 else 0)
 
+
+
+@pytest.mark.gpu
+def test_batch_fp32_bulk_prices_within_1e5_of_fp64():
+    """The benchmark's batch workload (its first 16 draws: N in {128, 256, 512},
+    N/4 steps, tol 1e-8) in FP32-bulk through the batch path, against the same
+    jobs solved one by one in FP64 (itself at parity with the oracle to 1e-10):
+    every price within the FP32-bulk bound of 1e-5 relative."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_02700_gb300 import binding as B
+    ws = batch_draw(512)[:16]
+    prices, sts, _ = B.solve_batch([gpu_job(w) for w in ws], lanes=16)
+    assert all(s == 0 for s in sts), sts
+    errs = []
+    for w, p32 in zip(ws, prices):
+        s = gpu_solver(with_(w, precision="fp64"))
+        p64, _, st, _ = s.solve()
+        s.close()
+        errs.append(abs(p32 - p64) / abs(p64))
+    assert max(errs) <= 1e-5, [(w.name, e) for w, e in zip(ws, errs) if e > 1e-5]
