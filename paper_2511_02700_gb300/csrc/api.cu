@@ -80,7 +80,7 @@ void fill_layout(int N, Layout& L) {
     g.N = N;
     g.P = 2 * N;
     g.rows = g.P + 2;
-    g.ng = (g.P / 2 + 1 + cgroup<R>() - 1) / cgroup<R>();
+    g.ng = spectrum_groups<R>(g.P);
     g.nge = N / rgroup<R>();
     g.ldS = round_up(N + 1, 32);
     g.ldR = round_up(N + 1, 32);
@@ -89,9 +89,9 @@ void fill_layout(int N, Layout& L) {
     const size_t fieldR = (size_t)(N + 1) * g.ldR * sizeof(R);
     for (int i = R_V0; i <= R_OUT; ++i) L.size[i] = fieldS;
     L.size[R_RES] = L.size[R_DLT] = fieldR;
-    L.size[R_S] = (size_t)g.ng * g.rows * 16;
-    L.size[R_WH] = L.size[R_WHI] = (size_t)g.ng * g.P * 16;
-    L.size[R_E] = (size_t)g.nge * N * 16;
+    L.size[R_S] = (size_t)g.ng * g.rows * cgroup_bytes<R>();
+    L.size[R_WH] = L.size[R_WHI] = (size_t)g.ng * g.P * cgroup_bytes<R>();
+    L.size[R_E] = (size_t)g.nge * N * rgroup_bytes<R>();
     L.size[R_TWR] = (size_t)tw_entries(g.P) * 2 * sizeof(R);   // base table + stage tables
     L.size[R_TWD] = (size_t)tw_entries(g.P) * 16;
     const size_t tl = (size_t)(2 * N + 7);
@@ -257,7 +257,7 @@ TapeLayout tape_layout(const Layout& L, int n_steps, int interval, int ndirs) {
     t.spec1 = align256(L.size[R_WH]);
     t.omega = align256((size_t)N * N * 8);
     t.part = align256(L.size[R_PART]);
-    t.rows = align256((size_t)(L.g.P / 2 + 1) * L.g.P * 16);
+    t.rows = align256((size_t)spectrum_groups<double>(L.g.P) * L.g.P * cgroup_bytes<double>());
     t.nparts = align256((size_t)adjoint_dot_blocks(N) * 4 * 8);
     t.nckpt = (n_steps + interval - 1) / interval;
     t.seg_slots = interval + 3;                       // the damped first step has four theta steps
@@ -928,7 +928,7 @@ static pide2d_status weight_spectrum(pide2d* H, const double* omega, void* Wh, v
     const Geometry g = H->L.g;
     Geometry gd = g;
     gd.rows = g.P;
-    gd.ng = g.P / 2 + 1;
+    gd.ng = spectrum_groups<double>(g.P);
     FwdArgs<double> wa{};
     wa.g = gd;
     wa.mode = FWD_WEIGHTS;
@@ -1725,7 +1725,7 @@ PriceSizes price_sizes(const pide2d_price_grid* g) {
 template <typename R>
 void price_layout(pide2d_price* H) {
     const int P = H->P;
-    const int ng = (P / 2 + 1 + cgroup<R>() - 1) / cgroup<R>();
+    const int ng = spectrum_groups<R>(P);
     const int nzz = 2 * H->nz;
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -1739,8 +1739,8 @@ void price_layout(pide2d_price* H) {
     H->off_part = take((size_t)((nzz * nzz + 255) / 256) * 3 * 8);
     H->off_moment = take(4 * 8);
     H->off_params = take(16 * 8);
-    H->off_rows = take((size_t)(P / 2 + 1) * P * 16);
-    H->off_wh = take((size_t)ng * P * 16);
+    H->off_rows = take((size_t)spectrum_groups<double>(P) * P * cgroup_bytes<double>());
+    H->off_wh = take((size_t)ng * P * cgroup_bytes<R>());
     H->off_twr = take((size_t)tw_entries(P) * 2 * sizeof(R));
     H->off_twd = take((size_t)tw_entries(P) * 16);
     H->off_tin_s = take((size_t)H->nin * 4);
@@ -1748,7 +1748,7 @@ void price_layout(pide2d_price* H) {
     H->off_tout_t = take((size_t)H->nx1 * 4);
     H->off_tout_u = take((size_t)H->nx1 * 4 * 8);
     H->off_A = take((size_t)P * P * sizeof(R));
-    H->off_S = take((size_t)ng * P * 16);
+    H->off_S = take((size_t)ng * P * cgroup_bytes<R>());
     H->off_By = take((size_t)H->nout * H->nout * 8);
     H->off_loop = o;                // the time-loop fields follow (ps_loop_bytes)
     H->total = o;
@@ -1822,7 +1822,7 @@ static pide2d_status price_create(pide2d_price* H, const pide2d_price_grid* g) {
     gd.N = P / 2;
     gd.P = P;
     gd.rows = P;
-    gd.ng = P / 2 + 1;
+    gd.ng = spectrum_groups<double>(P);
     FwdArgs<double> wa{};
     wa.g = gd;
     wa.mode = FWD_WEIGHTS;

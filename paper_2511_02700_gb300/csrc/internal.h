@@ -19,6 +19,11 @@ template <typename R> using St = typename state_t<R>::type;
 template <typename R> __host__ __device__ constexpr int cgroup() { return 16 / (2 * (int)sizeof(R)); }
 // DST column groups: 16 bytes of real values per (group, row)
 template <typename R> __host__ __device__ constexpr int rgroup() { return 16 / (int)sizeof(R); }
+// bytes of one (group, row) entry of the spectrum and of the DST buffer
+template <typename R> constexpr size_t cgroup_bytes() { return (size_t)cgroup<R>() * 2 * sizeof(R); }
+template <typename R> constexpr size_t rgroup_bytes() { return (size_t)rgroup<R>() * sizeof(R); }
+// spectrum column groups of a length-P transform (P/2 + 1 columns)
+template <typename R> constexpr int spectrum_groups(int P) { return (P / 2 + 1 + cgroup<R>() - 1) / cgroup<R>(); }
 
 enum FwdMode { FWD_FULL = 0, FWD_FULL0 = 1, FWD_INCR = 2, FWD_WEIGHTS = 3 };
 enum ColMode { COL_FULL = 0, COL_INCR = 1 };

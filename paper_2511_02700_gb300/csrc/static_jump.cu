@@ -36,10 +36,12 @@ constexpr int kP = 2 * kStaticMaxN;
 constexpr int kH = kP / 2 + 1;
 constexpr int kLd = (kStaticMaxN + 1 + 31) / 32 * 32;
 // byte offsets of the scratch regions at the maximum size (smaller grids use a prefix of each)
-constexpr size_t kOffS = 0;                                                 // spectrum, (P/2+1) x (P+2) x 16 B
-constexpr size_t kOffWt = kOffS + al256((size_t)kH * (kP + 2) * 16);        // FP64 row spectra of Omega
-constexpr size_t kOffWh = kOffWt + al256((size_t)kH * kP * 16);             // conj(omega-hat) / P^2
-constexpr size_t kOffTw = kOffWh + al256((size_t)kH * kP * 16);             // twiddles
+constexpr size_t kOffS = 0;                                                 // spectrum, column groups x (P+2) rows
+constexpr size_t kNg = (size_t)spectrum_groups<double>(kP);
+constexpr size_t kGb = cgroup_bytes<double>();
+constexpr size_t kOffWt = kOffS + al256(kNg * (kP + 2) * kGb);              // FP64 row spectra of Omega
+constexpr size_t kOffWh = kOffWt + al256(kNg * kP * kGb);                   // conj(omega-hat) / P^2
+constexpr size_t kOffTw = kOffWh + al256(kNg * kP * kGb);                   // twiddles
 constexpr size_t kOffX = kOffTw + al256((size_t)tw_entries(kP) * 16);      // U as FP64 state field
 constexpr size_t kOffOut = kOffX + al256((size_t)(kStaticMaxN + 1) * kLd * 8);
 constexpr size_t kStaticBytes = kOffOut + al256((size_t)(kStaticMaxN + 1) * kLd * 8);
@@ -105,7 +107,7 @@ extern "C" pide2d_status pide2d_jump_static(int n, const double* omega, const do
     g.N = n;
     g.P = 2 * n;
     g.rows = g.P + 2;
-    g.ng = g.P / 2 + 1;                  // FP64: one complex column per 16-byte group
+    g.ng = spectrum_groups<double>(g.P);
     g.nge = n / rgroup<double>();
     g.ldS = (n + 1 + 31) / 32 * 32;
     g.ldR = g.ldS;

@@ -898,9 +898,11 @@ PIDE_FFT_KERNEL(double, P) k_weights_col(Geometry g, const double2* Sd, cpx<RO>*
     double2* buf = reinterpret_cast<double2*>(smem_raw) + (size_t)unit * CF::ULEN;
     const int k1 = blockIdx.x * CF::UNITS + unit;
     const bool valid = k1 <= P / 2;
+    constexpr int Gd = cgroup<double>();
+    const int gd = k1 / Gd, cd = k1 - gd * Gd;
     auto load = [&](int i) -> double2 {
         // rows >= N of the zero-padded Omega are zero
-        return (valid && i < N) ? Sd[(size_t)k1 * P + i] : mk<double>(0, 0);
+        return (valid && i < N) ? Sd[((size_t)gd * P + i) * Gd + cd] : mk<double>(0, 0);
     };
     constexpr int Go = cgroup<RO>();
     const int go = k1 / Go, co = k1 - go * Go;
@@ -1114,7 +1116,7 @@ cudaError_t launch_ps_tin(int P, int nin, int nx1, const int* s, const double* w
 }
 template <typename R>
 cudaError_t launch_ps_rows_fwd(int P, const R* A, int nin, void* S, const void* tw, cudaStream_t st) {
-    const int rows = P, ng = (P / 2 + 1 + cgroup<R>() - 1) / cgroup<R>();
+    const int rows = P, ng = spectrum_groups<R>(P);
 #define CASE(PP)                                                                                     \
     if constexpr (LoopSize<R, PP>::ok) {                                                             \
         using CF = Cfg<R, PP>;                                                                       \
