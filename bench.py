@@ -138,7 +138,7 @@ def algorithmic_bytes(cls, n, hcount=4):
         3: spec_full + wh + spec_n,                            # column pass full
         4: spec_n + wh + spec_n,                               # column pass incr
         5: spec_n + 8 * cells + 16 * cells + 4 * cells + 4 * cells,   # inverse full: S, BY, W+Y, r, E
-        6: spec_n + 16 * cells + 8 * cells + 4 * cells + 4 * cells,   # inverse incr: S, BY, r, D, E
+        6: spec_n + 16 * cells + 4 * cells + 4 * cells + 4 * cells,   # inverse incr: S, BY, r (write), D, E
         7: 8 * cells,                                          # column DST
         8: 4 * cells + 16 * cells + 4 * cells + spec_n,        # row DST back (E, Y, D) + increment R2C rows
     }[cls]

@@ -65,13 +65,17 @@ __device__ __forceinline__ R diff_state(const S* Y, size_t idx, int ld, R d11, R
     const R dxy = st_diff(Y[idx + ld + 1], Y[idx - ld + 1]) - st_diff(Y[idx + ld - 1], Y[idx - ld - 1]);
     return d11 * dxx + d22 * dyy + d12 * dxy;
 }
+// The increment D of a fixed-point iteration solves M D = r(Y) exactly, M being
+// (1 + h_t theta r_w) I minus h_t theta times the non-mixed part of D, which the
+// DST-I inverts (eq. 3.24 with the mixed term lagged).  The residual of Y + D is
+// then r(Y) + h_t theta B D - (M D - h_t theta a12 delta_12 D)
+//     = h_t theta (B D + a12 delta_12 D):
+// the B D of this sweep and the mixed difference of D, with no cancellation
+// between r(Y) and M D.  (The residual is formed from the full operator at the
+// start of every step, so rounding in the DST does not accumulate across steps.)
 template <typename R>
-__device__ __forceinline__ R diff_plain(const R* D, size_t idx, int ld, R d11, R d22, R d12) {
-    const R c = D[idx];
-    const R dxx = D[idx + 1] + D[idx - 1] - R(2) * c;
-    const R dyy = D[idx + ld] + D[idx - ld] - R(2) * c;
-    const R dxy = (D[idx + ld + 1] - D[idx - ld + 1]) - (D[idx + ld - 1] - D[idx - ld - 1]);
-    return d11 * dxx + d22 * dyy + d12 * dxy;
+__device__ __forceinline__ R mixed_plain(const R* D, size_t idx, int ld) {
+    return (D[idx + ld + 1] - D[idx - ld + 1]) - (D[idx + ld - 1] - D[idx - ld - 1]);
 }
 
 template <typename R> struct ResidAtomic;
@@ -259,10 +263,7 @@ __device__ __forceinline__ void prefetch_inverse_rows(const InvArgs<R>& a, const
     const int lo = m2 - 1, hi = m2 + 2 < N ? m2 + 2 : N;     // stencil rows, inside the N + 1 rows
     if (a.mode == INV_INCR) {
         l2_prefetch(BYv + (size_t)m2 * ld, (size_t)nr * ld * sizeof(S_));
-        if (do_resid) {
-            l2_prefetch(a.r + (size_t)m2 * ldR, (size_t)nr * ldR * sizeof(R));
-            l2_prefetch(a.D + (size_t)lo * ldR, (size_t)(hi - lo + 1) * ldR * sizeof(R));
-        }
+        if (do_resid) l2_prefetch(a.D + (size_t)lo * ldR, (size_t)(hi - lo + 1) * ldR * sizeof(R));
     } else if (a.mode == INV_FULL && do_resid) {
         l2_prefetch(a.W + (size_t)m2 * ld, (size_t)nr * ld * sizeof(S_));
         l2_prefetch(a.Y + (size_t)lo * ld, (size_t)(hi - lo + 1) * ld * sizeof(S_));
@@ -333,11 +334,7 @@ __device__ __forceinline__ void row_inverse_body(const InvArgs<R>& a) {
                     }
                 } else {  // INV_INCR
                     BYv[idx] = st_add(BYv[idx], zv);
-                    if (do_resid) {
-                        const R d = a.D[idr];
-                        rr[half] = a.r[idr] + a.htt * zv
-                                   - (a.cid * d - a.htt * diff_plain(a.D, idr, ldR, a.d11, a.d22, a.d12));
-                    }
+                    if (do_resid) rr[half] = a.htt * (zv + a.d12 * mixed_plain(a.D, idr, ldR));
                 }
                 if (do_resid) a.r[idr] = rr[half];
             }
@@ -360,98 +357,15 @@ __device__ __forceinline__ void row_inverse_body(const InvArgs<R>& a) {
     };
     block_fft<R, -1, P>(buf, t, tw, SmemLoad<R>{buf}, store_e);
 }
+// The single-job kernel reads its arguments from a shared-memory copy: inlined
+// from the parameter block itself, this FFT kernel needed several times the
+// spill traffic (register allocation differs with the arguments' address space).
 template <typename R, int P>
-// the single-job kernel keeps its own copy of the body: inlined from a
-// reference to the parameter block, this FFT kernel spilled three times more
-PIDE_FFT_KERNEL(R, P) k_row_inverse(InvArgs<R> a) {
-    using C = cpx<R>;
-    using S_ = St<R>;
-    using CF = Cfg<R, P>;
-    constexpr int NT = CF::NT, N = P / 2;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int unit = threadIdx.x / NT, t = threadIdx.x - unit * NT;
-    C* buf = reinterpret_cast<C*>(smem_raw) + (size_t)unit * CF::ULEN;
-    const int p = blockIdx.x * CF::UNITS + unit;
-    const int m2 = 2 * p + 1;
-    const bool valid = m2 <= N - 1;
-    const bool hasb = valid && (m2 + 1 <= N - 1);
-    constexpr int Gc = cgroup<R>();
-    const C* S = (const C*)a.S;
-    const int rows = a.g.rows;
-    const C* tw = (const C*)a.tw;
-    // the device-side fixed-point loop decides on the device whether a residual is needed
-    const bool do_resid = a.conv_flag ? (*a.conv_flag == 0) : (a.do_resid != 0);
-    auto load = [&](int pos) -> C {
-        const bool hi = pos > P / 2;
-        const int k = hi ? P - pos : pos;
-        C xa = mk<R>(0, 0), xb = mk<R>(0, 0);
-        if (valid) {
-            const int g = k / Gc, c = k - g * Gc;
-            xa = S[((size_t)g * rows + (m2 - 1)) * Gc + c];
-            xb = S[((size_t)g * rows + m2) * Gc + c];
-        }
-        if (k == 0 || k == P / 2) { xa.y = 0; xb.y = 0; }
-        if (hi) { xa.y = -xa.y; xb.y = -xb.y; }
-        return mk<R>(xa.x - xb.y, xa.y + xb.x);
-    };
-    const int ld = a.g.ldS, ldR = a.g.ldR;
-    S_* const BYv = a.BYind ? *a.BYind : a.BY;
-    if (t == 0 && valid) prefetch_inverse_rows(a, BYv, m2, hasb, do_resid);
-    auto epilogue = [&](int m1, C zz) {
-        if (m1 == 0) {
-            if (do_resid) {
-                buf[padi(0)] = mk<R>(0, 0);
-                buf[padi(N)] = mk<R>(0, 0);
-            }
-            return;
-        }
-        if (m1 >= N) return;
-        R rr[2] = {R(0), R(0)};
-        if (valid) {
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                if (half == 1 && !hasb) break;
-                const int row = m2 + half;
-                const R zv = half == 0 ? zz.x : zz.y;
-                const size_t idx = (size_t)row * ld + m1;
-                const size_t idr = (size_t)row * ldR + m1;
-                if (a.mode == INV_OUT) {
-                    a.out[idx] = (double)zv;
-                } else if (a.mode == INV_FULL) {
-                    BYv[idx] = st_from_r<S_, R>(zv);
-                    if (do_resid) {
-                        const S_ y = a.Y[idx];
-                        rr[half] = st_diff(a.W[idx], y) + a.htt * zv - a.htt * a.rw * st_r(y)
-                                   + a.htt * diff_state(a.Y, idx, ld, a.d11, a.d22, a.d12);
-                    }
-                } else {  // INV_INCR
-                    BYv[idx] = st_add(BYv[idx], zv);
-                    if (do_resid) {
-                        const R d = a.D[idr];
-                        rr[half] = a.r[idr] + a.htt * zv
-                                   - (a.cid * d - a.htt * diff_plain(a.D, idr, ldR, a.d11, a.d22, a.d12));
-                    }
-                }
-                if (do_resid) a.r[idr] = rr[half];
-            }
-        }
-        if (do_resid) {
-            buf[padi(m1)] = mk<R>(rr[0], rr[1]);
-            buf[padi(P - m1)] = mk<R>(-rr[0], -rr[1]);
-        }
-    };
-    block_fft<R, +1, P, false>(buf, t, tw, load, epilogue);
-    if (!do_resid) return;   // uniform across the block
-    constexpr int GE = rgroup<R>();
-    auto store_e = [&](int k, C zz) {
-        if (k >= N) return;
-        const int gE = k / GE, c = k - gE * GE;
-        const R va = k >= 1 ? R(-0.5) * zz.y : R(0);
-        const R vb = k >= 1 ? R(0.5) * zz.x : R(0);
-        if (valid) a.E[((size_t)gE * N + m2) * GE + c] = va;
-        if (hasb) a.E[((size_t)gE * N + m2 + 1) * GE + c] = vb;
-    };
-    block_fft<R, -1, P>(buf, t, tw, SmemLoad<R>{buf}, store_e);
+PIDE_FFT_KERNEL(R, P) k_row_inverse(const __grid_constant__ InvArgs<R> a0) {
+    __shared__ InvArgs<R> sa;
+    if (threadIdx.x == 0) sa = a0;
+    __syncthreads();
+    row_inverse_body<R, P>(sa);
 }
 template <typename R, int P>
 PIDE_FFT_KERNEL(R, P) k_row_inverse_jobs(const InvArgs<R>* __restrict__ arr, JobsCtl jc) {
