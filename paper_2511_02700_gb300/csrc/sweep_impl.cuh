@@ -289,22 +289,31 @@ __device__ __forceinline__ void row_inverse_body(const InvArgs<R>& a) {
     const C* tw = (const C*)a.tw;
     // the device-side fixed-point loop decides on the device whether a residual is needed
     const bool do_resid = a.conv_flag ? (*a.conv_flag == 0) : (a.do_resid != 0);
-    auto load = [&](int pos) -> C {
-        const bool hi = pos > P / 2;
-        const int k = hi ? P - pos : pos;
+    const int ld = a.g.ldS, ldR = a.g.ldR;
+    S_* const BYv = a.BYind ? *a.BYind : a.BY;
+    if (t == 0 && valid) prefetch_inverse_rows(a, BYv, m2, hasb, do_resid);
+    // the two spectrum rows, each value read once (the Hermitian extension uses
+    // every k twice): k at plain indices 2k, 2k + 1 of buf, which the first stage
+    // reads completely before it writes
+    for (int k = t; k <= P / 2; k += NT) {
         C xa = mk<R>(0, 0), xb = mk<R>(0, 0);
         if (valid) {
             const int g = k / Gc, c = k - g * Gc;
             xa = S[((size_t)g * rows + (m2 - 1)) * Gc + c];
             xb = S[((size_t)g * rows + m2) * Gc + c];
         }
+        buf[2 * k] = xa;
+        buf[2 * k + 1] = xb;
+    }
+    __syncthreads();
+    auto load = [&](int pos) -> C {
+        const bool hi = pos > P / 2;
+        const int k = hi ? P - pos : pos;
+        C xa = buf[2 * k], xb = buf[2 * k + 1];
         if (k == 0 || k == P / 2) { xa.y = 0; xb.y = 0; }
         if (hi) { xa.y = -xa.y; xb.y = -xb.y; }
         return mk<R>(xa.x - xb.y, xa.y + xb.x);
     };
-    const int ld = a.g.ldS, ldR = a.g.ldR;
-    S_* const BYv = a.BYind ? *a.BYind : a.BY;
-    if (t == 0 && valid) prefetch_inverse_rows(a, BYv, m2, hasb, do_resid);
     auto epilogue = [&](int m1, C zz) {
         if (m1 == 0) {
             if (do_resid) {
@@ -453,16 +462,22 @@ __device__ __forceinline__ void dst_row_body(const DstRowArgs<R>& a) {
     const bool hasb = valid && (m2 + 1 <= N - 1);
     constexpr int GE = rgroup<R>();
     const C* tw = (const C*)a.tw;
-    auto load = [&](int i) -> C {
-        const int j = i <= N ? i : P - i;
-        const R sg = i <= N ? R(1) : R(-1);
+    // the two DST rows, each value read once (the odd extension uses every j
+    // twice), at plain indices of buf, which the first stage reads before it writes
+    for (int j = t; j <= N; j += NT) {
         R ea = 0, eb = 0;
         if (valid && j >= 1 && j <= N - 1) {
             const int gE = j / GE, c = j - gE * GE;
-            ea = sg * a.E[((size_t)gE * N + m2) * GE + c];
-            if (hasb) eb = sg * a.E[((size_t)gE * N + m2 + 1) * GE + c];
+            ea = a.E[((size_t)gE * N + m2) * GE + c];
+            if (hasb) eb = a.E[((size_t)gE * N + m2 + 1) * GE + c];
         }
-        return mk<R>(ea, eb);
+        buf[j] = mk<R>(ea, eb);
+    }
+    __syncthreads();
+    auto load = [&](int i) -> C {
+        const int j = i <= N ? i : P - i;
+        const C e = buf[j];
+        return i <= N ? e : mk<R>(-e.x, -e.y);
     };
     St<R>* const Yv = a.Yind ? *a.Yind : a.Y;
     R rmax = 0;
