@@ -231,6 +231,21 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def aggregate_over_ranks(ms, units, device=None):
+    """Whole-job time and work over the ranks of the default process group:
+    the slowest rank's milliseconds (MAX) and the units of all ranks (SUM).
+    Without a process group (one GPU) the rank's own values."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms), float(units)
+    tt = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    uu = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    dist.all_reduce(uu, op=dist.ReduceOp.SUM)
+    return float(tt.item()), float(uu.item())
+
+
 # --------------------------------------------------------------------------- our arm
 def run_ours(a):
     import torch
@@ -303,15 +318,7 @@ def run_ours(a):
     launches = [kt.launches[i] for i in range(9)]
     kms = [kt.ms[i] for i in range(9)]
     # aggregate over ranks
-    t_max = ms
-    units_all = units
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        uu = torch.tensor([float(units)], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dist.all_reduce(uu, op=dist.ReduceOp.SUM)
-        t_max, units_all = float(tt.item()), float(uu.item())
+    t_max, units_all = aggregate_over_ranks(ms, units, dev)
     value = units_all / (t_max / 1e3)
     # roofline of the dominant kernel class
     top = max(range(9), key=lambda i: kms[i])
