@@ -102,7 +102,7 @@ void fill_layout(int N, Layout& L) {
     L.size[R_OMEGA] = (size_t)N * N * 8;
     L.size[R_PART] = (size_t)((N * N + 255) / 256) * 3 * 8;
     L.size[R_PARAMS] = 16 * 8;
-    L.size[R_MOMENT] = 4 * 8;
+    L.size[R_MOMENT] = moment_doubles() * 8;
     L.size[R_GL] = (size_t)kGlTotal * 8;
     L.size[R_RESID] = 16;
     L.size[R_CTL] = sizeof(FpCtl);
@@ -243,6 +243,7 @@ cudaError_t prof_event(pide2d* H, cudaEvent_t* e) {
 namespace {
 enum AdjField { A_LAM, A_MU, A_BMU, A_NU, A_XI, A_PEND, A_COUNT };
 constexpr int kAdjAcc = 6;        // <xi,V>, <xi,dxx V>, <xi,dxy V>, <xi,dyy V>, shift 1, shift 2
+constexpr size_t kMomentBytes = (moment_doubles() * 8 + 255) / 256 * 256;   // moment buffer, 256-aligned
 
 struct TapeLayout {
     size_t ckpt, seg, fin, adj, spec, scr, acc, total;
@@ -267,7 +268,7 @@ TapeLayout tape_layout(const Layout& L, int n_steps, int interval, int ndirs) {
     t.fin = o;   o += 5 * t.field;                    // the final state, put back after the adjoint
     t.adj = o;   o += (size_t)A_COUNT * t.field;
     t.spec = o;  o += (size_t)(2 + ndirs) * t.spec1;  // flipped Wh, Whi; one Wh per direction
-    t.scr = o;   o += 3 * t.omega + t.part + 256 + 2 * 256 + t.rows + t.nparts;
+    t.scr = o;   o += 3 * t.omega + t.part + kMomentBytes + 2 * 256 + t.rows + t.nparts;
     t.acc = o;   o += align256((size_t)(kAdjAcc + ndirs) * 8);
     t.total = o;
     return t;
@@ -1414,7 +1415,7 @@ template <typename R>
 static pide2d_status state_dots(pide2d* H, const TapeLayout& t, const St<R>* V, double tau, int ndirs) {
     const Geometry g = H->L.g;
     char* scr = H->tape.base + t.scr;
-    double* part = reinterpret_cast<double*>(scr + 3 * t.omega + t.part + 3 * 256 + t.rows);
+    double* part = reinterpret_cast<double*>(scr + 3 * t.omega + t.part + kMomentBytes + 2 * 256 + t.rows);
     double* acc = reinterpret_cast<double*>(H->tape.base + t.acc);
     const double* xi = reinterpret_cast<const double*>(H->tape.base + t.adj + A_XI * t.field);
     PIDE_CUDA(launch_dots_state<R>(g, xi, V, part, acc, 1.0, H->stream));
@@ -1443,10 +1444,10 @@ static pide2d_status do_adjoint(pide2d* H, const pide2d_model* dirs, int ndirs, 
     double* om_d = reinterpret_cast<double*>(scr + 2 * t.omega);
     double* part = reinterpret_cast<double*>(scr + 3 * t.omega);
     double* moment = reinterpret_cast<double*>(scr + 3 * t.omega + t.part);
-    double* par_p = reinterpret_cast<double*>(scr + 3 * t.omega + t.part + 256);
-    double* par_m = reinterpret_cast<double*>(scr + 3 * t.omega + t.part + 512);
-    void* rows = scr + 3 * t.omega + t.part + 768;
-    double* dpart = reinterpret_cast<double*>(scr + 3 * t.omega + t.part + 768 + t.rows);
+    double* par_p = reinterpret_cast<double*>(scr + 3 * t.omega + t.part + kMomentBytes);
+    double* par_m = reinterpret_cast<double*>(scr + 3 * t.omega + t.part + kMomentBytes + 256);
+    void* rows = scr + 3 * t.omega + t.part + kMomentBytes + 512;
+    double* dpart = reinterpret_cast<double*>(scr + 3 * t.omega + t.part + kMomentBytes + 512 + t.rows);
     double* acc = reinterpret_cast<double*>(tb + t.acc);
     auto afield = [&](int i) { return tb + t.adj + (size_t)i * t.field; };
     St<R>* lam = reinterpret_cast<St<R>*>(afield(A_LAM));
@@ -1737,7 +1738,7 @@ void price_layout(pide2d_price* H) {
     H->off_omega = take((size_t)nzz * nzz * 8);
     H->off_pad = take((size_t)(P / 2) * (P / 2) * 8);
     H->off_part = take((size_t)((nzz * nzz + 255) / 256) * 3 * 8);
-    H->off_moment = take(4 * 8);
+    H->off_moment = take(moment_doubles() * 8);
     H->off_params = take(16 * 8);
     H->off_rows = take((size_t)spectrum_groups<double>(P) * P * cgroup_bytes<double>());
     H->off_wh = take((size_t)ng * P * cgroup_bytes<R>());

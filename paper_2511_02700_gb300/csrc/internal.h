@@ -287,6 +287,10 @@ struct WeightJob {
 };
 cudaError_t launch_weights(const LevyParams& L, const WeightJob& j, double* omega, double* partials,
                            int* nblocks, cudaStream_t s);
+// the R_I moment (eq. 3.3): blocks of the quadrature and the doubles of its buffer
+// (three moments, one spare, then the blocks' partial sums)
+constexpr int kMomentBlocks = 64;
+constexpr size_t moment_doubles() { return 4 + 3 * (size_t)kMomentBlocks; }
 cudaError_t launch_moment(const LevyParams& L, double H, const double* glx, const double* glw, int ngl,
                           double tsh, double* out3, cudaStream_t s);
 cudaError_t launch_finalize(const double* partials, int nblocks, const double* moment, double r,

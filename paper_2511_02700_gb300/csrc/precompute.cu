@@ -116,14 +116,16 @@ __global__ void k_weights(LevyParams L, WeightJob j, double* omega, double* part
 // ---------------------------------------------------------------------------
 // eq. 3.3 moment over R_I = [-H, H]^2 (one block)
 // ---------------------------------------------------------------------------
+// kMomentBlocks blocks each sum a strided share of the nodes into part[3 b ..];
+// k_moment_sum adds the partial sums in block order (deterministic)
 __global__ void k_moment(LevyParams L, double H, const double* glx, const double* glw, int ngl, double tsh,
-                         double* out3) {
+                         double* part) {
     const double pi = 3.141592653589793;
     const int kmax = (int)(6.5 / tsh);
     const int nts = 2 * kmax + 1;
     const int total = 4 * ngl * nts;
     double m11 = 0.0, m12 = 0.0, m22 = 0.0;
-    for (int it = threadIdx.x; it < total; it += blockDim.x) {
+    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
         const int e = it / (ngl * nts);
         const int rem = it - e * ngl * nts;
         const int ti = rem / nts;
@@ -165,9 +167,16 @@ __global__ void k_moment(LevyParams L, double H, const double* glx, const double
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        out3[0] = a[0];
-        out3[1] = b[0];
-        out3[2] = c[0];
+        part[3 * blockIdx.x + 0] = a[0];
+        part[3 * blockIdx.x + 1] = b[0];
+        part[3 * blockIdx.x + 2] = c[0];
+    }
+}
+__global__ void k_moment_sum(const double* part, int nb, double* out3) {
+    if (threadIdx.x < 3) {
+        double acc = 0.0;
+        for (int b = 0; b < nb; ++b) acc += part[3 * b + threadIdx.x];
+        out3[threadIdx.x] = acc;
     }
 }
 
@@ -348,7 +357,12 @@ cudaError_t launch_weights(const LevyParams& L, const WeightJob& j, double* omeg
 }
 cudaError_t launch_moment(const LevyParams& L, double H, const double* glx, const double* glw, int ngl, double tsh,
                           double* out3, cudaStream_t s) {
-    k_moment<<<1, 256, 0, s>>>(L, H, glx, glw, ngl, tsh, out3);
+    // out3 holds the three moments, then kMomentBlocks x 3 partial sums (moment_doubles())
+    double* part = out3 + 4;
+    k_moment<<<kMomentBlocks, 256, 0, s>>>(L, H, glx, glw, ngl, tsh, part);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_moment_sum<<<1, 32, 0, s>>>(part, kMomentBlocks, out3);
     return cudaGetLastError();
 }
 cudaError_t launch_finalize(const double* partials, int nblocks, const double* moment, double r,
