@@ -49,6 +49,8 @@ def args_parse():
     p.add_argument("--no-batch", action="store_true", help="skip the 512-pricing batch measurement")
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
     p.add_argument("--no-sweep", action="store_true", help="skip the FP32-bulk vs FP64 convergence sweep")
+    p.add_argument("--no-paper", action="store_true",
+                   help="skip the paper's own set-ups (price-space scheme, VG0 on the wide log domain)")
     p.add_argument("--host-loop", action="store_true",
                    help="drive the fixed-point loop from the host in the timed region too (one launch per "
                         "kernel, as the profilers see it)")
@@ -354,6 +356,7 @@ def run_ours(a):
     batch = None if (a.no_batch or ws > 1) else run_batch(B, torch, dev)
     adjoint = None if (a.no_adjoint or ws > 1) else run_adjoint(B, torch, dev)
     sweep = None if (a.no_sweep or ws > 1) else run_sweep(B, torch, dev)
+    paper = None if (a.no_paper or ws > 1) else run_paper_schemes(B, torch, dev)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": t_max / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -363,7 +366,7 @@ def run_ours(a):
                        "l2": "working set > L2 (inputs larger than the 129 MB L2, no flush)"},
             "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": gpu_launches,
             "clocks": ck, "fp_iters_per_step": iters, "create_s": create_s, "kernels": kernels,
-            "batch": batch, "adjoint": adjoint, "convergence_sweep": sweep,
+            "batch": batch, "adjoint": adjoint, "convergence_sweep": sweep, "paper_schemes": paper,
             "loop": "host-driven fixed-point loop" if a.host_loop else
                     "device-side fixed-point loop (CUDA graph while-node), one host sync per time step"}
     print(json.dumps(line), flush=True)
@@ -479,6 +482,70 @@ def run_adjoint(B, torch, dev):
                 "fp32_bulk_forward_with_checkpoints_s": t_fwd32, "fp32_bulk_adjoint_s": t_adj32,
                 "fp32_bulk_grad_max_abs_err_over_max_grad": max(abs(a_ - b_) for a_, b_ in zip(g32, grad)) / scale})
     return out
+
+
+def _bilinear_at(x, V, p1, p2):
+    """V[m2, m1] on the grid x (both axes) at (p1, p2), linear in each axis."""
+    import numpy as np
+    def w(p):
+        i = int(np.searchsorted(x, p, side="right")) - 1
+        i = min(max(i, 0), len(x) - 2)
+        t = (p - x[i]) / (x[i + 1] - x[i])
+        return i, t
+    i1, t1 = w(p1)
+    i2, t2 = w(p2)
+    return float((1 - t2) * ((1 - t1) * V[i2, i1] + t1 * V[i2, i1 + 1])
+                 + t2 * ((1 - t1) * V[i2 + 1, i1] + t1 * V[i2 + 1, i1 + 1]))
+
+
+def run_paper_schemes(B, torch, dev):
+    """The paper's own Sec. 4 set-ups through the CUDA path, each timed end to
+    end (handle creation with the device precompute, all time steps, values
+    back): Algorithm 1 in price space on the sinh grid (FP64 where the
+    transform fits, N_t = N_x / 2, tol 1e-7; VG1 and NIG1), and VG0 on the wide log domain (half-width 11.5,
+    FP32-bulk, 2048^2, N/2 steps, tol 1e-8).  Each reports the price at (K, K)
+    beside the paper's Table 4 value (N_x = 800)."""
+    from paper_2511_02700_gb300.workloads import PAPER_SETS
+    res = {"price_space": []}
+    for name in ("VG1", "NIG1"):
+        ps = PAPER_SETS[name]
+        model = B.make_model(ps.alpha, ps.delta, ps.lam, ps.eta, ps.rho, ps.r)
+        for nx in (160, 320):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            x, n_z, h_z, nym, nyp = B.price_sinh_grid(nx, ps.strike, ps.x_max_over_k * ps.strike, ps.z_max_iii)
+            # FP64 transforms go up to length 4096; longer ones (NIG1 at N_x = 320) run in FP32-bulk
+            prec = "fp64"
+            try:
+                pj = B.PriceJump(x, n_z, h_z, nym, nyp, model, precision=B.PIDE2D_FP64, device=dev)
+            except B.PideError:
+                prec = "fp32-bulk"
+                pj = B.PriceJump(x, n_z, h_z, nym, nyp, model, precision=B.PIDE2D_FP32_BULK, device=dev)
+            V, st, status = pj.solve(B.make_contract(B.PIDE2D_PUT_AVG, ps.strike, ps.maturity), nx // 2, tol=1e-7)
+            V = V.cpu().numpy()
+            wall = time.perf_counter() - t0
+            pj.close()
+            price = _bilinear_at(x, V, ps.strike, ps.strike)
+            res["price_space"].append({
+                "set": name, "n_x": nx, "precision": prec, "time_steps": nx // 2, "status": status, "wall_s": wall,
+                "fp_iters_total": st.fp_iters_total, "cell_iterations_per_s": st.cell_iters / wall,
+                "price_at_KK": price, "table4_at_KK": ps.table4_at_k, "diff": price - ps.table4_at_k})
+    ps = PAPER_SETS["VG0"]
+    n, hw = 2048, 11.5
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    grid = B.make_grid(n, B.PIDE2D_FP32_BULK, 3, half_width=hw)
+    model = B.make_model(ps.alpha, ps.delta, ps.lam, ps.eta, ps.rho, ps.r)
+    s = B.Solver(grid, model, B.make_contract(B.PIDE2D_PUT_AVG, ps.strike, ps.maturity), n // 2, tol=1e-8,
+                 device=dev)
+    price, _, st, _ = s.solve()
+    wall = time.perf_counter() - t0
+    s.close()
+    res["vg0_wide_log_domain"] = {
+        "n": n, "half_width": hw, "time_steps": n // 2, "precision": "fp32-bulk", "wall_s": wall,
+        "fp_iters_total": st.fp_iters_total, "cell_iterations_per_s": st.cell_iters / wall,
+        "price_at_KK": price, "table4_at_KK": ps.table4_at_k, "diff": price - ps.table4_at_k}
+    return res
 
 
 def run_sweep(B, torch, dev):

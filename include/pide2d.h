@@ -317,6 +317,19 @@ typedef struct {
 typedef struct pide2d_price pide2d_price_t;
 
 /* Workspace bytes for this grid.  Errors: ERR_ARG, ERR_UNSUPPORTED (P too large). */
+/* The paper's non-uniform price grid (Sec. 4), host-side, no GPU work:
+ * uniform x = c xi on [0, x_int = 2.5 K], then x_int + c sinh(xi - xi_int) up
+ * to x_max, on nx + 1 equidistant xi nodes, with c chosen so that
+ * xi_int / xi_max = max(frac, x_int / x_max) (c = infinity, i.e. a uniform grid,
+ * when x_int >= x_max); the z-lattice N_z = 2 nx cells of h_z = z_iii / N_z
+ * (z_iii = z_max^III); the y_out range from the first positive node to
+ * x_max: ny_minus = ceil(-ln x_1 / h_z), ny_plus = ceil(ln x_max / h_z).
+ *   x_out  host, nx + 1 doubles (written); grid->x is set to x_out.
+ * Errors: ERR_ARG (nx < 4 or > 8192, K, x_max, z_iii <= 0, frac outside
+ * (0, 1), NULL pointers); message via pide2d_last_error(NULL). */
+pide2d_status pide2d_price_sinh_grid(int nx, double strike, double x_max, double z_iii, double frac,
+                                     double* x_out, pide2d_price_grid* grid);
+
 pide2d_status pide2d_price_workspace_bytes(const pide2d_price_grid* grid, size_t* bytes);
 
 /* Builds the interpolation tables (host, FP64), the weights w, sigma_w sigma_w^T

@@ -100,6 +100,8 @@ def lib():
         L.pide2d_record.argtypes = [c_void_p, c_void_p, c_size_t, c_int, c_int]
         L.pide2d_adjoint.argtypes = [c_void_p, POINTER(pide2d_model), c_int, POINTER(c_double)]
         L.pide2d_price_workspace_bytes.argtypes = [POINTER(pide2d_price_grid), POINTER(c_size_t)]
+        L.pide2d_price_sinh_grid.argtypes = [c_int, c_double, c_double, c_double, c_double, c_void_p,
+                                             POINTER(pide2d_price_grid)]
         L.pide2d_price_create.argtypes = [POINTER(pide2d_price_grid), POINTER(pide2d_model), c_void_p, c_size_t,
                                           c_void_p, POINTER(c_void_p)]
         L.pide2d_price_apply_jump.argtypes = [c_void_p, c_void_p, c_void_p]
@@ -120,7 +122,7 @@ def lib():
                      "pide2d_profile_read", "pide2d_jump_static", "pide2d_greeks", "pide2d_batch_workspace_bytes",
                      "pide2d_batch_solve", "pide2d_tape_bytes", "pide2d_record", "pide2d_adjoint",
                      "pide2d_price_workspace_bytes", "pide2d_price_create", "pide2d_price_apply_jump",
-                     "pide2d_price_get_weights", "pide2d_price_solve"):
+                     "pide2d_price_get_weights", "pide2d_price_solve", "pide2d_price_sinh_grid"):
             getattr(L, name).restype = c_int
         _LIB = L
     return _LIB
@@ -436,6 +438,16 @@ def price_function():
             return (grad_out * g, None, None, None, None, None, None, None, None)
 
     return _Price
+
+
+def price_sinh_grid(nx, strike, x_max, z_iii, frac=0.65):
+    """pide2d_price_sinh_grid: the paper's price grid (Sec. 4).  Returns
+    (x, n_z, h_z, ny_minus, ny_plus) as PriceJump takes them."""
+    import numpy as np
+    x = np.empty(nx + 1, dtype=np.float64)
+    g = pide2d_price_grid()
+    _check(lib().pide2d_price_sinh_grid(nx, strike, x_max, z_iii, frac, x.ctypes.data, byref(g)))
+    return x, g.n_z, g.h_z, g.ny_minus, g.ny_plus
 
 
 class PriceJump:

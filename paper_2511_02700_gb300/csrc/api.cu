@@ -2408,6 +2408,44 @@ pide2d_status pide2d_adjoint(pide2d_t* H, const pide2d_model* dirs, int ndirs, d
                                             : do_adjoint<float>(H, dirs, ndirs, grad);
 }
 
+pide2d_status pide2d_price_sinh_grid(int nx, double strike, double x_max, double z_iii, double frac,
+                                     double* x_out, pide2d_price_grid* grid) {
+    if (nx < 4 || nx > 8192 || !(strike > 0.0) || !(x_max > 0.0) || !(z_iii > 0.0) || !(frac > 0.0 && frac < 1.0) ||
+        !x_out || !grid) {
+        pide::set_global_error("pide2d_price_sinh_grid: invalid arguments");
+        return PIDE2D_ERR_ARG;
+    }
+    const double x_int = 2.5 * strike;
+    const double F = std::max(frac, x_int / x_max);
+    if (F < 1.0) {
+        // c with xi_int / xi_max = F, xi_int = x_int / c, xi_max = xi_int + asinh((x_max - x_int) / c);
+        // the ratio falls from 1 (c -> 0) to x_int / x_max (c -> infinity): bisection on log c
+        auto ratio = [&](double c) { return 1.0 / (1.0 + c / x_int * std::asinh((x_max - x_int) / c)); };
+        double lo = std::log(1e-6 * x_int), hi = std::log(1e6 * x_max);
+        for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(1.0, std::fabs(hi)); ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (ratio(std::exp(mid)) > F) lo = mid;
+            else hi = mid;
+        }
+        const double c = std::exp(0.5 * (lo + hi));
+        const double xi_int = x_int / c, xi_max = xi_int + std::asinh((x_max - x_int) / c);
+        for (int m = 0; m <= nx; ++m) {
+            const double xi = m * (xi_max / nx);
+            x_out[m] = xi <= xi_int ? c * xi : x_int + c * std::sinh(xi - xi_int);
+        }
+    } else {
+        for (int m = 0; m <= nx; ++m) x_out[m] = m * (x_max / nx);
+    }
+    x_out[nx] = x_max;
+    grid->nx = nx;
+    grid->x = x_out;
+    grid->n_z = 2 * nx;
+    grid->h_z = z_iii / grid->n_z;
+    grid->ny_minus = (int)std::ceil(-std::log(x_out[1]) / grid->h_z);
+    grid->ny_plus = (int)std::ceil(std::log(x_max) / grid->h_z);
+    return PIDE2D_OK;
+}
+
 pide2d_status pide2d_price_workspace_bytes(const pide2d_price_grid* g, size_t* bytes) {
     const std::string e = check_price_grid(g);
     if (!e.empty() || !bytes) {

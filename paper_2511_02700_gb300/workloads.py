@@ -84,3 +84,34 @@ def random_field(n: int, seed: int, lo: float = 0.0, hi: float = 100.0) -> np.nd
 
 def with_(w: Workload, **kw) -> Workload:
     return replace(w, **kw)
+
+
+# The paper's own parameter sets (Table 2: NTS alpha, lambda, delta, eta, the
+# matrix rho as (rho11, rho12, rho22), r, T, K; sigma = 0), the price-space
+# domains of its Sec. 4 experiments (x_max / K and z_max^III), and its Table 4
+# price at (K, K) (N_x = 800; 400 for NIG0).  Printed values, cited data only.
+@dataclass(frozen=True)
+class PaperSet:
+    name: str
+    alpha: float
+    lam: float
+    delta: float
+    eta: tuple
+    rho: tuple
+    r: float
+    maturity: float
+    strike: float
+    x_max_over_k: float
+    z_max_iii: float
+    table4_at_k: float
+
+
+PAPER_SETS = {
+    "VG0": PaperSet("VG0", 0.0, 1.0, 1.0, (-0.1, -0.2), (0.09, 0.06, 0.16), 0.05, 1.0, 100.0, 57.0, 11.5010,
+                    8.8020),
+    "VG1": PaperSet("VG1", 0.0, 6.0, 6.0, (-0.1, -0.2), (0.01, 0.0, 0.0225), 0.0, 0.5, 100.0, 5.0, 2.1410, 2.9029),
+    "NIG0": PaperSet("NIG0", 0.5, 20766.4, 0.77576, (-37.688, -2.224), (3.984, 3.160, 3.512), 0.0, 0.5, 100.0,
+                     6.0, 0.4172, 5.1186),
+    "NIG1": PaperSet("NIG1", 0.5, 57.1108, 4.26367, (-0.295846, -0.292984), (0.037021, 0.026574, 0.054613), 0.0,
+                     0.5, 100.0, 7.0, 0.8807, 5.3956),
+}

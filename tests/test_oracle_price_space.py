@@ -119,3 +119,25 @@ def test_table4_with_the_papers_discretisation(name):
         res = PriceScheme(mo, pg, co, n // 2, tol=1e-7).solve()
         errs.append(max(abs(res.price_at(a, a) - table[(a, a)]) for a in (90.0, 100.0, 110.0)))
     assert errs[1] < errs[0] and errs[1] < 0.04, errs
+
+
+@pytest.mark.parametrize("name,xm,ziii,n", [("VG1", 5.0, 2.1410, 160), ("NIG1", 7.0, 0.8807, 80),
+                                            ("VG0", 57.0, 11.5010, 40)])
+def test_c_abi_sinh_grid_matches_oracle_grid(name, xm, ziii, n):
+    """pide2d_price_sinh_grid (host code of the library, no GPU) builds the same
+    Sec. 4 grid as the oracle's PriceGrid: nodes to 1e-12 relative, the same
+    z-lattice, and the unpadded y_out range (the oracle pads #in to a 7-smooth
+    length, the CUDA path's FFT length is a power of two)."""
+    import math
+    from paper_2511_02700_gb300 import binding as B
+    from paper_2511_02700_gb300 import build
+    build.build()
+    K = 100.0
+    pg = PriceGrid(n, K, xm * K, ziii)
+    x, n_z, h_z, nym, nyp = B.price_sinh_grid(n, K, xm * K, ziii)
+    assert np.max(np.abs(x - pg.x) / np.maximum(pg.x, 1.0)) <= 1e-12
+    assert n_z == pg.n_z and h_z == pytest.approx(pg.h_z, rel=1e-15)
+    assert nym == math.ceil(-math.log(pg.x[1]) / pg.h_z) and nyp == math.ceil(math.log(pg.x_max) / pg.h_z)
+    assert pg.ny_minus - nym == pg.ny_plus - nyp >= 0
+    with pytest.raises(B.PideError):
+        B.price_sinh_grid(3, K, xm * K, ziii)
