@@ -138,10 +138,15 @@ __device__ __forceinline__ void row_forward_body(const FwdArgs<R>& a) {
         block_fft<R, -1, P>(buf, t, tw, load, SmemStore<R>{buf});
     } else {
         const int m2a = rho - N / 2 - 1;
-        for (int idx = t; idx < P + 2; idx += NT) {
-            const int m1 = idx - N / 2 - 1;
-            nodes[idx] = valid ? node_value(a, m1, m2a) : R(0);
-            nodes[P + 2 + idx] = valid ? node_value(a, m1, m2a + 1) : R(0);
+        // a compile-time trip count lets the loop unroll and its loads go out together
+#pragma unroll
+        for (int q = 0; q < (P + 2 + NT - 1) / NT; ++q) {
+            const int idx = t + q * NT;
+            if (idx < P + 2) {
+                const int m1 = idx - N / 2 - 1;
+                nodes[idx] = valid ? node_value(a, m1, m2a) : R(0);
+                nodes[P + 2 + idx] = valid ? node_value(a, m1, m2a + 1) : R(0);
+            }
         }
         __syncthreads();
         auto load = [&](int i) -> C {
@@ -295,7 +300,10 @@ __device__ __forceinline__ void row_inverse_body(const InvArgs<R>& a) {
     // the two spectrum rows, each value read once (the Hermitian extension uses
     // every k twice): k at plain indices 2k, 2k + 1 of buf, which the first stage
     // reads completely before it writes
-    for (int k = t; k <= P / 2; k += NT) {
+#pragma unroll
+    for (int q = 0; q < (P / 2 + NT) / NT; ++q) {
+        const int k = t + q * NT;
+        if (k > P / 2) break;
         C xa = mk<R>(0, 0), xb = mk<R>(0, 0);
         if (valid) {
             const int g = k / Gc, c = k - g * Gc;
@@ -464,7 +472,10 @@ __device__ __forceinline__ void dst_row_body(const DstRowArgs<R>& a) {
     const C* tw = (const C*)a.tw;
     // the two DST rows, each value read once (the odd extension uses every j
     // twice), at plain indices of buf, which the first stage reads before it writes
-    for (int j = t; j <= N; j += NT) {
+#pragma unroll
+    for (int q = 0; q < (N + NT) / NT; ++q) {
+        const int j = t + q * NT;
+        if (j > N) break;
         R ea = 0, eb = 0;
         if (valid && j >= 1 && j <= N - 1) {
             const int gE = j / GE, c = j - gE * GE;
