@@ -24,6 +24,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -83,7 +84,9 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # raw samples go to $PIDE2D_CLOCKS_DIR (default: the temporary directory)
+        out_dir = os.environ.get("PIDE2D_CLOCKS_DIR", tempfile.gettempdir())
+        self.path = os.path.join(out_dir, f"pide2d_clocks_rank{gpu_index}.csv")
 
     def start(self):
         try:
