@@ -11,6 +11,6 @@ from .levy import (NTSModel, char_exponent_1d, levy_density, levy_density_subord
 from .scheme import (CALL_AVG, PUT_ASSET1, PUT_AVG, Contract, Grid, Precomputed, Scheme,
                      apply_diffusion, cell_average, circulant_product, cell_integral_r2, diffusion_matrix, extend,
                      far_field, greeks, initial_values, jump_direct, jump_fft, midpoints, precompute,
-                     r1_moment, sl_interpolate, sl_weights, zones)
+                     r1_moment, sl_interpolate, sl_weights, solve_nonmixed, zones)
 from .sensitivities import PARAMS as SENSITIVITY_PARAMS, price_gradient_fd
 from .price_space import PriceGrid, PriceScheme, PriceSpaceOperators

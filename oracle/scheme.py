@@ -363,6 +363,24 @@ def apply_diffusion(grid: Grid, a: np.ndarray, V: np.ndarray) -> np.ndarray:
     return 0.5 * a[0, 0] * d11 + a[0, 1] * d12 + 0.5 * a[1, 1] * d22
 
 
+def solve_nonmixed(grid: Grid, a: np.ndarray, r_w: float, ht: float, theta: float,
+                   rhs: np.ndarray) -> np.ndarray:
+    """X with ((1 + ht theta r_w) I - ht theta (a11/2 d11 + a22/2 d22)) X = rhs on
+    the interior nodes ((N-1) x (N-1), zero Dirichlet ring): the matrix of
+    eq. (3.24) without the mixed term a12 d1 d2 (Sec. 3.2.1 differences).  The
+    operator is diagonal in the 2D sine basis sin(pi k m / N), with
+    eigenvalues 1 + ht theta (r_w + a11/2 l_k1 + a22/2 l_k2),
+    l_k = (2 - 2 cos(pi k / N)) / h^2; the type-I DST of scipy is used as a
+    library step.  (Used to check the CUDA path's inner solve kernel by kernel;
+    the scheme itself solves eq. (3.24) with the full matrix.)"""
+    from scipy.fft import dstn, idstn
+    n, h = grid.n, grid.h
+    k = np.arange(1, n)
+    lk = (2.0 - 2.0 * np.cos(np.pi * k / n)) / (h * h)
+    lam = 1.0 + ht * theta * (r_w + 0.5 * a[0, 0] * lk[None, :] + 0.5 * a[1, 1] * lk[:, None])
+    return idstn(dstn(rhs, type=1) / lam, type=1)
+
+
 def sl_weights(shift_cells: float, order: int):
     """Lagrange weights for evaluating at node + shift (|shift| < 1 cell).
     Returns (first tap offset, weights).  order 1: linear on [o, o+1];

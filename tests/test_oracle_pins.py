@@ -18,7 +18,7 @@ from oracle import (CALL_AVG, PUT_ASSET1, PUT_AVG, Contract, Grid, NTSModel, Sch
                     circulant_product, diffusion_matrix, extend, far_field, initial_values,
                     jump_direct, jump_fft, levy_density, levy_density_subordinated,
                     model_from_subordinated_bm, precompute, put_price_1d, r1_moment,
-                    sl_interpolate, sl_weights, variance, zones)
+                    sl_interpolate, sl_weights, solve_nonmixed, variance, zones)
 from oracle.scheme import MID_W, midpoints
 
 WORKLOAD = dict(kappa=0.5, beta=(-0.10, -0.05), sigma=(0.20, 0.25), corr=0.3, r=0.03)
@@ -270,6 +270,27 @@ def test_diffusion_exact_on_quadratics_and_matrix_consistent():
     lhs = apply_diffusion(g, a, V).ravel()
     rhs = D @ V[1:-1, 1:-1].ravel() + apply_diffusion(g, a, ring).ravel()
     assert np.abs(lhs - rhs).max() < 1e-10
+
+
+@pytest.mark.parametrize("n", [8, 16, 33])
+def test_nonmixed_solve_equals_sparse_direct_solve(n):
+    """The sine-basis solve of the eq. (3.24) matrix without its mixed term
+    against a sparse LU solve of the same matrix assembled from the finite
+    differences (diffusion_matrix with a12 = 0); n = 33 is an odd grid."""
+    import scipy.sparse as sp_
+    import scipy.sparse.linalg as spla_
+    g = Grid(n)
+    a = np.array([[0.05, 0.0], [0.0, 0.0725]])
+    r_w, ht, theta = 3.7, 0.02, 0.5
+    rhs = np.random.default_rng(n).standard_normal((n - 1, n - 1))
+    A = (sp_.identity((n - 1) ** 2) * (1.0 + ht * theta * r_w) - ht * theta * diffusion_matrix(g, a)).tocsc()
+    ref = spla_.spsolve(A, rhs.ravel()).reshape(n - 1, n - 1)
+    # the mixed coefficient is ignored: a12 != 0 gives the same solution
+    a_mixed = a.copy()
+    a_mixed[0, 1] = a_mixed[1, 0] = 0.03
+    for aa in (a, a_mixed):
+        got = solve_nonmixed(g, aa, r_w, ht, theta, rhs)
+        assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
 
 
 @pytest.mark.parametrize("order,deg", [(1, 1), (3, 3)])
