@@ -60,13 +60,20 @@ enum {
     PIDE2D_PUT_ASSET1 = 2   /* max(K - S1, 0): single-asset reduction (tests)     */
 };
 
-/* arithmetic of the transforms (FFT, DST, interpolation); state, weights,
- * reductions and the stop test are FP64 in both modes */
+/* Arithmetic of the transforms (FFT, DST, interpolation, stencils).  In both
+ * modes the weights, sigma_w sigma_w^T and the rates are computed in FP64, the
+ * eq. 3.25 stopping quantity that is compared with fp_tol is an FP64 value,
+ * and the price is read out in FP64.  The state fields (V history, Y, W,
+ * B_w Y) are FP64 in PIDE2D_FP64 mode and double-float pairs of FP32 values
+ * (hi + lo, about 48 significant bits) in PIDE2D_FP32_BULK mode.  In
+ * FP32-bulk mode the node that attains the eq. 3.25 maximum of a block is
+ * chosen by FP32 ratios and its ratio is then evaluated in FP64, so the value
+ * compared with fp_tol is within 2^-20 relative of the exact FP64 maximum. */
 enum { PIDE2D_FP64 = 0, PIDE2D_FP32_BULK = 1 };
 
 /* Spatial grid [Sec. 3.2, uniform in log price]. */
 typedef struct {
-    int n;                /* N: power of two, 8 <= N <= 4096 (FP64: N <= 2048)  */
+    int n;                /* N: power of two, 8 <= N <= 4096 (both precisions)  */
     int n_z;              /* N_z: 0 or N/2 (z_max^III = L); other values ERR_ARG */
     double s_center[2];   /* ln S0 per axis (node N/2)                            */
     double half_width;    /* L > 0                                                */
@@ -184,6 +191,30 @@ pide2d_status pide2d_greeks(pide2d_t* h, double* delta1, double* delta2, double*
 pide2d_status pide2d_apply_jump(pide2d_t* h, const double* U, double tau, int far_field,
                                 double* out);
 
+/* Diagnostic: one iteration of the fixed-point loop (eqs. 3.24-3.25) as the
+ * time loop runs it, applied to a caller residual r.  With
+ *   M = (1 + ht theta r_w) I - ht theta (a11/2 d11 + a22/2 d22)
+ * on the interior nodes (zero Dirichlet ring; the eq. 3.24 operator without
+ * its mixed term, which the loop carries in the fixed point), it computes
+ *   delta  = M^{-1} r         (DST-I along rows, then columns, and back),
+ *   bdelta = B_w delta        (the increment sweep of eq. 3.17: zero far field,
+ *                              the midpoint interpolation of T_in folded into
+ *                              the weight spectrum),
+ *   *stop  = max |delta| / max(1, |delta|)  (eq. 3.25 for an iterate from 0),
+ * through the same kernels and launch shapes as the time loop (row DST of r,
+ * column DST pass, row DST pass with the R2C rows of delta, column pass,
+ * inverse row pass).
+ *   r           (N+1)^2 doubles [m2][m1], device or host; interior nodes used
+ *   ht, theta   ht > 0, 0 < theta <= 1
+ *   delta_out, bdelta_out  NULL or (N+1)^2 doubles (device or host); only the
+ *               interior entries are written
+ *   stop_out    NULL or one host double
+ * Uses the handle's scratch fields only (callable between time steps without
+ * changing the solution).  Blocks until done.  Errors: ERR_ARG, ERR_STATE,
+ * ERR_CUDA. */
+pide2d_status pide2d_iteration_probe(pide2d_t* h, const double* r, double ht, double theta,
+                                     double* delta_out, double* bdelta_out, double* stop_out);
+
 /* Kernel classes of the time loop, for pide2d_profile_read(). */
 enum {
     PIDE2D_KERNEL_PREP = 0,            /* W = T_SL[...] and Y^{n,0} (Algorithm 1 steps 2-3)   */
@@ -248,6 +279,43 @@ pide2d_status pide2d_record(pide2d_t* h, void* tape, size_t bytes, int interval,
  * Errors: ERR_STATE (no tape or the solve is not finished), ERR_ARG,
  * ERR_NOT_CONVERGED (an adjoint solve hit kmax; grad still written), ERR_CUDA. */
 pide2d_status pide2d_adjoint(pide2d_t* h, const pide2d_model* dirs, int ndirs, double* grad);
+
+/* ------------------------------------------------------------------------
+ * Workload parameterisation [Appendix A, Table A5]: the NTS process as a
+ * Brownian motion with drift beta and volatilities sigma, correlation corr,
+ * time-changed by a unit-mean tempered-stable subordinator G with index
+ * alpha and variance V[G(1)] = kappa.  Table A5 gives E[G(1)] =
+ * delta Gamma(1-alpha) / lambda^(1-alpha) and V[G(1)] / E[G(1)] =
+ * (1-alpha) / lambda, so
+ *   lambda = (1 - alpha) / kappa,  delta = lambda^(1-alpha) / Gamma(1-alpha),
+ *   eta = beta,  rho = [[s1^2, corr s1 s2], [corr s1 s2, s2^2]],
+ * and the paper's extra Gaussian part sigma sigma^T is 0 (as in its Sec. 4).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    double alpha;         /* 0 <= alpha < 1                                        */
+    double kappa;         /* variance of G(1), > 0                                 */
+    double beta[2];       /* Brownian drift                                        */
+    double sigma[2];      /* Brownian volatilities, > 0                            */
+    double corr;          /* Brownian correlation, |corr| < 1                      */
+    double r;             /* riskless rate                                         */
+} pide2d_workload;
+
+/* The pide2d_model of a workload (the mapping above; host only).
+ * Errors: ERR_ARG (invalid workload or NULL out; message via
+ * pide2d_last_error(NULL)). */
+pide2d_status pide2d_model_from_workload(const pide2d_workload* w, pide2d_model* out);
+
+/* dirs[0..5] (host, 6 structs) receive the derivatives of that model with
+ * respect to sigma1, sigma2, corr, kappa, beta1, beta2: the directions
+ * pide2d_adjoint takes for the workload's gradient.  Errors: ERR_ARG. */
+pide2d_status pide2d_workload_directions(const pide2d_workload* w, pide2d_model* dirs);
+
+/* pide2d_adjoint along the six workload directions: grad[0..5] (host) =
+ * d V^{N_t}(S0) / d (sigma1, sigma2, corr, kappa, beta1, beta2).  The handle
+ * must have been created with pide2d_model_from_workload(w) and recorded with
+ * ndirs >= 6.  Errors: ERR_ARG (NULL, invalid workload, or a handle whose
+ * model is not w's), and those of pide2d_adjoint. */
+pide2d_status pide2d_adjoint_workload(pide2d_t* h, const pide2d_workload* w, double* grad);
 
 /* ------------------------------------------------------------------------
  * Batches: many independent pricings on one GPU (one time loop each, as in
@@ -366,16 +434,18 @@ pide2d_status pide2d_price_get_weights(pide2d_price_t* h, double* omega_out, dou
 const char* pide2d_price_last_error(const pide2d_price_t* h);
 void pide2d_price_destroy(pide2d_price_t* h);
 
-/* B_w U (eq. 3.17 sweep) computed without any device allocation.  The paper
- * has no counterpart: this entry point exists for callers that cannot
- * allocate device memory -- e.g. a plugin in a host process whose memory
- * manager owns the whole device, or a service that must not call cudaMalloc
- * (it can synchronise the device) after start-up.  Its scratch is a fixed
- * 7.2 MB device array inside the library, present on every GPU where the
- * library is loaded until the process exits; hence n <= 256.
+/* The jump sum of a field U with given weights and a zero far field -- the
+ * same sum pide2d_apply_jump computes with far_field = 0 -- without any
+ * device allocation.  The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory -- e.g. a plugin in a host
+ * process whose memory manager owns the whole device, or a service that must
+ * not call cudaMalloc (it can synchronise the device) after start-up.  Its
+ * scratch is a fixed 7.2 MB device array inside the library, present on
+ * every GPU where the library is loaded until the process exits; hence
+ * n <= 256.
  *   n      power of two in [8, 256] (FP64 arithmetic, N_z = n/2)
- *   omega  device, n x n doubles, the weights [l2 + n/2][l1 + n/2] (eq. 3.5),
- *          e.g. from pide2d_get_weights
+ *   omega  device, n x n doubles, the weights [l2 + n/2][l1 + n/2] in the
+ *          layout pide2d_get_weights returns them
  *   U      device, (n+1)^2 doubles [m2][m1]; its interior nodes are used and
  *          every other node counts as 0
  *   out    device, (n+1)^2 doubles; receives B_w U at the interior nodes, the

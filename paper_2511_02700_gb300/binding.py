@@ -50,6 +50,11 @@ class pide2d_kernel_times(ctypes.Structure):
     _fields_ = [("launches", c_int * 16), ("ms", c_double * 16)]
 
 
+class pide2d_workload(ctypes.Structure):
+    _fields_ = [("alpha", c_double), ("kappa", c_double), ("beta", c_double * 2), ("sigma", c_double * 2),
+                ("corr", c_double), ("r", c_double)]
+
+
 class pide2d_job(ctypes.Structure):
     _fields_ = [("grid", pide2d_grid), ("model", pide2d_model), ("contract", pide2d_contract),
                 ("theta", c_double), ("dt", c_double), ("fp_tol", c_double)]
@@ -90,6 +95,8 @@ def lib():
         L.pide2d_get_values.argtypes = [c_void_p, c_void_p]
         L.pide2d_get_weights.argtypes = [c_void_p, c_void_p, c_void_p]
         L.pide2d_apply_jump.argtypes = [c_void_p, c_void_p, c_double, c_int, c_void_p]
+        L.pide2d_iteration_probe.argtypes = [c_void_p, c_void_p, c_double, c_double, c_void_p, c_void_p,
+                                             POINTER(c_double)]
         L.pide2d_last_error.argtypes = [c_void_p]
         L.pide2d_last_error.restype = ctypes.c_char_p
         L.pide2d_profile.argtypes = [c_void_p, c_int]
@@ -99,6 +106,9 @@ def lib():
         L.pide2d_tape_bytes.argtypes = [c_void_p, c_int, c_int, POINTER(c_size_t)]
         L.pide2d_record.argtypes = [c_void_p, c_void_p, c_size_t, c_int, c_int]
         L.pide2d_adjoint.argtypes = [c_void_p, POINTER(pide2d_model), c_int, POINTER(c_double)]
+        L.pide2d_model_from_workload.argtypes = [POINTER(pide2d_workload), POINTER(pide2d_model)]
+        L.pide2d_workload_directions.argtypes = [POINTER(pide2d_workload), POINTER(pide2d_model)]
+        L.pide2d_adjoint_workload.argtypes = [c_void_p, POINTER(pide2d_workload), POINTER(c_double)]
         L.pide2d_price_workspace_bytes.argtypes = [POINTER(pide2d_price_grid), POINTER(c_size_t)]
         L.pide2d_price_sinh_grid.argtypes = [c_int, c_double, c_double, c_double, c_double, c_void_p,
                                              POINTER(pide2d_price_grid)]
@@ -118,9 +128,11 @@ def lib():
         L.pide2d_destroy.argtypes = [c_void_p]
         L.pide2d_destroy.restype = None
         for name in ("pide2d_workspace_bytes", "pide2d_create", "pide2d_step", "pide2d_solve",
-                     "pide2d_get_values", "pide2d_get_weights", "pide2d_apply_jump", "pide2d_profile",
+                     "pide2d_get_values", "pide2d_get_weights", "pide2d_apply_jump", "pide2d_iteration_probe",
+                     "pide2d_profile",
                      "pide2d_profile_read", "pide2d_jump_static", "pide2d_greeks", "pide2d_batch_workspace_bytes",
                      "pide2d_batch_solve", "pide2d_tape_bytes", "pide2d_record", "pide2d_adjoint",
+                     "pide2d_model_from_workload", "pide2d_workload_directions", "pide2d_adjoint_workload",
                      "pide2d_price_workspace_bytes", "pide2d_price_create", "pide2d_price_apply_jump",
                      "pide2d_price_get_weights", "pide2d_price_solve", "pide2d_price_sinh_grid"):
             getattr(L, name).restype = c_int
@@ -177,6 +189,13 @@ def pide2d_apply_jump(h, U_ptr, tau, far_field, out_ptr):
     _check(lib().pide2d_apply_jump(h, c_void_p(U_ptr), tau, int(far_field), c_void_p(out_ptr)), h)
 
 
+def pide2d_iteration_probe(h, r_ptr, ht, theta, delta_ptr, bdelta_ptr):
+    stop = c_double(0.0)
+    _check(lib().pide2d_iteration_probe(h, c_void_p(r_ptr), ht, theta, c_void_p(delta_ptr) if delta_ptr else None,
+                                        c_void_p(bdelta_ptr) if bdelta_ptr else None, byref(stop)), h)
+    return stop.value
+
+
 def pide2d_greeks(h, delta1, delta2, gamma11, gamma12, gamma22):
     _check(lib().pide2d_greeks(h, *[c_void_p(p) if p else None for p in
                                     (delta1, delta2, gamma11, gamma12, gamma22)]), h)
@@ -214,6 +233,13 @@ def pide2d_adjoint(h, dirs):
     arr = (pide2d_model * k)(*dirs)
     g = (c_double * k)()
     st = _check(lib().pide2d_adjoint(h, arr, k, g), h)
+    return list(g), st
+
+
+def pide2d_adjoint_workload(h, workload):
+    """Returns (gradient in SUBORDINATED_BM_PARAMS order, status)."""
+    g = (c_double * 6)()
+    st = _check(lib().pide2d_adjoint_workload(h, byref(workload), g), h)
     return list(g), st
 
 
@@ -276,35 +302,33 @@ def make_model(alpha, delta, lam, eta, rho, r, sigma_cov=(0.0, 0.0, 0.0)):
     return m
 
 
+def make_workload(alpha, kappa, beta, sigma, corr, r):
+    w = pide2d_workload()
+    w.alpha, w.kappa = alpha, kappa
+    w.beta[0], w.beta[1] = beta
+    w.sigma[0], w.sigma[1] = sigma
+    w.corr, w.r = corr, r
+    return w
+
+
 def model_from_subordinated_bm(alpha, kappa, beta, sigma, corr, r):
-    """Unit-mean tempered-stable subordinator with variance kappa (Table A5:
-    lambda = (1-alpha)/kappa, delta = lambda^(1-alpha)/Gamma(1-alpha)),
-    Brownian drift beta and covariance [[s1^2, c s1 s2], [c s1 s2, s2^2]]."""
-    lam = (1.0 - alpha) / kappa
-    delta = lam ** (1.0 - alpha) / math.gamma(1.0 - alpha)
-    s1, s2 = sigma
-    return make_model(alpha, delta, lam, beta, (s1 * s1, corr * s1 * s2, s2 * s2), r)
+    """pide2d_model_from_workload: the NTS model of a unit-mean tempered-stable
+    subordinator with variance kappa, Brownian drift beta, volatilities sigma
+    and correlation corr (the mapping lives in the C library)."""
+    m = pide2d_model()
+    _check(lib().pide2d_model_from_workload(byref(make_workload(alpha, kappa, beta, sigma, corr, r)), byref(m)))
+    return m
 
 
 SUBORDINATED_BM_PARAMS = ("sigma1", "sigma2", "corr", "kappa", "beta1", "beta2")
 
 
-def subordinated_bm_directions(alpha, kappa, beta, sigma, corr):
-    """Tangents d(model)/dp of model_from_subordinated_bm for p in
+def subordinated_bm_directions(alpha, kappa, beta, sigma, corr, r=0.0):
+    """pide2d_workload_directions: the six model tangents for
     SUBORDINATED_BM_PARAMS, as pide2d_model directions for pide2d_adjoint."""
-    lam = (1.0 - alpha) / kappa
-    delta = lam ** (1.0 - alpha) / math.gamma(1.0 - alpha)
-    s1, s2 = sigma
-    z = (0.0, 0.0)
-    dirs = [
-        make_model(0.0, 0.0, 0.0, z, (2.0 * s1, corr * s2, 0.0), 0.0),           # sigma1
-        make_model(0.0, 0.0, 0.0, z, (0.0, corr * s1, 2.0 * s2), 0.0),           # sigma2
-        make_model(0.0, 0.0, 0.0, z, (0.0, s1 * s2, 0.0), 0.0),                  # corr
-        make_model(0.0, -(1.0 - alpha) * delta / kappa, -lam / kappa, z, (0.0, 0.0, 0.0), 0.0),  # kappa
-        make_model(0.0, 0.0, 0.0, (1.0, 0.0), (0.0, 0.0, 0.0), 0.0),             # beta1
-        make_model(0.0, 0.0, 0.0, (0.0, 1.0), (0.0, 0.0, 0.0), 0.0),             # beta2
-    ]
-    return dirs
+    dirs = (pide2d_model * 6)()
+    _check(lib().pide2d_workload_directions(byref(make_workload(alpha, kappa, beta, sigma, corr, r)), dirs))
+    return list(dirs)
 
 
 def make_contract(payoff=PIDE2D_PUT_AVG, strike=100.0, maturity=1.0):
@@ -370,6 +394,15 @@ class Solver:
         pide2d_apply_jump(self.h, U.data_ptr(), tau, far_field, out.data_ptr())
         return out
 
+    def iteration_probe(self, r, ht, theta=0.5):
+        """pide2d_iteration_probe: (delta, B_w delta, stop) for a residual field r."""
+        torch = self.torch
+        r = r.to(device=self.ws.device, dtype=torch.float64).contiguous()
+        d = torch.zeros_like(r)
+        bd = torch.zeros_like(r)
+        stop = pide2d_iteration_probe(self.h, r.data_ptr(), ht, theta, d.data_ptr(), bd.data_ptr())
+        return d, bd, stop
+
     def record(self, interval=16, ndirs=6):
         """Checkpoint the time loop for pide2d_adjoint (before the first step)."""
         torch = self.torch
@@ -381,6 +414,10 @@ class Solver:
 
     def adjoint(self, dirs):
         return pide2d_adjoint(self.h, dirs)
+
+    def adjoint_workload(self, workload):
+        """Gradient with respect to SUBORDINATED_BM_PARAMS (pide2d_adjoint_workload)."""
+        return pide2d_adjoint_workload(self.h, workload)
 
     def close(self):
         if self.h:
@@ -422,12 +459,13 @@ def price_function():
         @staticmethod
         def forward(ctx, params, alpha, r, grid, contract, n_steps, theta=0.5, tol=1e-10, interval=16):
             p = [float(x) for x in params.detach().cpu().tolist()]
-            sig, corr, kap, beta = (p[0], p[1]), p[2], p[3], (p[4], p[5])
-            model = model_from_subordinated_bm(alpha, kap, beta, sig, corr, r)
+            wl = make_workload(alpha, p[3], (p[4], p[5]), (p[0], p[1]), p[2], r)
+            model = pide2d_model()
+            _check(lib().pide2d_model_from_workload(byref(wl), byref(model)))
             s = Solver(grid, model, contract, n_steps, theta=theta, tol=tol)
             s.record(interval=interval, ndirs=6)
             price, _, _, _ = s.solve()
-            g, _ = s.adjoint(subordinated_bm_directions(alpha, kap, beta, sig, corr))
+            g, _ = s.adjoint_workload(wl)
             s.close()
             ctx.save_for_backward(torch.tensor(g, dtype=torch.float64))
             return torch.tensor(price, dtype=torch.float64)

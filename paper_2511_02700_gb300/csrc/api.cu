@@ -124,7 +124,6 @@ std::string check_grid(const pide2d_grid* g) {
     if (!std::isfinite(g->s_center[0]) || !std::isfinite(g->s_center[1])) return "grid.s_center must be finite";
     if (g->sl_order != 0 && g->sl_order != 1 && g->sl_order != 3) return "grid.sl_order must be 0, 1 or 3";
     if (g->precision != PIDE2D_FP64 && g->precision != PIDE2D_FP32_BULK) return "grid.precision invalid";
-    if (g->precision == PIDE2D_FP64 && g->n > 2048) return "FP64 mode supports n <= 2048";
     return "";
 }
 
@@ -517,6 +516,12 @@ struct SolveSpec {
     const St<R>* W;
     int far;
     double Kd;
+    // difference sweep: when Vprev is set, the first sweep transforms
+    // Y^{0} - Vprev with the halo g(tau) - g(tau_prev) and B_w Y^{0} =
+    // BVprev + that sweep (BVprev = B_w Vprev with the halo at tau_prev)
+    const St<R>* Vprev;
+    const St<R>* BVprev;
+    double Kd_prev;
     const void* Wh;
     const void* Whi;
     double theta, ht;
@@ -549,6 +554,13 @@ static void build_solve_args(pide2d* H, const SolveSpec<R>& sp, SolveArgs<R>* ou
     FwdArgs<R>& fa = out->fa;
     fa.g = g;
     fa.mode = sp.far ? FWD_FULL : FWD_FULL0;
+    const bool diff = sp.far && sp.Vprev && sp.BVprev;
+    if (diff) {
+        fa.mode = FWD_DIFF;
+        fa.Yref = sp.Vprev;
+        fa.Kd_prev = (R)sp.Kd_prev;
+        fa.dKd = (R)(sp.Kd - sp.Kd_prev);
+    }
     fa.Y = sp.Y;
     fa.D = H->at<R>(R_DLT);
     fa.E1 = (const R*)(sizeof(R) == 4 ? (const void*)H->at<float>(R_E1F) : (const void*)H->at<double>(R_E1D));
@@ -572,10 +584,12 @@ static void build_solve_args(pide2d* H, const SolveSpec<R>& sp, SolveArgs<R>* ou
         // staged s1, i.e. (e^{s1,min} + e^{s2}) / 2 >= K e^{-r tau}: their transforms
         // are zero, so the row pass stops before them and the column pass treats
         // them as zero (a relative margin of 1e-6 covers the FP32 evaluation)
+        // (for the difference sweep both g(tau) and g(tau_prev) vanish there)
+        const double kz = diff ? std::max(sp.Kd, sp.Kd_prev) : sp.Kd;
         const double e1min = std::exp(H->s_lo1 + (-N / 2 - 1) * hg);
         int m2z = 3 * N / 2 + 1;
         for (int m2 = N; m2 <= 3 * N / 2; ++m2) {
-            if (0.5 * (e1min + std::exp(H->s_lo2 + m2 * hg)) >= sp.Kd * (1.0 + 1e-6)) {
+            if (0.5 * (e1min + std::exp(H->s_lo2 + m2 * hg)) >= kz * (1.0 + 1e-6)) {
                 m2z = m2;
                 break;
             }
@@ -600,6 +614,8 @@ static void build_solve_args(pide2d* H, const SolveSpec<R>& sp, SolveArgs<R>* ou
     ia.d22 = d22;
     ia.d12 = d12;
     ia.rw = (R)rw;
+    ia.rw_lo = (R)(rw - (double)(R)rw);
+    ia.BV = diff ? sp.BVprev : nullptr;
     ia.E = H->at<R>(R_E);
     ia.tw = tw;
     DstColArgs<R>& da = out->da;
@@ -626,6 +642,7 @@ static void build_solve_args(pide2d* H, const SolveSpec<R>& sp, SolveArgs<R>* ou
     out->cai.rhi = N / 2 + N + 2;
     std::memcpy(&out->iai, &ia, sizeof ia);
     out->iai.mode = INV_INCR;
+    out->iai.BV = nullptr;          // the increment pass does not read it (and it must not key the loop graphs)
 }
 
 template <typename R>
@@ -675,10 +692,10 @@ static pide2d_status fixed_point_solve(pide2d* H, const SolveSpec<R>& sp, int* i
         PIDE_LAUNCH(PIDE2D_KERNEL_DST_COL, launch_dst_col<R>(da, H->stream));
         PIDE_CUDA(cudaMemsetAsync(H->at<void>(R_RESID), 0, 16, H->stream));
         PIDE_LAUNCH(PIDE2D_KERNEL_DST_ROW, launch_dst_row<R>(ra, H->stream));
-        R rhost = 0;
-        PIDE_CUDA(cudaMemcpyAsync(&rhost, H->at<void>(R_RESID), sizeof(R), cudaMemcpyDeviceToHost, H->stream));
+        double rhost = 0.0;
+        PIDE_CUDA(cudaMemcpyAsync(&rhost, H->at<void>(R_RESID), sizeof(double), cudaMemcpyDeviceToHost, H->stream));
         PIDE_CUDA(cudaStreamSynchronize(H->stream));
-        resid = (double)rhost;
+        resid = rhost;
         conv = resid < H->tol;
         if (!std::isfinite(resid)) break;
         // B_w of the increment keeps B_w Y^{k} current (needed for the next W);
@@ -728,6 +745,7 @@ static pide2d_status build_theta_step(pide2d* H, const int* list, int cnt, doubl
     pa.cz = H->at<R>(R_RES);   // the residual field is free until the first sweep of the step
     pa.htm = (R)htm;
     pa.rw = (R)rw;
+    pa.rw_lo = (R)(rw - (double)(R)rw);
     pa.d11 = d11;
     pa.d22 = d22;
     pa.d12 = d12;
@@ -758,6 +776,9 @@ static pide2d_status build_theta_step(pide2d* H, const int* list, int cnt, doubl
     sp.W = W;
     sp.far = 1;
     sp.Kd = Kd_now;
+    sp.Vprev = pa.V[0];             // V^{n-1}, whose B_w V (with the halo at tau_prev) is BV
+    sp.BVprev = BV;
+    sp.Kd_prev = Kd_prev;
     sp.Wh = H->at<void>(R_WH);
     sp.Whi = H->at<void>(R_WHI);
     sp.theta = theta;
@@ -943,6 +964,91 @@ static pide2d_status weight_spectrum(pide2d* H, const double* omega, void* Wh, v
     return PIDE2D_OK;
 }
 
+// B_w V^0 of an FP32-bulk handle, computed in FP64.  Every later sweep of the
+// time loop transforms a difference (Y^{n,0} - V^{n-1}, or an increment), so
+// B_w V carries the rounding of this first sweep through the whole solve.
+// The FP64 spectra are staged in the state-field region, which holds nothing
+// else yet (V^0 is in field 0; the result goes to field bv at the end):
+//   R_OUT (field 9)   V^0 in FP64, then B_w V^0 at the interior nodes
+//   fields 1..8       FP64 row spectra of Omega, then the FP64 spectrum of V^0,
+//                     and the FP64 weight spectrum conj(w^)/P^2 after them
+// Each state field holds >= 8 (N+1)^2 bytes, so fields 1..8 hold the
+// 32 (N+1)^2 + 32 N (N+1) bytes needed.  The staging is cleared afterwards.
+static pide2d_status bv0_fp64(pide2d* H) {
+    const Geometry g = H->L.g;
+    const int N = g.N;
+    cudaStream_t s = H->stream;
+    Geometry gd = g;
+    gd.ng = spectrum_groups<double>(g.P);
+    gd.nge = N / rgroup<double>();
+    const size_t rows_b = (size_t)gd.ng * g.P * cgroup_bytes<double>();
+    const size_t spec_b = (size_t)gd.ng * gd.rows * cgroup_bytes<double>();
+    const size_t wh_off = align256(std::max(rows_b, spec_b));
+    const size_t wh_b = (size_t)gd.ng * g.P * cgroup_bytes<double>();
+    const size_t avail = H->L.off[R_OUT] - H->L.off[R_V1];
+    if (wh_off + wh_b > avail) {
+        H->err = "internal: FP64 staging of B_w V^0 does not fit";
+        return PIDE2D_ERR_STATE;
+    }
+    char* base = (char*)H->field(1);
+    void* S64 = base;
+    void* Wh64 = base + wh_off;
+    double* V64 = H->at<double>(R_OUT);
+    const void* twd = H->at<void>(R_TWD);
+    // conj(w^)/P^2 in FP64 (eq. 3.13), as weight_spectrum with an FP64 output
+    Geometry gw = gd;
+    gw.rows = g.P;
+    FwdArgs<double> wa{};
+    wa.g = gw;
+    wa.mode = FWD_WEIGHTS;
+    wa.omega = H->at<double>(R_OMEGA);
+    wa.S = S64;
+    wa.pair0 = 0;
+    wa.npairs = N / 2;
+    wa.tw = twd;
+    PIDE_CUDA(launch_row_forward<double>(wa, s));
+    PIDE_CUDA(launch_weights_col<double>(gw, S64, Wh64, nullptr, twd, s));
+    // V^0 in FP64 (the values field 0 holds as double-float pairs)
+    const double* dgl = H->at<double>(R_GL);
+    const double* glp = dgl + 2 * (kGlNear + kGlFar + kGlEdge);
+    PIDE_CUDA(launch_payoff<double>(gd, H->at<double>(R_E1D), H->at<double>(R_E2D), H->s_lo1, H->s_lo2, H->h,
+                                    H->contract.strike, H->contract.payoff, glp, glp + kGlPay, kGlPay, V64, s));
+    FwdArgs<double> fa{};
+    fa.g = gd;
+    fa.mode = FWD_FULL;
+    fa.Y = V64;
+    fa.E1 = H->at<double>(R_E1D);
+    fa.E2 = H->at<double>(R_E2D);
+    fa.Kd = H->contract.strike;
+    fa.payoff = H->contract.payoff;
+    fa.S = S64;
+    fa.pair0 = 0;
+    fa.npairs = N + 1;
+    fa.tw = twd;
+    PIDE_CUDA(launch_row_forward<double>(fa, s));
+    ColArgs<double> ca{};
+    ca.g = gd;
+    ca.mode = COL_FULL;
+    ca.S = S64;
+    ca.Wh = Wh64;
+    ca.rlo = 0;
+    ca.rhi = g.P + 2;
+    ca.tw = twd;
+    PIDE_CUDA(launch_col<double>(ca, s));
+    InvArgs<double> ia{};
+    ia.g = gd;
+    ia.mode = INV_OUT;
+    ia.do_resid = 0;
+    ia.S = S64;
+    ia.out = V64;                  // the interior nodes of V^0 are read before this pass
+    ia.tw = twd;
+    PIDE_CUDA(launch_row_inverse<double>(ia, s));
+    PIDE_CUDA(launch_state_from_double<float>(g, V64, g.ldS, (St<float>*)H->field(H->bv), s));
+    PIDE_CUDA(cudaMemsetAsync(H->field(1), 0, H->L.off[R_BV] - H->L.off[R_V1], s));
+    PIDE_CUDA(cudaMemsetAsync(H->field(6), 0, H->L.off[R_RES] - H->L.off[R_BY], s));
+    return PIDE2D_OK;
+}
+
 template <typename R>
 static pide2d_status do_create(pide2d* H) {
     const Geometry g = H->L.g;
@@ -1004,6 +1110,12 @@ static pide2d_status do_create(pide2d* H) {
     PIDE_CUDA(launch_payoff<R>(g, H->at<double>(R_E1D), H->at<double>(R_E2D), H->s_lo1, H->s_lo2, H->h,
                                H->contract.strike, H->contract.payoff, glp, glp + kGlPay, kGlPay,
                                (St<R>*)H->field(0), s));
+    if constexpr (sizeof(R) == 4) {
+        const pide2d_status bs = bv0_fp64(H);
+        if (bs != PIDE2D_OK) return bs;
+        PIDE_CUDA(cudaStreamSynchronize(s));
+        return PIDE2D_OK;
+    }
     FwdArgs<R> fa{};
     fa.g = g;
     fa.mode = FWD_FULL;
@@ -1083,6 +1195,65 @@ static pide2d_status do_apply_jump(pide2d* H, const double* U, double tau, int f
     PIDE_CUDA(cudaMemcpy2DAsync(out + (N + 1) + 1, (size_t)(N + 1) * 8, OUT + g.ldS + 1, (size_t)g.ldS * 8,
                                 (size_t)(N - 1) * 8, N - 1, cudaMemcpyDefault, s));
     PIDE_CUDA(cudaStreamSynchronize(s));
+    return PIDE2D_OK;
+}
+
+// One iteration of the increment loop on a caller residual (pide2d_iteration_probe):
+// the DST solve of the non-mixed operator, the increment's B_w sweep and the
+// eq. 3.25 quantity, through the kernels and launch shapes of the time loop.
+// Scratch: R_OUT (the residual in FP64), R_X (Y, from zero), R_W (B_w Y, from
+// zero); W is rebuilt at the start of every theta step, so a probe between
+// steps does not disturb the time loop.
+template <typename R>
+static pide2d_status do_iteration_probe(pide2d* H, const double* r, double ht, double theta, double* delta_out,
+                                        double* bdelta_out, double* stop_out) {
+    const Geometry g = H->L.g;
+    const int N = g.N;
+    cudaStream_t s = H->stream;
+    double* OUT = H->at<double>(R_OUT);
+    St<R>* Y = H->at<St<R>>(R_X);
+    St<R>* BY = H->at<St<R>>(R_W);
+    PIDE_CUDA(cudaMemcpy2DAsync(OUT, (size_t)g.ldS * 8, r, (size_t)(N + 1) * 8, (size_t)(N + 1) * 8, N + 1,
+                                cudaMemcpyDefault, s));
+    PIDE_CUDA(launch_row_dst<R>(g, OUT, H->at<R>(R_E), H->at<void>(R_TWR), s));
+    PIDE_CUDA(cudaMemsetAsync(Y, 0, H->L.size[R_X], s));
+    PIDE_CUDA(cudaMemsetAsync(BY, 0, H->L.size[R_W], s));
+    SolveSpec<R> sp{};
+    sp.Y = Y;
+    sp.BY = BY;
+    sp.W = BY;
+    sp.far = 0;
+    sp.Kd = 0.0;
+    sp.Wh = H->at<void>(R_WH);
+    sp.Whi = H->at<void>(R_WHI);
+    sp.theta = theta;
+    sp.ht = ht;
+    sp.step_end = 0;
+    sp.device_loop = false;
+    SolveArgs<R> A;
+    build_solve_args<R>(H, sp, &A);
+    PIDE_CUDA(launch_dst_col<R>(A.da, s));
+    PIDE_CUDA(cudaMemsetAsync(H->at<void>(R_RESID), 0, 16, s));
+    PIDE_CUDA(launch_dst_row<R>(A.ra, s));
+    PIDE_CUDA(launch_col<R>(A.cai, s));
+    A.iai.do_resid = 1;
+    PIDE_CUDA(launch_row_inverse<R>(A.iai, s));
+    // Y = 0 + delta exactly, B_w Y = 0 + B_w delta exactly
+    const size_t ldo = (size_t)(N + 1) * 8;
+    if (delta_out) {
+        PIDE_CUDA(launch_state_to_double<R>(g, Y, OUT, g.ldS, s));
+        PIDE_CUDA(cudaMemcpy2DAsync(delta_out + (N + 1) + 1, ldo, OUT + g.ldS + 1, (size_t)g.ldS * 8,
+                                    (size_t)(N - 1) * 8, N - 1, cudaMemcpyDefault, s));
+    }
+    if (bdelta_out) {
+        PIDE_CUDA(launch_state_to_double<R>(g, BY, OUT, g.ldS, s));
+        PIDE_CUDA(cudaMemcpy2DAsync(bdelta_out + (N + 1) + 1, ldo, OUT + g.ldS + 1, (size_t)g.ldS * 8,
+                                    (size_t)(N - 1) * 8, N - 1, cudaMemcpyDefault, s));
+    }
+    double stop = 0.0;
+    PIDE_CUDA(cudaMemcpyAsync(&stop, H->at<void>(R_RESID), 8, cudaMemcpyDeviceToHost, s));
+    PIDE_CUDA(cudaStreamSynchronize(s));
+    if (stop_out) *stop_out = stop;
     return PIDE2D_OK;
 }
 
@@ -2340,6 +2511,19 @@ pide2d_status pide2d_apply_jump(pide2d_t* H, const double* U, double tau, int fa
                                             : do_apply_jump<float>(H, U, tau, far_field, out);
 }
 
+pide2d_status pide2d_iteration_probe(pide2d_t* H, const double* r, double ht, double theta, double* delta_out,
+                                     double* bdelta_out, double* stop_out) {
+    if (!H || !r) return PIDE2D_ERR_ARG;
+    if (H->broken) return PIDE2D_ERR_STATE;
+    if (!(ht > 0.0) || !(theta > 0.0) || !(theta <= 1.0)) {
+        H->err = "iteration probe: ht must be > 0 and theta in (0, 1]";
+        return PIDE2D_ERR_ARG;
+    }
+    return H->grid.precision == PIDE2D_FP64
+               ? do_iteration_probe<double>(H, r, ht, theta, delta_out, bdelta_out, stop_out)
+               : do_iteration_probe<float>(H, r, ht, theta, delta_out, bdelta_out, stop_out);
+}
+
 pide2d_status pide2d_profile(pide2d_t* H, int enable) {
     if (!H) return PIDE2D_ERR_ARG;
     if (enable) {
@@ -2406,6 +2590,89 @@ pide2d_status pide2d_adjoint(pide2d_t* H, const pide2d_model* dirs, int ndirs, d
     }
     return H->grid.precision == PIDE2D_FP64 ? do_adjoint<double>(H, dirs, ndirs, grad)
                                             : do_adjoint<float>(H, dirs, ndirs, grad);
+}
+
+// ---------------------------------------------------------------------------
+// workload parameterisation (Appendix A, Table A5): a unit-mean tempered-
+// stable subordinator with variance kappa time-changes a Brownian motion with
+// drift beta and covariance [[s1^2, c s1 s2], [c s1 s2, s2^2]]
+// ---------------------------------------------------------------------------
+static std::string check_workload(const pide2d_workload* w) {
+    if (!w) return "workload is NULL";
+    if (!(w->alpha >= 0.0 && w->alpha < 1.0)) return "workload.alpha must lie in [0, 1)";
+    if (!(w->kappa > 0.0) || !std::isfinite(w->kappa)) return "workload.kappa must be positive";
+    if (!(w->sigma[0] > 0.0) || !(w->sigma[1] > 0.0) || !std::isfinite(w->sigma[0]) || !std::isfinite(w->sigma[1]))
+        return "workload.sigma must be positive";
+    if (!(std::fabs(w->corr) < 1.0)) return "workload.corr must lie in (-1, 1)";
+    if (!std::isfinite(w->beta[0]) || !std::isfinite(w->beta[1]) || !std::isfinite(w->r))
+        return "workload.beta and r must be finite";
+    return "";
+}
+
+pide2d_status pide2d_model_from_workload(const pide2d_workload* w, pide2d_model* out) {
+    const std::string e = check_workload(w);
+    if (!e.empty() || !out) {
+        pide::set_global_error(e.empty() ? "model is NULL" : e);
+        return PIDE2D_ERR_ARG;
+    }
+    // Table A5: E G(1) = delta Gamma(1 - alpha) / lambda^(1 - alpha) = 1 and
+    // V G(1) / E G(1) = (1 - alpha) / lambda = kappa
+    const double lam = (1.0 - w->alpha) / w->kappa;
+    std::memset(out, 0, sizeof *out);
+    out->alpha = w->alpha;
+    out->lambda = lam;
+    out->delta = std::pow(lam, 1.0 - w->alpha) / std::tgamma(1.0 - w->alpha);
+    out->eta[0] = w->beta[0];
+    out->eta[1] = w->beta[1];
+    const double s1 = w->sigma[0], s2 = w->sigma[1];
+    out->rho[0] = s1 * s1;
+    out->rho[1] = w->corr * s1 * s2;
+    out->rho[2] = s2 * s2;
+    out->r = w->r;
+    return PIDE2D_OK;
+}
+
+pide2d_status pide2d_workload_directions(const pide2d_workload* w, pide2d_model* dirs) {
+    pide2d_model m;
+    const pide2d_status st = pide2d_model_from_workload(w, &m);
+    if (st != PIDE2D_OK) return st;
+    if (!dirs) {
+        pide::set_global_error("dirs is NULL");
+        return PIDE2D_ERR_ARG;
+    }
+    std::memset(dirs, 0, 6 * sizeof *dirs);
+    const double s1 = w->sigma[0], s2 = w->sigma[1], c = w->corr;
+    dirs[0].rho[0] = 2.0 * s1;                   // sigma1
+    dirs[0].rho[1] = c * s2;
+    dirs[1].rho[1] = c * s1;                     // sigma2
+    dirs[1].rho[2] = 2.0 * s2;
+    dirs[2].rho[1] = s1 * s2;                    // corr
+    // kappa: d lambda / d kappa = -lambda / kappa, d delta / d kappa = -(1 - alpha) delta / kappa
+    dirs[3].lambda = -m.lambda / w->kappa;
+    dirs[3].delta = -(1.0 - w->alpha) * m.delta / w->kappa;
+    dirs[4].eta[0] = 1.0;                        // beta1
+    dirs[5].eta[1] = 1.0;                        // beta2
+    return PIDE2D_OK;
+}
+
+pide2d_status pide2d_adjoint_workload(pide2d_t* H, const pide2d_workload* w, double* grad) {
+    if (!H || !grad) return PIDE2D_ERR_ARG;
+    pide2d_model m, dirs[6];
+    if (pide2d_workload_directions(w, dirs) != PIDE2D_OK || pide2d_model_from_workload(w, &m) != PIDE2D_OK) {
+        H->err = g_create_error;
+        return PIDE2D_ERR_ARG;
+    }
+    // the handle must price this workload's model
+    auto close = [](double a, double b) { return std::fabs(a - b) <= 1e-12 * std::max(1.0, std::fabs(b)); };
+    const pide2d_model& hm = H->model;
+    const bool same = close(hm.alpha, m.alpha) && close(hm.delta, m.delta) && close(hm.lambda, m.lambda) &&
+                      close(hm.eta[0], m.eta[0]) && close(hm.eta[1], m.eta[1]) && close(hm.rho[0], m.rho[0]) &&
+                      close(hm.rho[1], m.rho[1]) && close(hm.rho[2], m.rho[2]) && close(hm.r, m.r);
+    if (!same) {
+        H->err = "pide2d_adjoint_workload: the handle was not created with this workload's model";
+        return PIDE2D_ERR_ARG;
+    }
+    return pide2d_adjoint(H, dirs, 6, grad);
 }
 
 pide2d_status pide2d_price_sinh_grid(int nx, double strike, double x_max, double z_iii, double frac,

@@ -25,7 +25,7 @@ template <typename R> constexpr size_t rgroup_bytes() { return (size_t)rgroup<R>
 // spectrum column groups of a length-P transform (P/2 + 1 columns)
 template <typename R> constexpr int spectrum_groups(int P) { return (P / 2 + 1 + cgroup<R>() - 1) / cgroup<R>(); }
 
-enum FwdMode { FWD_FULL = 0, FWD_FULL0 = 1, FWD_INCR = 2, FWD_WEIGHTS = 3 };
+enum FwdMode { FWD_FULL = 0, FWD_FULL0 = 1, FWD_INCR = 2, FWD_WEIGHTS = 3, FWD_DIFF = 4 };
 enum ColMode { COL_FULL = 0, COL_INCR = 1 };
 enum InvMode { INV_FULL = 0, INV_INCR = 1, INV_OUT = 2 };
 
@@ -42,11 +42,13 @@ struct Geometry {
 template <typename R> struct FwdArgs {
     Geometry g;
     int mode;
-    const St<R>* Y;          // FULL/FULL0: field whose interior is transformed
+    const St<R>* Y;          // FULL/FULL0/DIFF: field whose interior is transformed
+    const St<R>* Yref;       // DIFF: the interior transformed is Y - Yref
     const R* D;              // INCR: increment field (ring zero)
     const double* omega;     // WEIGHTS: N x N weights [l2][l1]
     const R* E1; const R* E2;// e^{s_m} tables (transform precision)
     R Kd;                    // K e^{-r tau} for the far field
+    R Kd_prev, dKd;          // DIFF: the halo is g(tau) - g(tau_prev); dKd = Kd - Kd_prev (rounded from FP64)
     int payoff;
     void* S;                 // spectrum out (cpx<R>, or cpx<double> for WEIGHTS)
     int pair0, npairs;       // row pairs (rho = 2 (pair0 + p), +1)
@@ -68,14 +70,16 @@ template <typename R> struct InvArgs {
     int do_resid;
     const int* conv_flag;    // device flag; when set, do_resid = !*conv_flag (device-side loop)
     const void* S;
-    St<R>* BY;               // FULL: set, INCR: accumulate
+    St<R>* BY;               // FULL: set (BV + the sweep when BV is given), INCR: accumulate
+    const St<R>* BV;         // FULL: B_w V^{n-1} when the sweep transformed Y - V^{n-1} (else NULL)
     St<R>* const* BYind;     // device-side loop: BY is read from *BYind
     double* out;             // OUT: plain FP64 result field (pitch ldS)
     const St<R>* Y;          // FULL: Y^0 (with ring)
     const St<R>* W;          // FULL: W
-    R* r;                    // residual field (R)
+    R* r;                    // (unused) residual field
     const R* D;              // INCR: increment field
     R htt, cid, d11, d22, d12, rw;   // h_t theta, 1 + h_t theta r_w, a11/(2h^2), a22/(2h^2), a12/(4h^2), r_w
+    R rw_lo;                 // r_w - rw (the low part of r_w in the transform precision)
     R* E;                    // DST rows output
     const void* tw;
 };
@@ -94,7 +98,7 @@ template <typename R> struct DstRowArgs {
     St<R>* Y;
     St<R>* const* Yind;      // device-side loop: Y is read from *Yind (set per step on the device)
     R* D;                    // increment out (interior)
-    void* resid;             // R-typed max |D| / max(1, |Y|) as unsigned bits
+    void* resid;             // FP64 max of |D| / max(1, |Y|) (eq. 3.25), as unsigned 64-bit bits
     void* S;                 // spectrum rows of the increment (R2C), cpx<R>
     const void* tw;
 };
@@ -109,6 +113,7 @@ template <typename R> struct PrepArgs {
     R* cz;                   // Z - V at interior nodes (R field, pitch ldR)
     R htm;                   // h_t (1 - theta)
     R rw, d11, d22, d12;     // r_w and D coefficients
+    R rw_lo;                 // r_w - rw
     int o1, o2, nt;          // SL: first tap offsets, taps per axis (2 or 4)
     R w1[4], w2[4];          // SL weights per axis
     const double* E1d; const double* E2d;   // e^{s} in FP64
@@ -141,6 +146,9 @@ template <typename R> cudaError_t launch_row_inverse(const InvArgs<R>& a, cudaSt
 template <typename R> cudaError_t launch_dst_col(const DstColArgs<R>& a, cudaStream_t s);
 template <typename R> cudaError_t launch_dst_row(const DstRowArgs<R>& a, cudaStream_t s);
 template <typename R> cudaError_t launch_prep(const PrepArgs<R>& a, cudaStream_t s);
+// row DST-I of an FP64 interior field (pitch g.ldS) into the DST buffer E
+template <typename R> cudaError_t launch_row_dst(const Geometry& g, const double* src, R* E, const void* tw,
+                                                cudaStream_t s);
 // the same kernels over K jobs of one geometry (a0: any job's arguments, for the launch shape)
 template <typename R> cudaError_t launch_row_forward_jobs(const FwdArgs<R>& a0, const FwdArgs<R>* arr, int K,
                                                          JobsCtl jc, cudaStream_t s);
@@ -254,7 +262,7 @@ cudaError_t launch_fp_tally(FpCtl* ctl, cudaStream_t s);
 
 // multi-job loop control (loop_ctl.cu)
 struct JobCheck {
-    const void* resid;       // the job's R-typed eq. 3.25 maximum (reset to 0 after each read)
+    const void* resid;       // the job's FP64 eq. 3.25 maximum (reset to 0 after each read)
     double tol;
     int kmax;
     int pad;

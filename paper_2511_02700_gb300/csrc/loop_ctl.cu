@@ -15,10 +15,12 @@
 
 namespace pide {
 
+// resid: the FP64 eq. 3.25 quantity of the iteration (written by k_dst_row in
+// both precisions)
 template <typename R>
-__global__ void k_fp_check(const R* resid, FpCtl* c, double tol, int kmax, cudaGraphConditionalHandle h) {
+__global__ void k_fp_check(const double* resid, FpCtl* c, double tol, int kmax, cudaGraphConditionalHandle h) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const double r = (double)*resid;
+    const double r = *resid;
     const int k = c->k + 1;
     c->k = k;
     const bool conv = r < tol;
@@ -53,7 +55,7 @@ __global__ void k_fp_tally(FpCtl* c) {
 template <typename R>
 cudaError_t launch_fp_check(const void* resid, FpCtl* ctl, double tol, int kmax, unsigned long long cond_handle,
                             cudaStream_t s) {
-    k_fp_check<R><<<1, 32, 0, s>>>((const R*)resid, ctl, tol, kmax, (cudaGraphConditionalHandle)cond_handle);
+    k_fp_check<R><<<1, 32, 0, s>>>((const double*)resid, ctl, tol, kmax, (cudaGraphConditionalHandle)cond_handle);
     return cudaGetLastError();
 }
 
@@ -77,7 +79,7 @@ __global__ void k_jobs_reset(int K, const JobCheck* jc, JobsState st) {
         st.conv[j] = 0;
         st.kconv[j] = 0;
         st.kcount[j] = 0;
-        *(R*)jc[j].resid = R(0);
+        *(double*)jc[j].resid = 0.0;
     }
 }
 
@@ -89,9 +91,9 @@ __global__ void k_jobs_check(int K, const JobCheck* jc, JobsState st, int iter) 
     int mine = 0;
     for (int j = threadIdx.x; j < K; j += blockDim.x) {
         if (st.conv[j]) continue;
-        R* rp = (R*)jc[j].resid;
-        const double r = (double)*rp;
-        *rp = R(0);                         // the next iteration's maximum starts from zero
+        double* rp = (double*)jc[j].resid;
+        const double r = *rp;
+        *rp = 0.0;                          // the next iteration's maximum starts from zero
         st.kcount[j] = iter;
         st.last[j] = r;
         const bool ok = r < jc[j].tol;

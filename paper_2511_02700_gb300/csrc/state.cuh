@@ -41,12 +41,42 @@ template <typename S, typename R> __device__ __forceinline__ S st_from_r(R v);
 template <> __device__ __forceinline__ float2 st_from_r<float2, float>(float v) { return make_float2(v, 0.f); }
 template <> __device__ __forceinline__ double st_from_r<double, double>(double v) { return v; }
 
+// B_w V - r_w V at a node, from the state values bv = (B_w V)(s) and v = V(s)
+// and r_w = rh + rl.  Both products are ~sum(w) |V|, so in FP32-bulk mode the
+// difference is formed in double-float arithmetic: rh * v.x = p + pe exactly
+// (FMA), and bv.x - p is exact when the two are within a factor of two
+// (Sterbenz), which is the cancelling case.
+__device__ __forceinline__ float jump_gen(float2 bv, float2 v, float rh, float rl) {
+    const float p = rh * v.x;
+    const float pe = fmaf(rh, v.x, -p);
+    const float t = bv.x - p;
+    return t + ((bv.y - pe) - (rh * v.y + rl * v.x));
+}
+__device__ __forceinline__ double jump_gen(double bv, double v, double rh, double rl) { return bv - (rh + rl) * v; }
+
 // far field g(s, tau): the payoff with the strike discounted, Kd = K e^{-r tau}
 template <typename R>
 __device__ __forceinline__ R far_value(int payoff, R Kd, R e1, R e2) {
     if (payoff == 0) return fmax(Kd - R(0.5) * (e1 + e2), R(0));
     if (payoff == 1) return fmax(R(0.5) * (e1 + e2) - Kd, R(0));
     return fmax(Kd - e1, R(0));
+}
+
+// g(s, tau) - g(s, tau_prev) with k0 = K e^{-r tau}, k1 = K e^{-r tau_prev} and
+// dk = k0 - k1 rounded once from FP64: piecewise in the payoff's argument a,
+// so no difference of two nearby far-field values is rounded
+template <typename R>
+__device__ __forceinline__ R far_diff(int payoff, R k0, R k1, R dk, R e1, R e2) {
+    const R a = payoff == 2 ? e1 : R(0.5) * (e1 + e2);
+    const R lo = fmin(k0, k1), hi = fmax(k0, k1);
+    if (payoff == 1) {                      // call: max(a - k, 0)
+        if (a <= lo) return R(0);
+        if (a >= hi) return -dk;
+        return k0 < k1 ? a - k0 : k1 - a;
+    }
+    if (a >= hi) return R(0);               // puts: max(k - a, 0)
+    if (a <= lo) return dk;
+    return k0 > k1 ? k0 - a : a - k1;
 }
 
 }  // namespace pide

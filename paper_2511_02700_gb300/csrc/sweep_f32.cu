@@ -11,6 +11,7 @@ namespace pide {
     template cudaError_t launch_dst_col<R>(const DstColArgs<R>&, cudaStream_t);                     \
     template cudaError_t launch_dst_row<R>(const DstRowArgs<R>&, cudaStream_t);                     \
     template cudaError_t launch_prep<R>(const PrepArgs<R>&, cudaStream_t);                          \
+    template cudaError_t launch_row_dst<R>(const Geometry&, const double*, R*, const void*, cudaStream_t); \
     template cudaError_t launch_ps_tin<R>(int, int, int, const int*, const double*, const double*, R*, cudaStream_t); \
     template cudaError_t launch_ps_rows_fwd<R>(int, const R*, int, void*, const void*, cudaStream_t); \
     template cudaError_t launch_ps_col<R>(int, void*, const void*, int, int, const void*, cudaStream_t); \

@@ -51,6 +51,13 @@ __device__ __forceinline__ R node_value(const FwdArgs<R>& a, int m1, int m2) {
     const int N = a.g.N;
     const bool in = (m1 >= 1 && m1 <= N - 1 && m2 >= 1 && m2 <= N - 1);
     if (a.mode == FWD_INCR) return in ? a.D[(size_t)m2 * a.g.ldR + m1] : R(0);
+    if (a.mode == FWD_DIFF) {
+        if (in) {
+            const size_t idx = (size_t)m2 * a.g.ldS + m1;
+            return st_diff(a.Y[idx], a.Yref[idx]);
+        }
+        return far_diff<R>(a.payoff, a.Kd, a.Kd_prev, a.dKd, a.E1[m1 + a.g.eoff], a.E2[m2 + a.g.eoff]);
+    }
     if (in) return st_r(a.Y[(size_t)m2 * a.g.ldS + m1]);
     if (a.mode == FWD_FULL0) return R(0);
     return far_value<R>(a.payoff, a.Kd, a.E1[m1 + a.g.eoff], a.E2[m2 + a.g.eoff]);
@@ -78,15 +85,23 @@ __device__ __forceinline__ R mixed_plain(const R* D, size_t idx, int ld) {
     return (D[idx + ld + 1] - D[idx - ld + 1]) - (D[idx + ld - 1] - D[idx - ld - 1]);
 }
 
-template <typename R> struct ResidAtomic;
-template <> struct ResidAtomic<float> {
-    static __device__ void max(void* p, float v) { atomicMax((unsigned int*)p, __float_as_uint(v)); }
+// |d| / max(1, |y|) to select the node of a block's eq. 3.25 maximum: in FP32
+// the fast division (2 ulp; max(1, |y|) stays far below 2^126), since the
+// selected node is evaluated again in FP64; in FP64 the exact quotient
+__device__ __forceinline__ float stop_ratio(float d, float y) { return __fdividef(fabsf(d), fmaxf(1.f, fabsf(y))); }
+__device__ __forceinline__ double stop_ratio(double d, double y) { return fabs(d) / fmax(1.0, fabs(y)); }
+
+// a warp's candidate for the eq. 3.25 maximum (shared-memory reduction slot)
+struct StopCand {
+    double q;      // its ratio in the transform precision (-1: no node)
+    double v;      // its ratio in FP64
+    int bad;       // a non-finite ratio or state was seen
+    int pad;
 };
-template <> struct ResidAtomic<double> {
-    static __device__ void max(void* p, double v) {
-        atomicMax((unsigned long long*)p, (unsigned long long)__double_as_longlong(v));
-    }
-};
+__device__ __forceinline__ float2 shfl_xor_state(float2 y, int o) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, y.x, o), __shfl_xor_sync(0xffffffffu, y.y, o));
+}
+__device__ __forceinline__ double shfl_xor_state(double y, int o) { return __shfl_xor_sync(0xffffffffu, y, o); }
 
 template <typename K>
 void set_smem(K kernel, size_t bytes) {
@@ -272,6 +287,7 @@ __device__ __forceinline__ void prefetch_inverse_rows(const InvArgs<R>& a, const
     } else if (a.mode == INV_FULL && do_resid) {
         l2_prefetch(a.W + (size_t)m2 * ld, (size_t)nr * ld * sizeof(S_));
         l2_prefetch(a.Y + (size_t)lo * ld, (size_t)(hi - lo + 1) * ld * sizeof(S_));
+        if (a.BV) l2_prefetch(a.BV + (size_t)m2 * ld, (size_t)nr * ld * sizeof(S_));
     }
 }
 
@@ -343,17 +359,27 @@ __device__ __forceinline__ void row_inverse_body(const InvArgs<R>& a) {
                 if (a.mode == INV_OUT) {
                     a.out[idx] = (double)zv;
                 } else if (a.mode == INV_FULL) {
-                    BYv[idx] = st_from_r<S_, R>(zv);
-                    if (do_resid) {
-                        const S_ y = a.Y[idx];
-                        rr[half] = st_diff(a.W[idx], y) + a.htt * zv - a.htt * a.rw * st_r(y)
-                                   + a.htt * diff_state(a.Y, idx, ld, a.d11, a.d22, a.d12);
+                    if (a.BV) {
+                        // the sweep transformed Y - V^{n-1}: B_w Y = B_w V^{n-1} + zv
+                        const S_ bv = a.BV[idx];
+                        BYv[idx] = st_add(bv, zv);
+                        if (do_resid) {
+                            const S_ y = a.Y[idx];
+                            rr[half] = st_diff(a.W[idx], y) + a.htt * (jump_gen(bv, y, a.rw, a.rw_lo) + zv)
+                                       + a.htt * diff_state(a.Y, idx, ld, a.d11, a.d22, a.d12);
+                        }
+                    } else {
+                        BYv[idx] = st_from_r<S_, R>(zv);
+                        if (do_resid) {
+                            const S_ y = a.Y[idx];
+                            rr[half] = st_diff(a.W[idx], y) + a.htt * zv - a.htt * a.rw * st_r(y)
+                                       + a.htt * diff_state(a.Y, idx, ld, a.d11, a.d22, a.d12);
+                        }
                     }
                 } else {  // INV_INCR
                     BYv[idx] = st_add(BYv[idx], zv);
                     if (do_resid) rr[half] = a.htt * (zv + a.d12 * mixed_plain(a.D, idr, ldR));
                 }
-                if (do_resid) a.r[idr] = rr[half];
             }
         }
         if (do_resid) {
@@ -463,7 +489,7 @@ __device__ __forceinline__ void dst_row_body(const DstRowArgs<R>& a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int unit = threadIdx.x / NT, t = threadIdx.x - unit * NT;
     C* buf = reinterpret_cast<C*>(smem_raw) + (size_t)unit * CF::ULEN;
-    R* red = reinterpret_cast<R*>(reinterpret_cast<C*>(smem_raw) + (size_t)CF::UNITS * CF::ULEN);
+    StopCand* red = reinterpret_cast<StopCand*>(reinterpret_cast<C*>(smem_raw) + (size_t)CF::UNITS * CF::ULEN);
     const int p = blockIdx.x * CF::UNITS + unit;
     const int m2 = 2 * p + 1;
     const bool valid = m2 <= N - 1;
@@ -491,7 +517,14 @@ __device__ __forceinline__ void dst_row_body(const DstRowArgs<R>& a) {
         return i <= N ? e : mk<R>(-e.x, -e.y);
     };
     St<R>* const Yv = a.Yind ? *a.Yind : a.Y;
-    R rmax = 0;
+    // eq. 3.25: the thread's largest ratio |D| / max(1, |Y|) in the transform
+    // precision selects a node, whose D and Y are kept; the block's selected
+    // node is evaluated again in FP64 below, and that FP64 value is what the
+    // stopping rule compares with tol.  A NaN ratio or Y marks the block
+    // non-finite.
+    R qmax = R(-1), dsel = R(0);
+    St<R> ysel = st_from_r<St<R>, R>(R(0));
+    bool bad = false;
     const int ld = a.g.ldS, ldR = a.g.ldR;
     // the state rows updated after the DST arrive in L2 while it runs
     if (t == 0 && valid) l2_prefetch(Yv + (size_t)m2 * ld, (size_t)(hasb ? 2 : 1) * ld * sizeof(St<R>));
@@ -506,7 +539,10 @@ __device__ __forceinline__ void dst_row_body(const DstRowArgs<R>& a) {
                 const St<R> y = st_add(Yv[idx], da);
                 Yv[idx] = y;
                 a.D[(size_t)m2 * ldR + m1] = da;
-                rmax = fmax(rmax, fabs(da) / fmax(R(1), fabs(st_r(y))));
+                const R yr = st_r(y);
+                const R q = stop_ratio(da, yr);
+                bad |= !(q == q) || !(yr == yr);
+                if (q > qmax) { qmax = q; dsel = da; ysel = y; }
             }
             if (hasb) {
                 db = R(0.5) * zz.x;
@@ -514,12 +550,44 @@ __device__ __forceinline__ void dst_row_body(const DstRowArgs<R>& a) {
                 const St<R> y = st_add(Yv[idx], db);
                 Yv[idx] = y;
                 a.D[(size_t)(m2 + 1) * ldR + m1] = db;
-                rmax = fmax(rmax, fabs(db) / fmax(R(1), fabs(st_r(y))));
+                const R yr = st_r(y);
+                const R q = stop_ratio(db, yr);
+                bad |= !(q == q) || !(yr == yr);
+                if (q > qmax) { qmax = q; dsel = db; ysel = y; }
             }
         }
         buf[padi((m1 + N / 2 + 1) & (P - 1))] = mk<R>(da, db);
     };
     block_fft<R, -1, P>(buf, t, tw, load, update);
+    // (reduced here, before the second transform, so the candidate's registers
+    // are free during it)
+    // block maximum of eq. 3.25 in FP64, one atomic per block: each warp's
+    // node with the largest ratio in the transform precision is re-evaluated
+    // in FP64 from its D and Y (as stored), and the block keeps the FP64 value
+    // of the warp with the largest transform-precision ratio.  With FP32
+    // ratios (two roundings of Y, 2 ulp of the quotient) the FP64 value found
+    // is within 2^-20 relative of the exact FP64 maximum.
+    for (int o = 16; o > 0; o >>= 1) {
+        const R oq = __shfl_xor_sync(0xffffffffu, qmax, o);
+        const R od = __shfl_xor_sync(0xffffffffu, dsel, o);
+        const St<R> oy = shfl_xor_state(ysel, o);
+        if (oq > qmax) { qmax = oq; dsel = od; ysel = oy; }
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
+    if (lane == 0) red[warp] = StopCand{(double)qmax, fabs((double)dsel) / fmax(1.0, fabs(st_dbl(ysel))), bad ? 1 : 0};
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        StopCand c = red[0];
+        for (int w = 1; w < nwarp; ++w) {
+            const StopCand o = red[w];
+            if (o.q > c.q) { c.q = o.q; c.v = o.v; }
+            c.bad |= o.bad;
+        }
+        // +inf for a non-finite block: the loop stops, not converged
+        const double v = c.bad ? __longlong_as_double(0x7ff0000000000000LL) : (c.q >= 0.0 ? c.v : 0.0);
+        atomicMax((unsigned long long*)a.resid, (unsigned long long)__double_as_longlong(v));
+    }
     // packed R2C of the two increment rows -> spectrum rows rho = m2 + N/2 + 1, +1
     // (the midpoint interpolation is a factor of the increment weight spectrum)
     block_fft<R, -1, P>(buf, t, tw, SmemLoad<R>{buf}, SmemStore<R>{buf});
@@ -546,16 +614,6 @@ __device__ __forceinline__ void dst_row_body(const DstRowArgs<R>& a) {
             }
         }
     }
-    // block maximum, one atomic per block
-    for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
-    if (lane == 0) red[warp] = rmax;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        R m = 0;
-        for (int w = 0; w < nwarp; ++w) m = fmax(m, red[w]);
-        ResidAtomic<R>::max(a.resid, m);
-    }
 }
 template <typename R, int P>
 PIDE_FFT_KERNEL(R, P) k_dst_row(const __grid_constant__ DstRowArgs<R> a) { dst_row_body<R, P>(a); }
@@ -563,6 +621,47 @@ template <typename R, int P>
 PIDE_FFT_KERNEL(R, P) k_dst_row_jobs(const DstRowArgs<R>* __restrict__ arr, JobsCtl jc) {
     if (jc.skip(blockIdx.y)) return;
     dst_row_body<R, P>(arr[blockIdx.y]);
+}
+
+// ---------------------------------------------------------------------------
+// row DST-I of an FP64 interior field into the DST buffer E: the same
+// transform k_row_inverse applies to the residual before the column DST, here
+// for a residual handed in by the caller (pide2d_iteration_probe)
+// ---------------------------------------------------------------------------
+template <typename R, int P>
+PIDE_FFT_KERNEL(R, P) k_row_dst(Geometry g, const double* __restrict__ src, R* __restrict__ E, const void* twv) {
+    using C = cpx<R>;
+    using CF = Cfg<R, P>;
+    constexpr int NT = CF::NT, N = P / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int unit = threadIdx.x / NT, t = threadIdx.x - unit * NT;
+    C* buf = reinterpret_cast<C*>(smem_raw) + (size_t)unit * CF::ULEN;
+    const int p = blockIdx.x * CF::UNITS + unit;
+    const int m2 = 2 * p + 1;
+    const bool valid = m2 <= N - 1;
+    const bool hasb = valid && (m2 + 1 <= N - 1);
+    const C* tw = (const C*)twv;
+    // odd extension of rows m2, m2 + 1 packed into one complex sequence
+    auto load = [&](int i) -> C {
+        const int j = i <= N ? i : P - i;
+        const R sg = i <= N ? R(1) : R(-1);
+        R xa = 0, xb = 0;
+        if (j >= 1 && j <= N - 1) {
+            if (valid) xa = sg * (R)src[(size_t)m2 * g.ldS + j];
+            if (hasb) xb = sg * (R)src[(size_t)(m2 + 1) * g.ldS + j];
+        }
+        return mk<R>(xa, xb);
+    };
+    constexpr int GE = rgroup<R>();
+    auto store_e = [&](int k, C zz) {
+        if (k >= N) return;
+        const int gE = k / GE, c = k - gE * GE;
+        const R va = k >= 1 ? R(-0.5) * zz.y : R(0);
+        const R vb = k >= 1 ? R(0.5) * zz.x : R(0);
+        if (valid) E[((size_t)gE * N + m2) * GE + c] = va;
+        if (hasb) E[((size_t)gE * N + m2 + 1) * GE + c] = vb;
+    };
+    block_fft<R, -1, P>(buf, t, tw, load, store_e);
 }
 
 // ---------------------------------------------------------------------------
@@ -587,7 +686,7 @@ __device__ __forceinline__ void explicit_body(const PrepArgs<R>& a) {
     const size_t idx = (size_t)m2 * ld + m1;
     const St<R>* V = a.V[0];
     a.cz[(size_t)m2 * a.g.ldR + m1] =
-        a.htm * (diff_state(V, idx, ld, a.d11, a.d22, a.d12) - a.rw * st_r(V[idx]) + st_r(a.BV[idx]));
+        a.htm * (diff_state(V, idx, ld, a.d11, a.d22, a.d12) + jump_gen(a.BV[idx], V[idx], a.rw, a.rw_lo));
 }
 
 template <typename R>
@@ -920,8 +1019,9 @@ __global__ void k_state_to_double(Geometry g, const St<R>* src, double* dst, int
         default: return cudaErrorInvalidValue;                                              \
     }
 
-// FP64 time-loop kernels exist up to P = 4096 (FP64 mode is limited to N <= 2048)
-template <typename R, int P> struct LoopSize { static constexpr bool ok = sizeof(R) == 4 || P <= 4096; };
+// time-loop kernels exist for every transform length in both precisions (an
+// 8192-point FP64 unit takes 139 KB of dynamic shared memory, one block per SM)
+template <typename R, int P> struct LoopSize { static constexpr bool ok = true; };
 
 template <typename R, int P, class K, class A>
 cudaError_t launch_fft_kernel(K kernel, const A& a, int work_units, size_t extra_smem, cudaStream_t s) {
@@ -977,7 +1077,7 @@ cudaError_t launch_dst_col_jobs(const DstColArgs<R>& a0, const DstColArgs<R>* ar
 template <typename R>
 cudaError_t launch_dst_row_jobs(const DstRowArgs<R>& a0, const DstRowArgs<R>* arr, int K, JobsCtl jc, cudaStream_t s) {
 #define CASE(PP)                                                                                             \
-    if constexpr (LoopSize<R, PP>::ok) return launch_fft_kernel_jobs<R, PP>(k_dst_row_jobs<R, PP>, arr, K, jc, PP / 4, 32 * sizeof(R), s); \
+    if constexpr (LoopSize<R, PP>::ok) return launch_fft_kernel_jobs<R, PP>(k_dst_row_jobs<R, PP>, arr, K, jc, PP / 4, 32 * sizeof(StopCand), s); \
     else return cudaErrorInvalidValue;
     PIDE_SWITCH_P(a0.g.P, CASE)
 #undef CASE
@@ -1029,9 +1129,21 @@ cudaError_t launch_dst_col(const DstColArgs<R>& a, cudaStream_t s) {
 template <typename R>
 cudaError_t launch_dst_row(const DstRowArgs<R>& a, cudaStream_t s) {
 #define CASE(PP)                                                                       \
-    if constexpr (LoopSize<R, PP>::ok) return launch_fft_kernel<R, PP>(k_dst_row<R, PP>, a, PP / 4, 32 * sizeof(R), s); \
+    if constexpr (LoopSize<R, PP>::ok) return launch_fft_kernel<R, PP>(k_dst_row<R, PP>, a, PP / 4, 32 * sizeof(StopCand), s); \
     else return cudaErrorInvalidValue;
     PIDE_SWITCH_P(a.g.P, CASE)
+#undef CASE
+}
+template <typename R>
+cudaError_t launch_row_dst(const Geometry& g, const double* src, R* E, const void* tw, cudaStream_t s) {
+#define CASE(PP)                                                                                      \
+    {                                                                                                 \
+        using CF = Cfg<R, PP>;                                                                        \
+        set_smem(k_row_dst<R, PP>, CF::SMEM);                                                         \
+        k_row_dst<R, PP><<<(PP / 4 + CF::UNITS - 1) / CF::UNITS, CF::THREADS, CF::SMEM, s>>>(g, src, E, tw); \
+        return cudaGetLastError();                                                                    \
+    }
+    PIDE_SWITCH_P(g.P, CASE)
 #undef CASE
 }
 template <typename R>

@@ -155,3 +155,37 @@ def test_adjoint_requires_tape_and_finished_solve():
         s3.adjoint(dirs)                       # more directions than the tape holds
     g, st = s3.adjoint(dirs[:2])
     assert st == 0 and all(math.isfinite(x) for x in g)
+
+
+def test_workload_adjoint_entry_equals_composed_directions():
+    """pide2d_adjoint_workload (the Table A5 tangents inside the library)
+    against pide2d_adjoint along tangents composed here by hand from the
+    mapping lambda = (1 - alpha)/kappa, delta = lambda^(1-alpha)/Gamma(1-alpha),
+    eta = beta, rho = [[s1^2, c s1 s2], [c s1 s2, s2^2]]."""
+    from paper_2511_02700_gb300 import binding as B
+    w = Workload("adjw", n=32, steps=8, alpha=0.5, tol=1e-13, precision="fp64")
+    s = gpu_solver(w)
+    s.record(interval=4, ndirs=6)
+    s.solve()
+    lam = (1.0 - w.alpha) / w.kappa
+    delta = lam ** (1.0 - w.alpha) / math.gamma(1.0 - w.alpha)
+    s1, s2, c = w.sigma[0], w.sigma[1], w.corr
+    z = (0.0, 0.0)
+    dirs = [B.make_model(0.0, 0.0, 0.0, z, (2 * s1, c * s2, 0.0), 0.0),
+            B.make_model(0.0, 0.0, 0.0, z, (0.0, c * s1, 2 * s2), 0.0),
+            B.make_model(0.0, 0.0, 0.0, z, (0.0, s1 * s2, 0.0), 0.0),
+            B.make_model(0.0, -(1.0 - w.alpha) * delta / w.kappa, -lam / w.kappa, z, (0.0, 0.0, 0.0), 0.0),
+            B.make_model(0.0, 0.0, 0.0, (1.0, 0.0), (0.0, 0.0, 0.0), 0.0),
+            B.make_model(0.0, 0.0, 0.0, (0.0, 1.0), (0.0, 0.0, 0.0), 0.0)]
+    g_ref, _ = s.adjoint(dirs)
+    wl = B.make_workload(w.alpha, w.kappa, w.beta, w.sigma, w.corr, w.r)
+    g, st = s.adjoint_workload(wl)
+    assert st == 0
+    scale = max(abs(x) for x in g_ref)
+    assert max(abs(a - b) for a, b in zip(g, g_ref)) <= 1e-12 * scale, (g, g_ref)
+    # a workload that is not the handle's model is refused
+    other = B.make_workload(w.alpha, w.kappa * 1.01, w.beta, w.sigma, w.corr, w.r)
+    with pytest.raises(B.PideError) as e:
+        s.adjoint_workload(other)
+    assert "ERR_ARG" in str(e.value)
+    s.close()

@@ -1,0 +1,125 @@
+"""GPU parity at the sizes the benchmark runs, against the FP64 CPU oracle,
+through the C ABI.
+
+* Full solves of the convergence-sweep option at N = 256 and 512: FP64 mode
+  at 1e-10 relative, FP32-bulk at 1e-5 relative, at S0 and in max-norm over
+  the region of interest (S_i <= 3K), element by element.
+* One fixed-point iteration of the increment loop (pide2d_iteration_probe):
+  at N = 4096, the 8192-point FP32-bulk kernels and launch shapes of the
+  benchmark's timed loop (column DST pass, row DST pass with the R2C rows of
+  the increment, column pass with the increment weight spectrum, inverse row
+  pass), and at N = 256 in FP64.  The increment is checked at every interior
+  node against the oracle's sine-basis solve, B_w of the increment at every
+  interior node against the oracle's FFT correlation (eq. 3.17), and the
+  eq. 3.25 quantity.
+* The 4096^2 benchmark workload itself, FP32-bulk against FP64 mode (the
+  1e-5 bound of the headline metric), 1024 time steps.
+
+The oracle runs in worker processes started with the spawn method when this
+module is collected, so its minutes overlap the GPU tests that run before.
+
+Tolerances: FP64 1e-10 relative for solves (the fixed points of the two
+iterations agree to the fixed-point tolerances used, 1e-12 / 1e-13); FP64
+operator checks 1e-12 of the scale (the GPU and oracle weight quadratures
+agree to ~1e-11 relative, the FFTs to ~1e-14); FP32 transforms 1e-5 of
+max|delta| for the DST solve (four 8192-point FP32 transforms,
+~log2(P) eps_32 each) and 2e-6 of sum(w) max|delta| for the jump sum.
+"""
+import atexit
+import math
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+from paper_2511_02700_gb300.workloads import LARGE_FP32_4096, Workload, with_
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import oracle_jobs as OJ  # noqa: E402
+from conftest import gpu_solver  # noqa: E402
+
+HT, THETA = 1.0 / 1024, 0.5                      # the 4096^2 workload's time step
+SOLVE_256 = Workload("h256", n=256, steps=64, alpha=0.5, tol=1e-13, precision="fp64")
+SOLVE_512 = Workload("h512", n=512, steps=128, alpha=0.5, tol=1e-12, precision="fp64")
+PROBE_4096 = with_(LARGE_FP32_4096, name="probe4096")
+PROBE_256 = Workload("probe256", n=256, steps=256, alpha=0.5, precision="fp64")
+
+_POOL = mp.get_context("spawn").Pool(3)
+atexit.register(_POOL.terminate)
+_JOBS = {
+    "solve512": _POOL.apply_async(OJ.solve, (SOLVE_512,)),
+    "probe4096": _POOL.apply_async(OJ.iteration_reference, (PROBE_4096, 4096, HT, THETA, 8)),
+    "solve256": _POOL.apply_async(OJ.solve, (SOLVE_256,)),
+    "probe256": _POOL.apply_async(OJ.iteration_reference, (PROBE_256, 256, HT, THETA)),
+}
+
+
+def oracle_result(key, timeout=1800):
+    return _JOBS[key].get(timeout=timeout)
+
+
+def roi_mask(n, half_width=2.5):
+    s = math.log(100.0) - half_width + np.arange(n + 1) * (2 * half_width / n)
+    m1 = np.exp(s) <= 300.0
+    M = np.outer(m1, m1)
+    M[0, :] = M[-1, :] = M[:, 0] = M[:, -1] = False
+    return M
+
+
+@pytest.mark.parametrize("key,w", [("solve256", SOLVE_256), ("solve512", SOLVE_512)])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_full_solve_matches_oracle(key, w, precision):
+    wg = w if precision == "fp64" else with_(w, precision="fp32", tol=1e-8)
+    s = gpu_solver(wg)
+    price, V, stats, st = s.solve(values=True)
+    s.close()
+    assert st == 0
+    V = V.cpu().numpy()
+    ref_price, ref_V = oracle_result(key)
+    tol = 1e-10 if precision == "fp64" else 1e-5
+    roi = roi_mask(w.n)
+    assert abs(price - ref_price) <= tol * abs(ref_price), (price, ref_price)
+    assert np.abs(V - ref_V)[roi].max() <= tol * np.abs(ref_V[roi]).max()
+    if precision == "fp64":
+        assert np.abs(V - ref_V).max() <= tol * np.abs(ref_V).max()
+
+
+@pytest.mark.parametrize("key,w,seed", [("probe4096", PROBE_4096, 4096), ("probe256", PROBE_256, 256)])
+def test_increment_iteration_matches_oracle(key, w, seed):
+    s = gpu_solver(w)
+    r = torch.from_numpy(OJ.probe_residual(w.n, seed))
+    d, bd, stop = s.iteration_probe(r, HT, THETA)
+    s.close()
+    d = d.cpu().numpy()[1:-1, 1:-1]
+    bd = bd.cpu().numpy()[1:-1, 1:-1]
+    ref_d, ref_bd, ref_stop, sum_w = oracle_result(key)
+    dmax = np.abs(ref_d).max()
+    fp64 = w.precision == "fp64"
+    assert np.abs(d - ref_d).max() <= (1e-12 if fp64 else 1e-5) * dmax
+    assert np.abs(bd - ref_bd).max() <= (1e-12 if fp64 else 2e-6) * sum_w * dmax
+    assert abs(stop - ref_stop) <= (1e-12 if fp64 else 1e-5) * ref_stop
+
+
+@pytest.mark.slow
+def test_large_workload_fp32_bulk_matches_fp64():
+    """4096^2, alpha 0.5, 1024 steps, tol 1e-7: the FP32-bulk solve the
+    benchmark times against the FP64-mode solve of the same configuration."""
+    w32 = LARGE_FP32_4096
+    w64 = with_(w32, precision="fp64")
+    s = gpu_solver(w64)
+    p64, V64, _, st64 = s.solve(values=True)
+    V64 = V64.cpu().numpy()
+    s.close()
+    s = gpu_solver(w32)
+    p32, V32, _, st32 = s.solve(values=True)
+    V32 = V32.cpu().numpy()
+    s.close()
+    assert st64 == 0 and st32 == 0
+    roi = roi_mask(w32.n)
+    assert abs(p32 - p64) <= 1e-5 * abs(p64), (p32, p64)
+    assert np.abs(V32 - V64)[roi].max() <= 1e-5 * np.abs(V64[roi]).max()
