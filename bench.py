@@ -50,6 +50,8 @@ def args_parse():
     p.add_argument("--no-batch", action="store_true", help="skip the 512-pricing batch measurement")
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
     p.add_argument("--no-sweep", action="store_true", help="skip the FP32-bulk vs FP64 convergence sweep")
+    p.add_argument("--no-fp64", action="store_true",
+                   help="skip the FP64-mode solve of the same workload (the error of the FP32-bulk result)")
     p.add_argument("--no-paper", action="store_true",
                    help="skip the paper's own set-ups (price-space scheme, VG0 on the wide log domain)")
     p.add_argument("--host-loop", action="store_true",
@@ -138,12 +140,12 @@ def algorithmic_bytes(cls, n, hcount=4):
     wh = P * H * 8
     return {
         0: (8 * hcount + 8 + 16) * cells,                      # prep: V history, BV -> W, Y
-        1: 8 * cells + spec_full,                              # row forward full: Y -> S
+        1: 16 * cells + spec_full,                             # row forward (difference): Y, V^{n-1} -> S
         2: 4 * cells + spec_n,                                 # row forward incr: D -> S
         3: spec_full + wh + spec_n,                            # column pass full
         4: spec_n + wh + spec_n,                               # column pass incr
-        5: spec_n + 8 * cells + 16 * cells + 4 * cells + 4 * cells,   # inverse full: S, BY, W+Y, r, E
-        6: spec_n + 16 * cells + 4 * cells + 4 * cells + 4 * cells,   # inverse incr: S, BY, r (write), D, E
+        5: spec_n + 8 * cells + 8 * cells + 16 * cells + 4 * cells,   # inverse full: S, BV, BY, W+Y, E
+        6: spec_n + 16 * cells + 4 * cells + 4 * cells,        # inverse incr: S, BY, D, E
         7: 8 * cells,                                          # column DST
         8: 4 * cells + 16 * cells + 4 * cells + spec_n,        # row DST back (E, Y, D) + increment R2C rows
     }[cls]
@@ -151,6 +153,11 @@ def algorithmic_bytes(cls, n, hcount=4):
 
 KERNEL_NAMES = ["k_prep", "k_row_forward(full)", "k_row_forward(incr)", "k_col(full)", "k_col(incr)",
                 "k_row_inverse(full)", "k_row_inverse(incr)", "k_dst_col", "k_dst_row+fwd"]
+# the kernels of one fixed-point iteration (the B_w sweep of an increment fused with the DST solve)
+ITERATION_KERNELS = (7, 8, 4, 6)
+# SURVEY's algorithmic bytes of one cell-iteration of the FFT sweep alone (FP32, P = 2N, pruned R2C):
+# read Y 4, two round trips of the N x (P/2+1) intermediate 32, read w^ 16, read W + write RHS 8
+SWEEP_BYTES_PER_CELL = 60
 
 
 def measured_peak():
@@ -188,6 +195,75 @@ def recorded_traffic(kernel, n):
 
 
 # --------------------------------------------------------------------------- oracle arm
+def host_cpu():
+    """nproc and the CPU model of this host (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu model")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return os.cpu_count() or 1, model or "unknown"
+
+
+def _oracle_replica(args):
+    steps, warmup, n_sample = args
+    return oracle_sample(steps, warmup, n_sample)
+
+
+def oracle_sample_all_cores(steps, warmup, n_sample=512, procs=None):
+    """The oracle sample on every host core: one single-threaded oracle
+    process per core (spawned), all on the same sample; aggregate throughput
+    = units of all processes over the slowest process's stepping time."""
+    import multiprocessing as mp
+    ncpu, _ = host_cpu()
+    procs = procs or ncpu
+    env_keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env_keep:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(procs) as pool:
+            res = pool.map(_oracle_replica, [(steps, warmup, n_sample)] * procs)
+    finally:
+        for k, v in env_keep.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    units = sum(r["units"] for r in res)
+    t = max(r["seconds"] for r in res)
+    return units / t, procs
+
+
+def cpu_baseline_block(steps, warmup, n_sample=512, all_cores=True):
+    """The oracle timed on this host: one core, and all cores as independent
+    replicas; the line's value is the all-core figure."""
+    ncpu, model = host_cpu()
+    one = oracle_sample(steps, warmup, n_sample)
+    out = dict(one)
+    out.update({"value_1core": one["value"], "cores_available": ncpu, "cpu_model": model})
+    if all_cores and ncpu > 1:
+        v_all, procs = oracle_sample_all_cores(steps, warmup, n_sample)
+        out.update({"value": v_all, "cores": procs, "value_all_cores": v_all,
+                    "sample": one["sample"] + f"; all-core figure: {procs} concurrent single-threaded oracle "
+                                              f"processes (spawned), one per core, on the same sample, units of all "
+                                              f"processes over the slowest one's time"})
+    out.pop("units", None)
+    out.pop("seconds", None)
+    return out
+
+
 def oracle_sample(steps, warmup, n_sample=512):
     """FP64 CPU oracle on a bounded sample of the workload: same model,
     tolerance and scheme on an n_sample^2 grid; times `steps` time steps
@@ -214,7 +290,7 @@ def oracle_sample(steps, warmup, n_sample=512):
         units += n_sample * n_sample * (k + 1)
         done += 1
     dt = time.perf_counter() - t0
-    return {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "units": units, "seconds": dt,
             "sample": f"FP64 oracle, {n_sample}^2 grid of the same model/tol, {done} time steps after "
                       f"{max(1, warmup)} warm-up steps ({dt:.1f} s; setup {setup:.1f} s); numpy/scipy "
                       "single-threaded FFT and sparse LU"}
@@ -224,7 +300,7 @@ def run_reference(a):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    cb = oracle_sample(a.steps, a.warmup)
+    cb = cpu_baseline_block(max(1, a.steps), max(1, a.warmup))
     w = workload(a.n)
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": None, "higher_is_better": True,
@@ -301,10 +377,10 @@ def run_ours(a):
         torch.distributed.barrier()
     ck = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    # kernels launched in the timed region.  Device loop: per step prep + full sweep (4), setup
-    # and tally (2), per iteration dst_col, dst_row, check, col, row_inverse (5).  Host loop:
-    # 4 per step, 4 per iteration.
-    gpu_launches = sum(4 + 4 * k for k in iters) if a.host_loop else sum(6 + 5 * k for k in iters)
+    # kernels launched in the timed region.  Device loop: per step k_explicit + k_prep and the
+    # difference sweep (5), setup and tally (2), per iteration dst_col, dst_row, check, col,
+    # row_inverse (5).  Host loop: 5 per step, 4 per iteration.
+    gpu_launches = sum(5 + 4 * k for k in iters) if a.host_loop else sum(7 + 5 * k for k in iters)
     # roofline pass: the next `steps` time steps with per-kernel CUDA events (host-driven loop,
     # one launch per kernel, so each launch can be bracketed)
     B.pide2d_profile(s.h, 1)
@@ -340,14 +416,34 @@ def run_ours(a):
                     f"CUDA events on the solver stream ({prof_ms / a.steps:.3f} ms/step there)",
             "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
             "share_of_kernel_time": kms[top] / total_kms if total_kms > 0 else None}
+    # the whole fixed-point iteration: its four kernels' summed event time per iteration, against
+    # their own algorithmic bytes and against the 60 B per cell of the FFT sweep alone
+    n_it = launches[ITERATION_KERNELS[0]]
+    if n_it:
+        it_ms = sum(kms[i] for i in ITERATION_KERNELS) / n_it
+        it_bytes = sum(algorithmic_bytes(i, n) for i in ITERATION_KERNELS)
+        roof["iteration"] = {
+            "kernels": [KERNEL_NAMES[i] for i in ITERATION_KERNELS], "ms_per_iteration": it_ms,
+            "algorithmic_bytes": it_bytes, "achieved": it_bytes / (it_ms / 1e3) / 1e9,
+            "frac": it_bytes / (it_ms / 1e3) / 1e9 / peak,
+            "sweep_bytes_per_cell": SWEEP_BYTES_PER_CELL,
+            "sweep_achieved": SWEEP_BYTES_PER_CELL * n * n / (it_ms / 1e3) / 1e9,
+            "sweep_frac": SWEEP_BYTES_PER_CELL * n * n / (it_ms / 1e3) / 1e9 / peak,
+            "note": "frac: the four kernels' own algorithmic bytes (DST solve and double-float state "
+                    "included); sweep_frac: 60 B per cell-iteration for the FFT sweep alone, over the "
+                    "same time, i.e. with the DST solve counted as overhead"}
     kernels = {KERNEL_NAMES[i]: {"launches": launches[i], "ms": round(kms[i], 3),
                                  "GBps": (algorithmic_bytes(i, n) * launches[i] / (kms[i] / 1e3) / 1e9)
                                  if kms[i] > 0 else None}
                for i in range(9) if launches[i]}
     # end to end: a fresh job from host inputs to host outputs through the C ABI
     e2e = None
+    e2e_V = None
     if not a.no_e2e:
-        e2e = run_e2e(B, torch, dev, grid, model, contract, w, a.warmup + a.steps)
+        e2e, e2e_V = run_e2e(B, torch, dev, grid, model, contract, w, a.warmup + a.steps)
+    fp64 = None
+    if not a.no_fp64 and e2e is not None and ws == 1:
+        fp64 = run_fp64_plain(B, torch, dev, w, e2e["price"], e2e_V)
     s.close()
     if ws > 1:
         torch.distributed.barrier()
@@ -355,7 +451,7 @@ def run_ours(a):
         return
     cb = None
     if not a.no_cpu_baseline and ws == 1:
-        cb = oracle_sample(steps=6, warmup=1)
+        cb = cpu_baseline_block(steps=6, warmup=1)
     batch = None if (a.no_batch or ws > 1) else run_batch(B, torch, dev)
     adjoint = None if (a.no_adjoint or ws > 1) else run_adjoint(B, torch, dev)
     sweep = None if (a.no_sweep or ws > 1) else run_sweep(B, torch, dev)
@@ -368,6 +464,10 @@ def run_ours(a):
                        "sl_order": w.sl_order, "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "working set > L2 (inputs larger than the 129 MB L2, no flush)"},
             "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": gpu_launches,
+            "error_vs_fp64": None if fp64 is None else {
+                "price_rel": fp64["price_rel_err"], "roi_maxnorm_rel": fp64["roi_maxnorm_rel_err"],
+                "bound": 1e-5, "against": "FP64-mode GPU solve of the same workload (fp64_plain)"},
+            "fp64_plain": fp64,
             "clocks": ck, "fp_iters_per_step": iters, "create_s": create_s, "kernels": kernels,
             "batch": batch, "adjoint": adjoint, "convergence_sweep": sweep, "paper_schemes": paper,
             "loop": "host-driven fixed-point loop" if a.host_loop else
@@ -421,26 +521,31 @@ def run_batch(B, torch, dev, lanes=256, fp64_sample=16):
 
 
 def run_adjoint(B, torch, dev):
+    """The adjoint workload at alpha 0.25 and 0.5 (run_adjoint_one each)."""
+    from paper_2511_02700_gb300.workloads import ADJOINT_FP64_1024, with_
+    return [run_adjoint_one(B, torch, dev, with_(ADJOINT_FP64_1024, alpha=a_)) for a_ in (0.25, 0.5)]
+
+
+def run_adjoint_one(B, torch, dev, w):
     """Adjoint on the 1024^2, 256-step FP64 workload: forward solve with
     checkpoints every 16 steps, then pide2d_adjoint for the six workload
     parameters; checked against FP64 central differences (step 1e-4) of the
     CUDA path's prices.  The FP32-bulk adjoint is timed beside it."""
-    from paper_2511_02700_gb300.workloads import ADJOINT_FP64_1024, ADJOINT_INTERVAL, with_
-    w = ADJOINT_FP64_1024
+    from paper_2511_02700_gb300.workloads import ADJOINT_INTERVAL, with_
     names = B.SUBORDINATED_BM_PARAMS
     out = {"workload": f"{w.name}: alpha {w.alpha}, {w.steps} steps, tol {w.tol}, checkpoint interval "
                        f"{ADJOINT_INTERVAL}", "params": list(names)}
 
     def forward_adjoint(wx):
         g, m, c = _job(B, wx)
-        dirs = B.subordinated_bm_directions(wx.alpha, wx.kappa, wx.beta, wx.sigma, wx.corr)
+        wl = B.make_workload(wx.alpha, wx.kappa, wx.beta, wx.sigma, wx.corr, wx.r)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         s = B.Solver(g, m, c, wx.steps, theta=wx.theta, tol=wx.tol, device=dev)
         s.record(interval=ADJOINT_INTERVAL, ndirs=6)
         price, _, st, _ = s.solve()
         t1 = time.perf_counter()
-        grad, ast = s.adjoint(dirs)
+        grad, ast = s.adjoint_workload(wl)
         t2 = time.perf_counter()
         s.close()
         return price, grad, t1 - t0, t2 - t1, st.cell_iters
@@ -620,10 +725,43 @@ def run_e2e(B, torch, dev, grid, model, contract, w, steps):
     # solve: the loop statistics (48 B), V and the price out
     h2d = 2 * (10 + 6 + 32 + 16 + 4) * 8 + (n + 1) * 4
     d2h = (n + 1) * (n + 1) * 8 + 9 * 8 + (n + 1) * 8 + 48 + 8
-    return {"value": stats.cell_iters / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": h2d / nsteps,
-            "d2h_bytes_per_step": d2h / nsteps, "steps": nsteps, "wall_s": t1 - t0, "price": price,
-            "fp_iters_total": stats.fp_iters_total,
-            "includes": "pide2d_create (device precompute) + pide2d_solve over all time steps + V to pinned host"}
+    return ({"value": stats.cell_iters / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": h2d / nsteps,
+             "d2h_bytes_per_step": d2h / nsteps, "steps": nsteps, "wall_s": t1 - t0, "price": price,
+             "fp_iters_total": stats.fp_iters_total,
+             "includes": "pide2d_create (device precompute) + pide2d_solve over all time steps + V to pinned host"},
+            host.numpy().reshape(n + 1, n + 1))
+
+
+def roi_mask(n, half_width, strike):
+    """Nodes with S_i <= 3K in both axes (the region of interest), boundary excluded."""
+    h = 2 * half_width / n
+    sg = math.log(strike) - half_width + h * np.arange(n + 1)
+    m1 = np.exp(sg) <= 3 * strike
+    roi = np.outer(m1, m1)
+    roi[0, :] = roi[-1, :] = roi[:, 0] = roi[:, -1] = False
+    return roi
+
+
+def run_fp64_plain(B, torch, dev, w, price32, V32):
+    """The same workload solved in FP64 mode on the same GPU (create + all
+    steps + V back), timed end to end; the FP32-bulk result's error against it
+    at S0 and in max-norm over the region of interest."""
+    grid = B.make_grid(w.n, B.PIDE2D_FP64, w.sl_order, half_width=w.half_width)
+    model = B.model_from_subordinated_bm(w.alpha, w.kappa, w.beta, w.sigma, w.corr, w.r)
+    contract = B.make_contract(B.PIDE2D_PUT_AVG, w.strike, w.maturity)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    s = B.Solver(grid, model, contract, w.steps, theta=w.theta, tol=w.tol, device=dev)
+    p64, V64, st, status = s.solve(values=True)
+    V64 = V64.cpu().numpy()
+    t1 = time.perf_counter()
+    s.close()
+    roi = roi_mask(w.n, w.half_width, w.strike)
+    return {"price": p64, "status": status, "wall_s": t1 - t0, "value": st.cell_iters / (t1 - t0), "unit": UNIT,
+            "fp_iters_total": st.fp_iters_total,
+            "price_rel_err": abs(price32 - p64) / abs(p64),
+            "roi_maxnorm_rel_err": float(np.abs(V32 - V64)[roi].max() / np.abs(V64[roi]).max()),
+            "includes": "pide2d_create + pide2d_solve (FP64 mode, device loop) + V to the host"}
 
 
 def main():
