@@ -513,6 +513,9 @@ def run_batch(B, torch, dev, lanes=256, fp64_sample=16):
         cells64 += st64.cell_iters
         t64 += a1 - a0
     return {"workload": "batch_draw(512): N in {128,256,512}, N/4 steps, FP32-bulk, tol 1e-8",
+            "loop": "one CUDA graph per chunk (while-node over theta steps around a while-node over "
+                    "fixed-point iterations), one launch and one host wait per chunk",
+            "tuning": st.tuning(), "create_s": st.create_s, "tune_s": st.tune_s, "loop_s": st.loop_s,
             "jobs": len(jobs), "lanes": lanes, "failures": st.failures, "wall_s": t1 - t0,
             "value": st.cell_iters / (t1 - t0), "unit": UNIT, "jobs_per_s": len(jobs) / (t1 - t0),
             "fp64_sample_jobs": fp64_sample, "price_max_rel_err_vs_fp64": max(errs),

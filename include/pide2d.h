@@ -110,6 +110,9 @@ typedef struct {
                           /* 1: the host reads the eq. 3.25 quantity after each  */
                           /*    iteration and launches the next one.  Tracing    */
                           /*    (pide2d_profile) always uses the host loop.      */
+    int fixed_shapes;     /* batches only: 1 keeps `lanes` and the single-job   */
+                          /*    launch shapes; 0 picks both per geometry group   */
+                          /*    by timed trials on its first chunk [0]           */
 } pide2d_options;
 
 typedef struct {
@@ -322,7 +325,10 @@ pide2d_status pide2d_adjoint_workload(pide2d_t* h, const pide2d_workload* w, dou
  * Algorithm 1).  Jobs of one geometry (n, precision, sl_order, number of
  * steps) are advanced in lockstep, up to `lanes` at a time: every kernel of
  * a theta step and of each fixed-point iteration is launched once for all
- * of them, and a job whose iteration has converged skips its share.
+ * of them, and a job whose iteration has converged skips its share.  The
+ * whole time loop of such a chunk is one CUDA graph (a while-node over the
+ * theta steps around a while-node over the fixed-point iterations, both
+ * ended on the device), launched once; the host waits once per chunk.
  * ------------------------------------------------------------------------ */
 typedef struct {
     pide2d_grid grid;
@@ -338,17 +344,28 @@ typedef struct {
     int failures;         /* jobs whose status was not OK                          */
     int fp_iters_total;   /* fixed-point iterations over all jobs                  */
     double cell_iters;    /* cell-applications of B_w over all jobs                */
+    int tuned;            /* geometry groups whose launch shape was picked by     */
+                          /* timed trials (the first 8 are listed below)          */
+    int tune_n[8];        /* the group's grid size N                              */
+    int tune_units[8];    /* FFT units per block of its multi-job kernels         */
+    int tune_lanes[8];    /* jobs per chunk                                       */
+    double tune_us_per_job[8];  /* the winning trial: microseconds per job of one */
+                                /* column pass of the fixed-point iteration       */
+    double create_s;      /* host wall time in the per-job precomputes             */
+    double tune_s;        /* host wall time in the launch-shape trials             */
+    double loop_s;        /* host wall time in the chunks' time loops              */
 } pide2d_batch_stats;
 
 /* Workspace for pide2d_batch_solve: min(lanes, count) lanes of the largest
  * job's pide2d_workspace_bytes (256-byte rounded), plus the argument arrays
- * of the multi-job launches.  1 <= lanes <= 1024.  Errors: ERR_ARG. */
+ * of the multi-job launches for every theta step of the longest job.
+ * 1 <= lanes <= 1024.  Errors: ERR_ARG. */
 pide2d_status pide2d_batch_workspace_bytes(const pide2d_job* jobs, int count, int lanes, size_t* bytes);
 
 /* Prices `count` jobs: prices[j] (host, count doubles) receives job j's value
  * at S0; statuses (host, count ints, optional) each job's status; stats
- * optional.  opts->host_loop is ignored (the multi-job loop reads the
- * number of jobs still iterating after each iteration).  workspace: device,
+ * optional.  opts->host_loop is ignored (the multi-job loop runs on the
+ * device).  All jobs of a chunk share damping.  workspace: device,
  * >= pide2d_batch_workspace_bytes(), 256-byte aligned, caller-owned.  Uses
  * the calling thread's current device; creates and destroys a few
  * non-blocking streams and host threads (no device allocation).  Blocks

@@ -38,7 +38,7 @@ class pide2d_contract(ctypes.Structure):
 
 
 class pide2d_options(ctypes.Structure):
-    _fields_ = [("kmax", c_int), ("damping", c_int), ("host_loop", c_int)]
+    _fields_ = [("kmax", c_int), ("damping", c_int), ("host_loop", c_int), ("fixed_shapes", c_int)]
 
 
 class pide2d_stats(ctypes.Structure):
@@ -61,7 +61,15 @@ class pide2d_job(ctypes.Structure):
 
 
 class pide2d_batch_stats(ctypes.Structure):
-    _fields_ = [("jobs_done", c_int), ("failures", c_int), ("fp_iters_total", c_int), ("cell_iters", c_double)]
+    _fields_ = [("jobs_done", c_int), ("failures", c_int), ("fp_iters_total", c_int), ("cell_iters", c_double),
+                ("tuned", c_int), ("tune_n", c_int * 8), ("tune_units", c_int * 8), ("tune_lanes", c_int * 8),
+                ("tune_us_per_job", c_double * 8), ("create_s", c_double), ("tune_s", c_double),
+                ("loop_s", c_double)]
+
+    def tuning(self):
+        """The launch shapes the batch picked, one dict per tuned geometry group."""
+        return [{"n": self.tune_n[i], "units_per_block": self.tune_units[i], "lanes": self.tune_lanes[i],
+                 "us_per_job_column_pass": self.tune_us_per_job[i]} for i in range(min(self.tuned, 8))]
 
 
 class pide2d_price_grid(ctypes.Structure):
@@ -431,7 +439,7 @@ class Solver:
             pass
 
 
-def solve_batch(jobs, lanes=16, kmax=100, damping=True, device="cuda", host_loop=False):
+def solve_batch(jobs, lanes=16, kmax=100, damping=True, device="cuda", host_loop=False, fixed_shapes=False):
     """Prices a list of pide2d_job through pide2d_batch_solve (workspace from
     PyTorch).  Returns (prices, statuses, stats)."""
     import torch
@@ -442,6 +450,7 @@ def solve_batch(jobs, lanes=16, kmax=100, damping=True, device="cuda", host_loop
     opts = pide2d_options()
     opts.kmax, opts.damping = kmax, 1 if damping else 0
     opts.host_loop = 1 if host_loop else 0
+    opts.fixed_shapes = 1 if fixed_shapes else 0
     torch.cuda.synchronize(device)
     prices, sts, stats, _ = pide2d_batch_solve(jobs, opts, lanes, base, nbytes)
     del ws

@@ -626,6 +626,10 @@ static void build_solve_args(pide2d* H, const SolveSpec<R>& sp, SolveArgs<R>* ou
     da.c1 = 2.0 * htt * a11 / (hg * hg);
     da.c2 = 2.0 * htt * a22 / (hg * hg);
     da.scale = (2.0 / N) * (2.0 / N);
+    da.rc0 = (R)da.c0;
+    da.rc1 = (R)da.c1;
+    da.rc2 = (R)da.c2;
+    da.rscale = (R)da.scale;
     da.tw = tw;
     DstRowArgs<R>& ra = out->ra;
     ra.g = g;
@@ -1312,8 +1316,9 @@ size_t arr_bytes(size_t each, int K) { return align256(each * (size_t)K); }
 
 template <typename R>
 struct GroupLayout {
-    size_t pa, fa, caf, iaf, da, ra, cai, iai, chk, conv, kconv, kcount, nonconv, last, active, total;
-    GroupLayout(int K) {
+    size_t pa, fa, caf, iaf, da, ra, cai, iai, chk, conv, kconv, kcount, nonconv, last, active, iter, it_total,
+        it_step, it_max, step, step_end, blobs, blob_bytes, total;
+    GroupLayout(int K, int T) {
         size_t o = 0;
         pa = o;      o += arr_bytes(sizeof(PrepArgs<R>), K);
         fa = o;      o += arr_bytes(sizeof(FwdArgs<R>), K);
@@ -1323,6 +1328,7 @@ struct GroupLayout {
         ra = o;      o += arr_bytes(sizeof(DstRowArgs<R>), K);
         cai = o;     o += arr_bytes(sizeof(ColArgs<R>), K);
         iai = o;     o += arr_bytes(sizeof(InvArgs<R>), K);
+        blob_bytes = o;                  // the argument arrays of one theta step (a multiple of 256)
         chk = o;     o += arr_bytes(sizeof(JobCheck), K);
         conv = o;    o += arr_bytes(4, K);
         kconv = o;   o += arr_bytes(4, K);
@@ -1330,165 +1336,145 @@ struct GroupLayout {
         nonconv = o; o += arr_bytes(4, K);
         last = o;    o += arr_bytes(8, K);
         active = o;  o += kArgAlign;
+        iter = o;    o += kArgAlign;
+        it_total = o; o += arr_bytes(4, K);
+        it_step = o; o += arr_bytes(4, K);
+        it_max = o;  o += arr_bytes(4, K);
+        step = o;    o += kArgAlign;
+        step_end = o; o += arr_bytes(4, T);
+        blobs = o;   o += blob_bytes * (size_t)T;
         total = o;
     }
 };
 
-// the next theta step of one job, as do_step would take it
-struct JobPlan {
-    int list[4];
-    int cnt;
-    double theta, ht, tau_prev, tau;
-    int res;
-    int step_end;
-};
+// the theta steps of a time loop of n_steps steps (the damped first step has four)
+int theta_steps(int n_steps, bool damping) { return n_steps + (damping ? 3 : 0); }
 }  // namespace
 
 namespace pide {
-size_t group_scratch_bytes(int K) {
-    return std::max(GroupLayout<float>(K).total, GroupLayout<double>(K).total);
+size_t group_scratch_bytes(int K, int n_steps) {
+    const int T = theta_steps(n_steps, true);
+    return std::max(GroupLayout<float>(K, T).total, GroupLayout<double>(K, T).total);
 }
 
 }  // namespace pide
 
+// The multi-job time loop of a chunk of K fresh handles of one geometry:
+//  1. on the host, the argument arrays of every theta step of every job, by
+//     the bookkeeping do_step performs (the field rotation does not depend on
+//     device results), uploaded as one blob per theta step;
+//  2. one CUDA graph for the whole loop: an outer while-node over the theta
+//     steps -- k_step_select copies the step's blob into the argument arrays,
+//     then W and Y^{n,0} (prep), the difference sweep, the reset of the
+//     per-job stopping state, an inner while-node over the fixed-point
+//     iterations (column DST, row DST with the eq. 3.25 maxima, the per-job
+//     check that ends the inner loop when no job iterates any more, column
+//     pass and inverse row pass of the jobs still iterating) and
+//     k_step_tally, which folds the counts into per-job statistics and ends
+//     the outer loop after the last theta step;
+//  3. one launch, one synchronisation, the statistics back to the handles.
 template <typename R>
-static pide2d_status group_solve(pide2d* const* hs, int K, char* scratch, std::string* err) {
+static pide2d_status group_solve(pide2d* const* hs, int K, char* scratch, int upb, std::string* err) {
     pide2d* H0 = hs[0];
     cudaStream_t s = H0->stream;
-    const GroupLayout<R> L(K);
-    std::vector<char> blob(L.chk);                         // the argument arrays, rebuilt per theta step
+    auto fail = [&](pide2d* H, pide2d_status st) {
+        *err = H->err;
+        return st;
+    };
+    for (int j = 0; j < K; ++j)
+        if (hs[j]->steps_done != 0) {
+            hs[j]->err = "multi-job loop: handle already stepped";
+            return fail(hs[j], PIDE2D_ERR_STATE);
+        }
+    const bool damped0 = H0->damping != 0;
+    const int T = theta_steps(H0->n_steps, damped0);
+    const GroupLayout<R> L(K, T);
     std::vector<JobCheck> chk(K);
+    int kmax_all = 0;
     for (int j = 0; j < K; ++j) {
         chk[j].resid = hs[j]->at<void>(R_RESID);
         chk[j].tol = hs[j]->tol;
         chk[j].kmax = hs[j]->kmax;
         chk[j].pad = 0;
+        kmax_all = std::max(kmax_all, hs[j]->kmax);
     }
-    auto fail = [&](pide2d* H, pide2d_status st) {
-        *err = H->err;
-        return st;
-    };
-    {
-        pide2d* H = H0;
-        PIDE_CUDA(cudaMemcpyAsync(scratch + L.chk, chk.data(), sizeof(JobCheck) * K, cudaMemcpyHostToDevice, s));
-        PIDE_CUDA(cudaMemsetAsync(scratch + L.nonconv, 0, 4 * (size_t)K, s));
-    }
-    JobsState st{};
-    st.conv = reinterpret_cast<int*>(scratch + L.conv);
-    st.kconv = reinterpret_cast<int*>(scratch + L.kconv);
-    st.kcount = reinterpret_cast<int*>(scratch + L.kcount);
-    st.nonconv = reinterpret_cast<int*>(scratch + L.nonconv);
-    st.last = reinterpret_cast<double*>(scratch + L.last);
-    st.active = reinterpret_cast<int*>(scratch + L.active);
-    const JobCheck* dchk = reinterpret_cast<const JobCheck*>(scratch + L.chk);
-    int kmax_all = 0;
-    for (int j = 0; j < K; ++j) kmax_all = std::max(kmax_all, hs[j]->kmax);
-    std::vector<int> kc(K);
-    std::vector<double> lastv(K);
-    std::vector<int> cur(K), v0(K), ktot(K);
-    std::vector<JobPlan> plan(K);
 
+    // 1. every theta step's argument arrays
+    std::vector<char> blobs(L.blob_bytes * (size_t)T, 0);
+    std::vector<int> step_end(T, 0);
+    PrepArgs<R> pa0{};
+    SolveArgs<R> A0{};
+    std::vector<int> cur(K), v0(K);
+    int t = 0;
     while (H0->steps_done < H0->n_steps) {
         const bool damped = H0->steps_done == 0 && H0->damping;
         const int nsub = damped ? 4 : 1;
-        for (int j = 0; j < K; ++j) {
-            cur[j] = v0[j] = hs[j]->hist[0];
-            ktot[j] = 0;
-        }
-        for (int sub = 0; sub < nsub; ++sub) {
-            PrepArgs<R> pa0{};
-            SolveArgs<R> A0{};
+        for (int j = 0; j < K; ++j) cur[j] = v0[j] = hs[j]->hist[0];
+        for (int sub = 0; sub < nsub; ++sub, ++t) {
+            if (t >= T) {
+                H0->err = "multi-job loop: theta step count";
+                return fail(H0, PIDE2D_ERR_STATE);
+            }
+            char* blob = blobs.data() + L.blob_bytes * (size_t)t;
+            step_end[t] = (!damped || sub == 3) ? 1 : 0;
             for (int j = 0; j < K; ++j) {
                 pide2d* H = hs[j];
-                JobPlan& p = plan[j];
-                p.res = H->freel.back();
+                if (H->damping != H0->damping || H->n_steps != H0->n_steps) {
+                    H->err = "multi-job loop: jobs differ in damping or step count";
+                    return fail(H, PIDE2D_ERR_ARG);
+                }
+                int list[4];
+                int cnt;
+                double theta, ht, tau_prev, tau;
+                const int res = H->freel.back();
                 H->freel.pop_back();
                 if (damped) {
                     const double q = H->dt / 4.0;
-                    p.list[0] = cur[j];
-                    p.cnt = 1;
-                    p.theta = 1.0;
-                    p.ht = q;
-                    p.tau_prev = sub * q;
-                    p.tau = (sub + 1) * q;
-                    p.step_end = sub == 3 ? 1 : 0;
+                    list[0] = cur[j];
+                    cnt = 1;
+                    theta = 1.0;
+                    ht = q;
+                    tau_prev = sub * q;
+                    tau = (sub + 1) * q;
                 } else {
                     const int n = H->steps_done + 1;
-                    p.cnt = (int)H->hist.size() < 4 ? (int)H->hist.size() : 4;
-                    for (int i = 0; i < p.cnt; ++i) p.list[i] = H->hist[i];
-                    p.theta = H->theta;
-                    p.ht = H->dt;
-                    p.tau_prev = (n - 1) * H->dt;
-                    p.tau = n * H->dt;
-                    p.step_end = 1;
+                    cnt = (int)H->hist.size() < 4 ? (int)H->hist.size() : 4;
+                    for (int i = 0; i < cnt; ++i) list[i] = H->hist[i];
+                    theta = H->theta;
+                    ht = H->dt;
+                    tau_prev = (n - 1) * H->dt;
+                    tau = n * H->dt;
                 }
                 PrepArgs<R> pa;
                 SolveSpec<R> sp;
                 const pide2d_status bs =
-                    build_theta_step<R>(H, p.list, p.cnt, p.theta, p.ht, p.tau_prev, p.tau, p.res, p.step_end, &pa, &sp);
+                    build_theta_step<R>(H, list, cnt, theta, ht, tau_prev, tau, res, step_end[t], &pa, &sp);
                 if (bs != PIDE2D_OK) return fail(H, bs);
                 SolveArgs<R> A;
                 build_solve_args<R>(H, sp, &A);
-                A.iai.conv_flag = st.conv + j;
-                std::memcpy(blob.data() + L.pa + j * sizeof pa, &pa, sizeof pa);
-                std::memcpy(blob.data() + L.fa + j * sizeof A.fa, &A.fa, sizeof A.fa);
-                std::memcpy(blob.data() + L.caf + j * sizeof A.caf, &A.caf, sizeof A.caf);
-                std::memcpy(blob.data() + L.iaf + j * sizeof A.iaf, &A.iaf, sizeof A.iaf);
-                std::memcpy(blob.data() + L.da + j * sizeof A.da, &A.da, sizeof A.da);
-                std::memcpy(blob.data() + L.ra + j * sizeof A.ra, &A.ra, sizeof A.ra);
-                std::memcpy(blob.data() + L.cai + j * sizeof A.cai, &A.cai, sizeof A.cai);
-                std::memcpy(blob.data() + L.iai + j * sizeof A.iai, &A.iai, sizeof A.iai);
-                if (j == 0) {
+                A.iai.conv_flag = nullptr;
+                std::memcpy(blob + L.pa + j * sizeof pa, &pa, sizeof pa);
+                std::memcpy(blob + L.fa + j * sizeof A.fa, &A.fa, sizeof A.fa);
+                std::memcpy(blob + L.caf + j * sizeof A.caf, &A.caf, sizeof A.caf);
+                std::memcpy(blob + L.iaf + j * sizeof A.iaf, &A.iaf, sizeof A.iaf);
+                std::memcpy(blob + L.da + j * sizeof A.da, &A.da, sizeof A.da);
+                std::memcpy(blob + L.ra + j * sizeof A.ra, &A.ra, sizeof A.ra);
+                std::memcpy(blob + L.cai + j * sizeof A.cai, &A.cai, sizeof A.cai);
+                std::memcpy(blob + L.iai + j * sizeof A.iai, &A.iai, sizeof A.iai);
+                if (t == 0 && j == 0) {
                     pa0 = pa;
                     A0 = A;
                 }
-                // the launch covers the longest row range of the chunk (each job stops at its own)
-                A0.fa.npairs = std::max(A0.fa.npairs, A.fa.npairs);
-            }
-            pide2d* H = H0;
-            auto arr = [&](size_t off) { return scratch + off; };
-            PIDE_CUDA(cudaMemcpyAsync(scratch, blob.data(), L.chk, cudaMemcpyHostToDevice, s));
-            bool expl = false;
-            for (int j = 0; j < K; ++j) expl = expl || plan[j].theta != 1.0;
-            PIDE_CUDA(launch_prep_jobs<R>(pa0, (const PrepArgs<R>*)arr(L.pa), K, expl, s));
-            JobsCtl all{st.conv, st.kconv, 0, 0};
-            PIDE_CUDA(launch_row_forward_jobs<R>(A0.fa, (const FwdArgs<R>*)arr(L.fa), K, all, s));
-            PIDE_CUDA(launch_col_jobs<R>(A0.caf, (const ColArgs<R>*)arr(L.caf), K, all, s));
-            PIDE_CUDA(launch_row_inverse_jobs<R>(A0.iaf, (const InvArgs<R>*)arr(L.iaf), K, all, s));
-            PIDE_CUDA(launch_jobs_reset<R>(K, dchk, st, s));
-            for (int it = 1; it <= kmax_all; ++it) {
-                const JobsCtl head{st.conv, st.kconv, it, 1};
-                const JobsCtl tail{st.conv, st.kconv, it, 2};
-                PIDE_CUDA(launch_dst_col_jobs<R>(A0.da, (const DstColArgs<R>*)arr(L.da), K, head, s));
-                PIDE_CUDA(launch_dst_row_jobs<R>(A0.ra, (const DstRowArgs<R>*)arr(L.ra), K, head, s));
-                PIDE_CUDA(launch_jobs_check<R>(K, dchk, st, it, s));
-                PIDE_CUDA(launch_col_jobs<R>(A0.cai, (const ColArgs<R>*)arr(L.cai), K, tail, s));
-                PIDE_CUDA(launch_row_inverse_jobs<R>(A0.iai, (const InvArgs<R>*)arr(L.iai), K, tail, s));
-                int act = 0;
-                PIDE_CUDA(cudaMemcpyAsync(&act, st.active, 4, cudaMemcpyDeviceToHost, s));
-                PIDE_CUDA(cudaStreamSynchronize(s));
-                if (act == 0) break;
-            }
-            PIDE_CUDA(cudaMemcpyAsync(kc.data(), st.kcount, 4 * (size_t)K, cudaMemcpyDeviceToHost, s));
-            PIDE_CUDA(cudaMemcpyAsync(lastv.data(), st.last, 8 * (size_t)K, cudaMemcpyDeviceToHost, s));
-            PIDE_CUDA(cudaStreamSynchronize(s));
-            // bookkeeping of each job, as theta_step / do_step do it
-            for (int j = 0; j < K; ++j) {
-                pide2d* Hj = hs[j];
-                const JobPlan& p = plan[j];
-                std::swap(Hj->bv, Hj->by);
-                const int N = Hj->L.g.N;
-                Hj->stats.cell_iters += (double)N * N * (kc[j] + 1);
-                Hj->stats.last_resid = lastv[j];
-                ktot[j] += kc[j];
+                // bookkeeping of theta_step / do_step
+                std::swap(H->bv, H->by);
                 if (damped) {
-                    if (cur[j] != v0[j]) Hj->freel.push_back(cur[j]);
-                    cur[j] = p.res;
+                    if (cur[j] != v0[j]) H->freel.push_back(cur[j]);
+                    cur[j] = res;
                 } else {
-                    Hj->hist.insert(Hj->hist.begin(), p.res);
-                    if (Hj->hist.size() > 4) {
-                        Hj->freel.push_back(Hj->hist.back());
-                        Hj->hist.pop_back();
+                    H->hist.insert(H->hist.begin(), res);
+                    if (H->hist.size() > 4) {
+                        H->freel.push_back(H->hist.back());
+                        H->hist.pop_back();
                     }
                 }
             }
@@ -1498,22 +1484,163 @@ static pide2d_status group_solve(pide2d* const* hs, int K, char* scratch, std::s
             if (damped) Hj->hist.assign({cur[j], v0[j]});
             Hj->steps_done++;
             Hj->stats.steps_done = Hj->steps_done;
-            Hj->stats.fp_iters_total += ktot[j];
-            if (ktot[j] > Hj->stats.fp_iters_max) Hj->stats.fp_iters_max = ktot[j];
             Hj->last_step_device = false;
         }
     }
-    // jobs with a theta step that stopped at kmax or on a non-finite residual
-    std::vector<int> nc(K);
+    const int Tused = t;
+    // the row pass of the full sweep covers every job's row range at every step
+    A0.fa.npairs = H0->L.g.N + 1;
+
+    JobsState st{};
+    st.conv = reinterpret_cast<int*>(scratch + L.conv);
+    st.kconv = reinterpret_cast<int*>(scratch + L.kconv);
+    st.kcount = reinterpret_cast<int*>(scratch + L.kcount);
+    st.nonconv = reinterpret_cast<int*>(scratch + L.nonconv);
+    st.last = reinterpret_cast<double*>(scratch + L.last);
+    st.active = reinterpret_cast<int*>(scratch + L.active);
+    st.iter = reinterpret_cast<int*>(scratch + L.iter);
+    st.it_total = reinterpret_cast<int*>(scratch + L.it_total);
+    st.it_step = reinterpret_cast<int*>(scratch + L.it_step);
+    st.it_max = reinterpret_cast<int*>(scratch + L.it_max);
+    st.step = reinterpret_cast<int*>(scratch + L.step);
+    const JobCheck* dchk = reinterpret_cast<const JobCheck*>(scratch + L.chk);
     {
         pide2d* H = H0;
+        PIDE_CUDA(cudaMemcpyAsync(scratch + L.chk, chk.data(), sizeof(JobCheck) * K, cudaMemcpyHostToDevice, s));
+        PIDE_CUDA(cudaMemcpyAsync(scratch + L.step_end, step_end.data(), 4 * (size_t)Tused, cudaMemcpyHostToDevice, s));
+        PIDE_CUDA(cudaMemcpyAsync(scratch + L.blobs, blobs.data(), L.blob_bytes * (size_t)Tused,
+                                  cudaMemcpyHostToDevice, s));
+        // per-job stopping state and statistics, the iteration and step counters
+        PIDE_CUDA(cudaMemsetAsync(scratch + L.conv, 0, L.step_end - L.conv, s));
+    }
+
+    // 2. the graph of the whole loop
+    pide2d* H = H0;
+    if (!H->cap) PIDE_CUDA(cudaStreamCreateWithFlags(&H->cap, cudaStreamNonBlocking));
+    cudaStream_t cs = H->cap;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    PIDE_CUDA(cudaGraphCreate(&g, 0));
+    const char* where = "";
+    cudaError_t e = cudaSuccess;
+#define PIDE_GTRY(call)          \
+    do {                         \
+        e = (call);              \
+        if (e != cudaSuccess) {  \
+            where = #call;       \
+            goto graph_done;     \
+        }                        \
+    } while (0)
+    {
+        auto arr = [&](size_t off) { return scratch + off; };
+        cudaGraphConditionalHandle hout, hin;
+        PIDE_GTRY(cudaGraphConditionalHandleCreate(&hout, g, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams cpo{};
+        cpo.type = cudaGraphNodeTypeConditional;
+        cpo.conditional.handle = hout;
+        cpo.conditional.type = cudaGraphCondTypeWhile;
+        cpo.conditional.size = 1;
+        cudaGraphNode_t outer = nullptr;
+        PIDE_GTRY(cudaGraphAddNode(&outer, g, nullptr, nullptr, 0, &cpo));
+        cudaGraph_t body_o = cpo.conditional.phGraph_out[0];
+        PIDE_GTRY(cudaGraphConditionalHandleCreate(&hin, body_o, 1, cudaGraphCondAssignDefault));
+        // the theta step's prologue
+        PIDE_GTRY(cudaStreamBeginCaptureToGraph(cs, body_o, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        {
+            cudaError_t x = launch_step_select(arr(L.blobs), L.blob_bytes, st, scratch, cs);
+            const JobsCtl all{st.conv, st.kconv, st.iter, 0};
+            if (x == cudaSuccess) x = launch_prep_jobs<R>(pa0, (const PrepArgs<R>*)arr(L.pa), K, true, cs);
+            if (x == cudaSuccess) x = launch_row_forward_jobs<R>(A0.fa, (const FwdArgs<R>*)arr(L.fa), K, all, upb, cs);
+            if (x == cudaSuccess) x = launch_col_jobs<R>(A0.caf, (const ColArgs<R>*)arr(L.caf), K, all, upb, cs);
+            if (x == cudaSuccess) x = launch_row_inverse_jobs<R>(A0.iaf, (const InvArgs<R>*)arr(L.iaf), K, all, upb, cs);
+            if (x == cudaSuccess) x = launch_jobs_reset<R>(K, dchk, st, (unsigned long long)hin, cs);
+            cudaGraph_t got = nullptr;
+            const cudaError_t x2 = cudaStreamEndCapture(cs, &got);
+            if (x != cudaSuccess) { e = x; where = "theta-step prologue launches"; goto graph_done; }
+            if (x2 != cudaSuccess) { e = x2; where = "cudaStreamEndCapture(prologue)"; goto graph_done; }
+        }
+        {
+            // the prologue is a chain: its last node has no dependents
+            size_t nn = 0;
+            PIDE_GTRY(cudaGraphGetNodes(body_o, nullptr, &nn));
+            std::vector<cudaGraphNode_t> nodes(nn);
+            PIDE_GTRY(cudaGraphGetNodes(body_o, nodes.data(), &nn));
+            std::vector<cudaGraphNode_t> leaves;
+            for (auto nd : nodes) {
+                size_t nd_out = 0;
+                PIDE_GTRY(cudaGraphNodeGetDependentNodes(nd, nullptr, nullptr, &nd_out));
+                if (nd_out == 0) leaves.push_back(nd);
+            }
+            cudaGraphNodeParams cpi{};
+            cpi.type = cudaGraphNodeTypeConditional;
+            cpi.conditional.handle = hin;
+            cpi.conditional.type = cudaGraphCondTypeWhile;
+            cpi.conditional.size = 1;
+            cudaGraphNode_t inner = nullptr;
+            PIDE_GTRY(cudaGraphAddNode(&inner, body_o, leaves.data(), nullptr, leaves.size(), &cpi));
+            cudaGraph_t body_i = cpi.conditional.phGraph_out[0];
+            // one fixed-point iteration of every job still iterating
+            PIDE_GTRY(cudaStreamBeginCaptureToGraph(cs, body_i, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+            {
+                const JobsCtl head{st.conv, st.kconv, st.iter, 1};
+                const JobsCtl tail{st.conv, st.kconv, st.iter, 2};
+                cudaError_t x = launch_dst_col_jobs<R>(A0.da, (const DstColArgs<R>*)arr(L.da), K, head, upb, cs);
+                if (x == cudaSuccess) x = launch_dst_row_jobs<R>(A0.ra, (const DstRowArgs<R>*)arr(L.ra), K, head, upb, cs);
+                if (x == cudaSuccess) x = launch_jobs_check(K, dchk, st, kmax_all, (unsigned long long)hin, cs);
+                if (x == cudaSuccess) x = launch_col_jobs<R>(A0.cai, (const ColArgs<R>*)arr(L.cai), K, tail, upb, cs);
+                if (x == cudaSuccess) x = launch_row_inverse_jobs<R>(A0.iai, (const InvArgs<R>*)arr(L.iai), K, tail, upb, cs);
+                cudaGraph_t got = nullptr;
+                const cudaError_t x2 = cudaStreamEndCapture(cs, &got);
+                if (x != cudaSuccess) { e = x; where = "iteration launches"; goto graph_done; }
+                if (x2 != cudaSuccess) { e = x2; where = "cudaStreamEndCapture(iteration)"; goto graph_done; }
+            }
+            // after the iterations: statistics and the next theta step
+            PIDE_GTRY(cudaStreamBeginCaptureToGraph(cs, body_o, &inner, nullptr, 1, cudaStreamCaptureModeRelaxed));
+            {
+                const cudaError_t x = launch_step_tally(K, st, (const int*)arr(L.step_end), Tused,
+                                                        (unsigned long long)hout, cs);
+                cudaGraph_t got = nullptr;
+                const cudaError_t x2 = cudaStreamEndCapture(cs, &got);
+                if (x != cudaSuccess) { e = x; where = "launch_step_tally"; goto graph_done; }
+                if (x2 != cudaSuccess) { e = x2; where = "cudaStreamEndCapture(tally)"; goto graph_done; }
+            }
+        }
+        PIDE_GTRY(cudaGraphInstantiate(&ex, g, 0));
+        PIDE_GTRY(cudaGraphLaunch(ex, s));
+    }
+graph_done:
+#undef PIDE_GTRY
+    if (e != cudaSuccess) {
+        if (ex) cudaGraphExecDestroy(ex);
+        cudaGraphDestroy(g);
+        H->err = std::string("multi-job loop graph: ") + where + ": " + cudaGetErrorString(e);
+        H->broken = true;
+        return fail(H, PIDE2D_ERR_CUDA);
+    }
+    // 3. one synchronisation; the statistics back to the handles
+    std::vector<int> tot(K), mx(K), nc(K);
+    std::vector<double> lastv(K);
+    {
+        const cudaError_t es = cudaStreamSynchronize(s);
+        cudaGraphExecDestroy(ex);
+        cudaGraphDestroy(g);
+        PIDE_CUDA(es);
+        PIDE_CUDA(cudaMemcpyAsync(tot.data(), st.it_total, 4 * (size_t)K, cudaMemcpyDeviceToHost, s));
+        PIDE_CUDA(cudaMemcpyAsync(mx.data(), st.it_max, 4 * (size_t)K, cudaMemcpyDeviceToHost, s));
         PIDE_CUDA(cudaMemcpyAsync(nc.data(), st.nonconv, 4 * (size_t)K, cudaMemcpyDeviceToHost, s));
+        PIDE_CUDA(cudaMemcpyAsync(lastv.data(), st.last, 8 * (size_t)K, cudaMemcpyDeviceToHost, s));
         PIDE_CUDA(cudaStreamSynchronize(s));
     }
     for (int j = 0; j < K; ++j) {
+        pide2d* Hj = hs[j];
+        const int N = Hj->L.g.N;
+        Hj->stats.fp_iters_total += tot[j];
+        Hj->stats.fp_iters_max = std::max(Hj->stats.fp_iters_max, mx[j]);
+        Hj->stats.cell_iters += (double)N * N * (double)(tot[j] + Tused);
+        Hj->stats.last_resid = lastv[j];
         if (nc[j]) {
-            hs[j]->err = "fixed-point iteration not converged in a theta step (multi-job loop)";
-            hs[j]->group_nonconv = true;
+            Hj->err = "fixed-point iteration not converged in a theta step (multi-job loop)";
+            Hj->group_nonconv = true;
         }
     }
     return PIDE2D_OK;
@@ -1522,9 +1649,66 @@ static pide2d_status group_solve(pide2d* const* hs, int K, char* scratch, std::s
 namespace pide {
 void set_handle_stream(pide2d_t* h, void* stream) { h->stream = static_cast<cudaStream_t>(stream); }
 
-pide2d_status solve_group(pide2d_t* const* hs, int K, void* scratch, std::string* err) {
-    return hs[0]->grid.precision == PIDE2D_FP64 ? group_solve<double>(hs, K, static_cast<char*>(scratch), err)
-                                                 : group_solve<float>(hs, K, static_cast<char*>(scratch), err);
+pide2d_status solve_group(pide2d_t* const* hs, int K, void* scratch, int upb, std::string* err) {
+    return hs[0]->grid.precision == PIDE2D_FP64 ? group_solve<double>(hs, K, (char*)scratch, upb, err)
+                                                : group_solve<float>(hs, K, (char*)scratch, upb, err);
+}
+
+// Timed trial of the multi-job launch shape: the increment column pass
+// (forward FFT, product with the weight spectrum, inverse FFT) of K fresh
+// handles of one geometry, `reps` times with upb FFT units per block.  The
+// pass works in place on each handle's spectrum buffer, which the time loop
+// rewrites before reading, so the trial leaves the solution untouched.
+template <typename R>
+static pide2d_status time_col(pide2d* const* hs, int K, char* scratch, int upb, int reps, double* ms) {
+    pide2d* H = hs[0];
+    cudaStream_t s = H->stream;
+    std::vector<ColArgs<R>> arr(K);
+    for (int j = 0; j < K; ++j) {
+        pide2d* Hj = hs[j];
+        SolveSpec<R> sp{};
+        sp.Y = (St<R>*)Hj->field(0);
+        sp.BY = (St<R>*)Hj->field(Hj->by);
+        sp.W = Hj->at<St<R>>(R_W);
+        sp.far = 1;
+        sp.Kd = Hj->contract.strike;
+        sp.Wh = Hj->at<void>(R_WH);
+        sp.Whi = Hj->at<void>(R_WHI);
+        sp.theta = Hj->theta;
+        sp.ht = Hj->dt;
+        SolveArgs<R> A;
+        build_solve_args<R>(Hj, sp, &A);
+        arr[j] = A.cai;
+    }
+    PIDE_CUDA(cudaMemcpyAsync(scratch, arr.data(), sizeof(ColArgs<R>) * K, cudaMemcpyHostToDevice, s));
+    const JobsCtl all{nullptr, nullptr, nullptr, 0};
+    cudaEvent_t e0, e1;
+    PIDE_CUDA(cudaEventCreate(&e0));
+    PIDE_CUDA(cudaEventCreate(&e1));
+    pide2d_status st = PIDE2D_OK;
+    cudaError_t e = launch_col_jobs<R>(arr[0], (const ColArgs<R>*)scratch, K, all, upb, s);   // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_col_jobs<R>(arr[0], (const ColArgs<R>*)scratch, K, all, upb, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e != cudaSuccess) {
+        H->err = std::string("launch-shape trial: ") + cudaGetErrorString(e);
+        H->broken = true;
+        st = PIDE2D_ERR_CUDA;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = (double)t / reps;
+    return st;
+}
+
+pide2d_status time_col_jobs(pide2d_t* const* hs, int K, void* scratch, int upb, int reps, double* ms, std::string* err) {
+    const pide2d_status st = hs[0]->grid.precision == PIDE2D_FP64 ? time_col<double>(hs, K, (char*)scratch, upb, reps, ms)
+                                                                  : time_col<float>(hs, K, (char*)scratch, upb, reps, ms);
+    if (st != PIDE2D_OK) *err = hs[0]->err;
+    return st;
 }
 }  // namespace pide
 

@@ -89,6 +89,7 @@ template <typename R> struct DstColArgs {
     R* E;
     const R* sin2;           // sin^2(pi k / (2N)), k = 0..N
     double c0, c1, c2, scale;// lambda = c0 + c1 sin2[k1] + c2 sin2[k2]; scale = (2/N)^2
+    R rc0, rc1, rc2, rscale; // the same, rounded once to the transform precision on the host
     const void* tw;
 };
 
@@ -127,14 +128,14 @@ template <typename R> struct PrepArgs {
 struct JobsCtl {
     const int* conv;         // per job: 1 once its loop stopped (converged, kmax or non-finite)
     const int* kconv;        // per job: the iteration at which it stopped
-    int iter;                // current iteration, 1-based
-    int mode;                // 0: every job; 1: jobs still iterating; 2: those and the ones stopped at `iter`
+    const int* iter;         // the current iteration, 1-based, on the device (written by the check kernel)
+    int mode;                // 0: every job; 1: jobs still iterating; 2: those and the ones stopped at *iter
 #ifdef __CUDACC__
     __device__ __forceinline__ bool skip(int j) const {
         if (mode == 0) return false;
         const int c = conv[j];
         if (mode == 1) return c != 0;
-        return c != 0 && kconv[j] < iter;
+        return c != 0 && kconv[j] < *iter;
     }
 #endif
 };
@@ -150,16 +151,19 @@ template <typename R> cudaError_t launch_prep(const PrepArgs<R>& a, cudaStream_t
 template <typename R> cudaError_t launch_row_dst(const Geometry& g, const double* src, R* E, const void* tw,
                                                 cudaStream_t s);
 // the same kernels over K jobs of one geometry (a0: any job's arguments, for the launch shape)
+// (upb: FFT units per block, <= 0 for the single-job shape; capped at 512 threads)
 template <typename R> cudaError_t launch_row_forward_jobs(const FwdArgs<R>& a0, const FwdArgs<R>* arr, int K,
-                                                         JobsCtl jc, cudaStream_t s);
+                                                         JobsCtl jc, int upb, cudaStream_t s);
 template <typename R> cudaError_t launch_col_jobs(const ColArgs<R>& a0, const ColArgs<R>* arr, int K, JobsCtl jc,
-                                                 cudaStream_t s);
+                                                 int upb, cudaStream_t s);
 template <typename R> cudaError_t launch_row_inverse_jobs(const InvArgs<R>& a0, const InvArgs<R>* arr, int K,
-                                                         JobsCtl jc, cudaStream_t s);
+                                                         JobsCtl jc, int upb, cudaStream_t s);
 template <typename R> cudaError_t launch_dst_col_jobs(const DstColArgs<R>& a0, const DstColArgs<R>* arr, int K,
-                                                     JobsCtl jc, cudaStream_t s);
+                                                     JobsCtl jc, int upb, cudaStream_t s);
 template <typename R> cudaError_t launch_dst_row_jobs(const DstRowArgs<R>& a0, const DstRowArgs<R>* arr, int K,
-                                                     JobsCtl jc, cudaStream_t s);
+                                                     JobsCtl jc, int upb, cudaStream_t s);
+// the single-job units per block of the FFT kernels at transform length P (0 if P is unsupported)
+int fft_units_per_block(int P, int prec_bytes);
 template <typename R> cudaError_t launch_prep_jobs(const PrepArgs<R>& a0, const PrepArgs<R>* arr, int K,
                                                   bool explicit_part, cudaStream_t s);
 // price-space jump operator (eqs. 3.12-3.17 on the paper's price grid); P x P transforms
@@ -274,9 +278,26 @@ struct JobsState {
     int* nonconv;            // [K] 1 if a theta step stopped without meeting the tolerance
     double* last;            // [K] last eq. 3.25 quantity
     int* active;             // jobs still iterating after the last check
+    int* iter;               // the current iteration of the theta step (1-based after the first check)
+    // statistics over the whole time loop, per job
+    int* it_total;           // [K] fixed-point iterations
+    int* it_step;            // [K] iterations of the current time step (the damped step has four theta steps)
+    int* it_max;             // [K] largest per-time-step count
+    int* step;               // theta steps done (one counter for the chunk)
 };
-template <typename R> cudaError_t launch_jobs_reset(int K, const JobCheck* jc, JobsState st, cudaStream_t s);
-template <typename R> cudaError_t launch_jobs_check(int K, const JobCheck* jc, JobsState st, int iter, cudaStream_t s);
+// resets the per-job stopping state and arms the graph condition `inner` of the iteration loop
+template <typename R> cudaError_t launch_jobs_reset(int K, const JobCheck* jc, JobsState st, unsigned long long inner,
+                                                  cudaStream_t s);
+// the stopping rule of every job after iteration *st.iter + 1 (incremented here); clears the
+// graph condition `cond` when no job iterates any more or kmax_all iterations were run
+cudaError_t launch_jobs_check(int K, const JobCheck* jc, JobsState st, int kmax_all, unsigned long long cond,
+                              cudaStream_t s);
+// dst (bytes) = blobs + (*st.step) * bytes: the argument arrays of the chunk's current theta step
+cudaError_t launch_step_select(const void* blobs, size_t bytes, JobsState st, void* dst, cudaStream_t s);
+// end of a theta step: fold each job's count into the statistics, advance *st.step, clear the
+// graph condition `cond` after `steps` theta steps; step_end[t] = 1 if theta step t ends a time step
+cudaError_t launch_step_tally(int K, JobsState st, const int* step_end, int steps, unsigned long long cond,
+                              cudaStream_t s);
 cudaError_t launch_fp_setup(FpCtl* ctl, void* Y, void* BY, int step_end, cudaStream_t s);
 
 // precompute (precompute.cu)

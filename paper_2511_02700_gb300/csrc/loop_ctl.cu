@@ -11,6 +11,8 @@
 // and theta.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace pide {
@@ -70,24 +72,35 @@ cudaError_t launch_fp_setup(FpCtl* ctl, void* Y, void* BY, int step_end, cudaStr
 }
 
 // ---------------------------------------------------------------------------
-// multi-job fixed-point loop (one launch per kernel over all jobs of a group):
-// the stopping rule of each job, and the count of jobs still iterating
+// multi-job time loop (one launch per kernel over all jobs of a chunk): the
+// whole loop of a chunk is one CUDA graph -- an outer while-node over the
+// theta steps (k_step_select picks the step's argument arrays, k_step_tally
+// advances the step) around an inner while-node over the fixed-point
+// iterations (k_jobs_check applies each job's stopping rule and ends the
+// inner loop when no job iterates any more)
 // ---------------------------------------------------------------------------
+// start of a theta step's iterations: every job iterating again, and the inner
+// loop's condition armed (a conditional handle keeps the value the previous
+// theta step's last check left)
 template <typename R>
-__global__ void k_jobs_reset(int K, const JobCheck* jc, JobsState st) {
+__global__ void k_jobs_reset(int K, const JobCheck* jc, JobsState st, cudaGraphConditionalHandle inner) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < K; j += gridDim.x * blockDim.x) {
         st.conv[j] = 0;
         st.kconv[j] = 0;
         st.kcount[j] = 0;
         *(double*)jc[j].resid = 0.0;
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *st.iter = 0;
+        cudaGraphSetConditional(inner, 1);
+    }
 }
 
-template <typename R>
-__global__ void k_jobs_check(int K, const JobCheck* jc, JobsState st, int iter) {
+__global__ void k_jobs_check(int K, const JobCheck* jc, JobsState st, int kmax_all, cudaGraphConditionalHandle h) {
     __shared__ int act;
     if (threadIdx.x == 0) act = 0;
     __syncthreads();
+    const int iter = *st.iter + 1;
     int mine = 0;
     for (int j = threadIdx.x; j < K; j += blockDim.x) {
         if (st.conv[j]) continue;
@@ -107,25 +120,68 @@ __global__ void k_jobs_check(int K, const JobCheck* jc, JobsState st, int iter) 
     }
     if (mine) atomicAdd(&act, mine);
     __syncthreads();
-    if (threadIdx.x == 0) *st.active = act;
+    if (threadIdx.x == 0) {
+        *st.iter = iter;                    // read by the kernels after this one (JobsCtl::skip)
+        *st.active = act;
+        if (act == 0 || iter >= kmax_all) cudaGraphSetConditional(h, 0);
+    }
+}
+
+__global__ void k_step_select(const uint4* __restrict__ blobs, size_t n16, JobsState st, uint4* __restrict__ dst) {
+    const uint4* src = blobs + (size_t)(*st.step) * n16;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+__global__ void k_step_tally(int K, JobsState st, const int* step_end, int steps, cudaGraphConditionalHandle h) {
+    const int t = *st.step;
+    const int end = step_end[t];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < K; j += gridDim.x * blockDim.x) {
+        const int k = st.kcount[j];
+        st.it_total[j] += k;
+        const int sk = st.it_step[j] + k;
+        if (end) {
+            if (sk > st.it_max[j]) st.it_max[j] = sk;
+            st.it_step[j] = 0;
+        } else {
+            st.it_step[j] = sk;
+        }
+    }
+    // one block: every thread has read *st.step before thread 0 advances it
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *st.step = t + 1;
+        if (t + 1 >= steps) cudaGraphSetConditional(h, 0);
+    }
 }
 
 template <typename R>
-cudaError_t launch_jobs_reset(int K, const JobCheck* jc, JobsState st, cudaStream_t s) {
-    k_jobs_reset<R><<<(K + 255) / 256, 256, 0, s>>>(K, jc, st);
+cudaError_t launch_jobs_reset(int K, const JobCheck* jc, JobsState st, unsigned long long inner, cudaStream_t s) {
+    k_jobs_reset<R><<<(K + 255) / 256, 256, 0, s>>>(K, jc, st, (cudaGraphConditionalHandle)inner);
     return cudaGetLastError();
 }
 
-template <typename R>
-cudaError_t launch_jobs_check(int K, const JobCheck* jc, JobsState st, int iter, cudaStream_t s) {
-    k_jobs_check<R><<<1, 1024, 0, s>>>(K, jc, st, iter);
+cudaError_t launch_jobs_check(int K, const JobCheck* jc, JobsState st, int kmax_all, unsigned long long cond,
+                              cudaStream_t s) {
+    k_jobs_check<<<1, 1024, 0, s>>>(K, jc, st, kmax_all, (cudaGraphConditionalHandle)cond);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_jobs_reset<float>(int, const JobCheck*, JobsState, cudaStream_t);
-template cudaError_t launch_jobs_reset<double>(int, const JobCheck*, JobsState, cudaStream_t);
-template cudaError_t launch_jobs_check<float>(int, const JobCheck*, JobsState, int, cudaStream_t);
-template cudaError_t launch_jobs_check<double>(int, const JobCheck*, JobsState, int, cudaStream_t);
+cudaError_t launch_step_select(const void* blobs, size_t bytes, JobsState st, void* dst, cudaStream_t s) {
+    const size_t n16 = bytes / 16;
+    const int blocks = (int)std::min<size_t>((n16 + 255) / 256, 1024);
+    k_step_select<<<blocks, 256, 0, s>>>((const uint4*)blobs, n16, st, (uint4*)dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_tally(int K, JobsState st, const int* step_end, int steps, unsigned long long cond,
+                              cudaStream_t s) {
+    k_step_tally<<<1, 1024, 0, s>>>(K, st, step_end, steps, (cudaGraphConditionalHandle)cond);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_jobs_reset<float>(int, const JobCheck*, JobsState, unsigned long long, cudaStream_t);
+template cudaError_t launch_jobs_reset<double>(int, const JobCheck*, JobsState, unsigned long long, cudaStream_t);
 
 template cudaError_t launch_fp_check<float>(const void*, FpCtl*, double, int, unsigned long long, cudaStream_t);
 template cudaError_t launch_fp_check<double>(const void*, FpCtl*, double, int, unsigned long long, cudaStream_t);

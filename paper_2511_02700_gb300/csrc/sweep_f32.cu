@@ -16,11 +16,11 @@ namespace pide {
     template cudaError_t launch_ps_rows_fwd<R>(int, const R*, int, void*, const void*, cudaStream_t); \
     template cudaError_t launch_ps_col<R>(int, void*, const void*, int, int, const void*, cudaStream_t); \
     template cudaError_t launch_ps_rows_inv<R>(int, const void*, int, double*, int, const void*, cudaStream_t); \
-    template cudaError_t launch_row_forward_jobs<R>(const FwdArgs<R>&, const FwdArgs<R>*, int, JobsCtl, cudaStream_t); \
-    template cudaError_t launch_col_jobs<R>(const ColArgs<R>&, const ColArgs<R>*, int, JobsCtl, cudaStream_t); \
-    template cudaError_t launch_row_inverse_jobs<R>(const InvArgs<R>&, const InvArgs<R>*, int, JobsCtl, cudaStream_t); \
-    template cudaError_t launch_dst_col_jobs<R>(const DstColArgs<R>&, const DstColArgs<R>*, int, JobsCtl, cudaStream_t); \
-    template cudaError_t launch_dst_row_jobs<R>(const DstRowArgs<R>&, const DstRowArgs<R>*, int, JobsCtl, cudaStream_t); \
+    template cudaError_t launch_row_forward_jobs<R>(const FwdArgs<R>&, const FwdArgs<R>*, int, JobsCtl, int, cudaStream_t); \
+    template cudaError_t launch_col_jobs<R>(const ColArgs<R>&, const ColArgs<R>*, int, JobsCtl, int, cudaStream_t); \
+    template cudaError_t launch_row_inverse_jobs<R>(const InvArgs<R>&, const InvArgs<R>*, int, JobsCtl, int, cudaStream_t); \
+    template cudaError_t launch_dst_col_jobs<R>(const DstColArgs<R>&, const DstColArgs<R>*, int, JobsCtl, int, cudaStream_t); \
+    template cudaError_t launch_dst_row_jobs<R>(const DstRowArgs<R>&, const DstRowArgs<R>*, int, JobsCtl, int, cudaStream_t); \
     template cudaError_t launch_prep_jobs<R>(const PrepArgs<R>&, const PrepArgs<R>*, int, bool, cudaStream_t); \
     template cudaError_t launch_weights_col<R>(const Geometry&, const void*, void*, void*, const void*, \
                                                cudaStream_t);                                       \
@@ -33,4 +33,17 @@ namespace pide {
 PIDE_INSTANTIATE(PIDE_PREC)
 #undef PIDE_INSTANTIATE
 
+}  // namespace pide
+
+namespace pide {
+int fft_units_per_block(int P, int prec_bytes) {
+#define CASE(PP) return prec_bytes == 4 ? Cfg<float, PP>::UNITS : Cfg<double, PP>::UNITS;
+    switch (P) {
+        case 16: CASE(16); case 32: CASE(32); case 64: CASE(64); case 128: CASE(128);
+        case 256: CASE(256); case 512: CASE(512); case 1024: CASE(1024);
+        case 2048: CASE(2048); case 4096: CASE(4096); case 8192: CASE(8192);
+        default: return 0;
+    }
+#undef CASE
+}
 }  // namespace pide

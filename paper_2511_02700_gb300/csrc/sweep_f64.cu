@@ -16,11 +16,11 @@ namespace pide {
     template cudaError_t launch_ps_rows_fwd<R>(int, const R*, int, void*, const void*, cudaStream_t); \
     template cudaError_t launch_ps_col<R>(int, void*, const void*, int, int, const void*, cudaStream_t); \
     template cudaError_t launch_ps_rows_inv<R>(int, const void*, int, double*, int, const void*, cudaStream_t); \
-    template cudaError_t launch_row_forward_jobs<R>(const FwdArgs<R>&, const FwdArgs<R>*, int, JobsCtl, cudaStream_t); \
-    template cudaError_t launch_col_jobs<R>(const ColArgs<R>&, const ColArgs<R>*, int, JobsCtl, cudaStream_t); \
-    template cudaError_t launch_row_inverse_jobs<R>(const InvArgs<R>&, const InvArgs<R>*, int, JobsCtl, cudaStream_t); \
-    template cudaError_t launch_dst_col_jobs<R>(const DstColArgs<R>&, const DstColArgs<R>*, int, JobsCtl, cudaStream_t); \
-    template cudaError_t launch_dst_row_jobs<R>(const DstRowArgs<R>&, const DstRowArgs<R>*, int, JobsCtl, cudaStream_t); \
+    template cudaError_t launch_row_forward_jobs<R>(const FwdArgs<R>&, const FwdArgs<R>*, int, JobsCtl, int, cudaStream_t); \
+    template cudaError_t launch_col_jobs<R>(const ColArgs<R>&, const ColArgs<R>*, int, JobsCtl, int, cudaStream_t); \
+    template cudaError_t launch_row_inverse_jobs<R>(const InvArgs<R>&, const InvArgs<R>*, int, JobsCtl, int, cudaStream_t); \
+    template cudaError_t launch_dst_col_jobs<R>(const DstColArgs<R>&, const DstColArgs<R>*, int, JobsCtl, int, cudaStream_t); \
+    template cudaError_t launch_dst_row_jobs<R>(const DstRowArgs<R>&, const DstRowArgs<R>*, int, JobsCtl, int, cudaStream_t); \
     template cudaError_t launch_prep_jobs<R>(const PrepArgs<R>&, const PrepArgs<R>*, int, bool, cudaStream_t); \
     template cudaError_t launch_weights_col<R>(const Geometry&, const void*, void*, void*, const void*, \
                                                cudaStream_t);                                       \

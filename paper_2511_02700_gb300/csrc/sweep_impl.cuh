@@ -38,6 +38,10 @@ template <typename R, int P> struct Cfg {
     static constexpr int ULEN = padded_len(P) + 4;
     static constexpr int MINB = (sizeof(R) == 4 ? 1024 : 512) / THREADS;
     static constexpr size_t SMEM = (size_t)UNITS * ULEN * sizeof(cpx<R>);
+    // multi-job kernels: launched with any number of units per block up to
+    // MAXT threads (the batch picks it by timed trials), same register target
+    static constexpr int MAXT = THREADS > 512 ? THREADS : 512;
+    static constexpr int JMINB = (sizeof(R) == 4 ? 1024 : 512) / MAXT > 0 ? (sizeof(R) == 4 ? 1024 : 512) / MAXT : 1;
 };
 
 template <typename R>
@@ -94,7 +98,8 @@ __device__ __forceinline__ double stop_ratio(double d, double y) { return fabs(d
 // a warp's candidate for the eq. 3.25 maximum (shared-memory reduction slot)
 struct StopCand {
     double q;      // its ratio in the transform precision (-1: no node)
-    double v;      // its ratio in FP64
+    double d;      // its increment
+    double y;      // its state value (FP64 of the stored state)
     int bad;       // a non-finite ratio or state was seen
     int pad;
 };
@@ -111,12 +116,13 @@ void set_smem(K kernel, size_t bytes) {
 }  // namespace
 
 #define PIDE_FFT_KERNEL(R, P) __global__ void __launch_bounds__(Cfg<R, P>::THREADS, Cfg<R, P>::MINB)
+#define PIDE_FFT_JOBS_KERNEL(R, P) __global__ void __launch_bounds__(Cfg<R, P>::MAXT, Cfg<R, P>::JMINB)
 
 // ---------------------------------------------------------------------------
 // forward row pass: T_in along s1 (from staged nodes) + packed R2C
 // ---------------------------------------------------------------------------
 template <typename R, int P>
-__device__ __forceinline__ void row_forward_body(const FwdArgs<R>& a) {
+__device__ __forceinline__ void row_forward_body(const FwdArgs<R>& a, int upb) {
     using C = cpx<R>;
     using CF = Cfg<R, P>;
     constexpr int NT = CF::NT, N = P / 2;
@@ -124,7 +130,7 @@ __device__ __forceinline__ void row_forward_body(const FwdArgs<R>& a) {
     const int unit = threadIdx.x / NT, t = threadIdx.x - unit * NT;
     C* buf = reinterpret_cast<C*>(smem_raw) + (size_t)unit * CF::ULEN;
     R* nodes = reinterpret_cast<R*>(buf);
-    const int p = blockIdx.x * CF::UNITS + unit;
+    const int p = blockIdx.x * upb + unit;
     const bool valid = p < a.npairs;
     const int rho = 2 * (a.pair0 + p);
     const C* tw = (const C*)a.tw;
@@ -192,11 +198,11 @@ __device__ __forceinline__ void row_forward_body(const FwdArgs<R>& a) {
     }
 }
 template <typename R, int P>
-PIDE_FFT_KERNEL(R, P) k_row_forward(const __grid_constant__ FwdArgs<R> a) { row_forward_body<R, P>(a); }
+PIDE_FFT_KERNEL(R, P) k_row_forward(const __grid_constant__ FwdArgs<R> a) { row_forward_body<R, P>(a, Cfg<R, P>::UNITS); }
 template <typename R, int P>
-PIDE_FFT_KERNEL(R, P) k_row_forward_jobs(const FwdArgs<R>* __restrict__ arr, JobsCtl jc) {
+PIDE_FFT_JOBS_KERNEL(R, P) k_row_forward_jobs(const FwdArgs<R>* __restrict__ arr, JobsCtl jc) {
     if (jc.skip(blockIdx.y)) return;
-    row_forward_body<R, P>(arr[blockIdx.y]);
+    row_forward_body<R, P>(arr[blockIdx.y], blockDim.x / Cfg<R, P>::NT);
 }
 
 // ---------------------------------------------------------------------------
@@ -204,14 +210,14 @@ PIDE_FFT_KERNEL(R, P) k_row_forward_jobs(const FwdArgs<R>* __restrict__ arr, Job
 // conj(w^)/P^2 in the last forward stage, inverse FFT writing rows 1..N
 // ---------------------------------------------------------------------------
 template <typename R, int P>
-__device__ __forceinline__ void col_body(const ColArgs<R>& a) {
+__device__ __forceinline__ void col_body(const ColArgs<R>& a, int upb) {
     using C = cpx<R>;
     using CF = Cfg<R, P>;
     constexpr int NT = CF::NT, N = P / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int unit = threadIdx.x / NT, t = threadIdx.x - unit * NT;
     C* buf = reinterpret_cast<C*>(smem_raw) + (size_t)unit * CF::ULEN;
-    const int k1 = blockIdx.x * CF::UNITS + unit;
+    const int k1 = blockIdx.x * upb + unit;
     const bool valid = k1 <= P / 2;
     constexpr int Gc = cgroup<R>();
     const int g = k1 / Gc, c = k1 - g * Gc;
@@ -260,11 +266,11 @@ __device__ __forceinline__ void col_body(const ColArgs<R>& a) {
     block_fft<R, +1, P>(buf, t, tw, SmemLoad<R>{buf}, store_out);
 }
 template <typename R, int P>
-PIDE_FFT_KERNEL(R, P) k_col(const __grid_constant__ ColArgs<R> a) { col_body<R, P>(a); }
+PIDE_FFT_KERNEL(R, P) k_col(const __grid_constant__ ColArgs<R> a) { col_body<R, P>(a, Cfg<R, P>::UNITS); }
 template <typename R, int P>
-PIDE_FFT_KERNEL(R, P) k_col_jobs(const ColArgs<R>* __restrict__ arr, JobsCtl jc) {
+PIDE_FFT_JOBS_KERNEL(R, P) k_col_jobs(const ColArgs<R>* __restrict__ arr, JobsCtl jc) {
     if (jc.skip(blockIdx.y)) return;
-    col_body<R, P>(arr[blockIdx.y]);
+    col_body<R, P>(arr[blockIdx.y], blockDim.x / Cfg<R, P>::NT);
 }
 
 // ---------------------------------------------------------------------------
@@ -292,7 +298,7 @@ __device__ __forceinline__ void prefetch_inverse_rows(const InvArgs<R>& a, const
 }
 
 template <typename R, int P>
-__device__ __forceinline__ void row_inverse_body(const InvArgs<R>& a) {
+__device__ __forceinline__ void row_inverse_body(const InvArgs<R>& a, int upb) {
     using C = cpx<R>;
     using S_ = St<R>;
     using CF = Cfg<R, P>;
@@ -300,7 +306,7 @@ __device__ __forceinline__ void row_inverse_body(const InvArgs<R>& a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int unit = threadIdx.x / NT, t = threadIdx.x - unit * NT;
     C* buf = reinterpret_cast<C*>(smem_raw) + (size_t)unit * CF::ULEN;
-    const int p = blockIdx.x * CF::UNITS + unit;
+    const int p = blockIdx.x * upb + unit;
     const int m2 = 2 * p + 1;
     const bool valid = m2 <= N - 1;
     const bool hasb = valid && (m2 + 1 <= N - 1);
@@ -408,26 +414,26 @@ PIDE_FFT_KERNEL(R, P) k_row_inverse(const __grid_constant__ InvArgs<R> a0) {
     __shared__ InvArgs<R> sa;
     if (threadIdx.x == 0) sa = a0;
     __syncthreads();
-    row_inverse_body<R, P>(sa);
+    row_inverse_body<R, P>(sa, Cfg<R, P>::UNITS);
 }
 template <typename R, int P>
-PIDE_FFT_KERNEL(R, P) k_row_inverse_jobs(const InvArgs<R>* __restrict__ arr, JobsCtl jc) {
+PIDE_FFT_JOBS_KERNEL(R, P) k_row_inverse_jobs(const InvArgs<R>* __restrict__ arr, JobsCtl jc) {
     if (jc.skip(blockIdx.y)) return;
-    row_inverse_body<R, P>(arr[blockIdx.y]);
+    row_inverse_body<R, P>(arr[blockIdx.y], blockDim.x / Cfg<R, P>::NT);
 }
 
 // ---------------------------------------------------------------------------
 // column DST pass with the eigenvalue division between the two transforms
 // ---------------------------------------------------------------------------
 template <typename R, int P>
-__device__ __forceinline__ void dst_col_body(const DstColArgs<R>& a) {
+__device__ __forceinline__ void dst_col_body(const DstColArgs<R>& a, int upb) {
     using C = cpx<R>;
     using CF = Cfg<R, P>;
     constexpr int NT = CF::NT, N = P / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int unit = threadIdx.x / NT, t = threadIdx.x - unit * NT;
     C* buf = reinterpret_cast<C*>(smem_raw) + (size_t)unit * CF::ULEN;
-    const int u = blockIdx.x * CF::UNITS + unit;
+    const int u = blockIdx.x * upb + unit;
     const int ka = 2 * u, kb = ka + 1;
     const bool valid = ka < N;
     constexpr int GE = rgroup<R>();
@@ -444,7 +450,7 @@ __device__ __forceinline__ void dst_col_body(const DstColArgs<R>& a) {
         }
         return mk<R>(xa, xb);
     };
-    const R c0 = (R)a.c0, c1 = (R)a.c1, c2 = (R)a.c2, sc = (R)a.scale;
+    const R c0 = a.rc0, c1 = a.rc1, c2 = a.rc2, sc = a.rscale;
     const R sa = valid ? a.sin2[ka] : R(0);
     const R sb = valid ? a.sin2[kb] : R(0);
     auto divide = [&](int k2, C zz) {
@@ -470,11 +476,11 @@ __device__ __forceinline__ void dst_col_body(const DstColArgs<R>& a) {
     block_fft<R, -1, P>(buf, t, tw, SmemLoad<R>{buf}, store);
 }
 template <typename R, int P>
-PIDE_FFT_KERNEL(R, P) k_dst_col(const __grid_constant__ DstColArgs<R> a) { dst_col_body<R, P>(a); }
+PIDE_FFT_KERNEL(R, P) k_dst_col(const __grid_constant__ DstColArgs<R> a) { dst_col_body<R, P>(a, Cfg<R, P>::UNITS); }
 template <typename R, int P>
-PIDE_FFT_KERNEL(R, P) k_dst_col_jobs(const DstColArgs<R>* __restrict__ arr, JobsCtl jc) {
+PIDE_FFT_JOBS_KERNEL(R, P) k_dst_col_jobs(const DstColArgs<R>* __restrict__ arr, JobsCtl jc) {
     if (jc.skip(blockIdx.y)) return;
-    dst_col_body<R, P>(arr[blockIdx.y]);
+    dst_col_body<R, P>(arr[blockIdx.y], blockDim.x / Cfg<R, P>::NT);
 }
 
 // ---------------------------------------------------------------------------
@@ -482,15 +488,15 @@ PIDE_FFT_KERNEL(R, P) k_dst_col_jobs(const DstColArgs<R>* __restrict__ arr, Jobs
 // row pass of the increment's B_w sweep (packed R2C) in the same block
 // ---------------------------------------------------------------------------
 template <typename R, int P>
-__device__ __forceinline__ void dst_row_body(const DstRowArgs<R>& a) {
+__device__ __forceinline__ void dst_row_body(const DstRowArgs<R>& a, int upb) {
     using C = cpx<R>;
     using CF = Cfg<R, P>;
     constexpr int NT = CF::NT, N = P / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int unit = threadIdx.x / NT, t = threadIdx.x - unit * NT;
     C* buf = reinterpret_cast<C*>(smem_raw) + (size_t)unit * CF::ULEN;
-    StopCand* red = reinterpret_cast<StopCand*>(reinterpret_cast<C*>(smem_raw) + (size_t)CF::UNITS * CF::ULEN);
-    const int p = blockIdx.x * CF::UNITS + unit;
+    StopCand* red = reinterpret_cast<StopCand*>(reinterpret_cast<C*>(smem_raw) + (size_t)upb * CF::ULEN);
+    const int p = blockIdx.x * upb + unit;
     const int m2 = 2 * p + 1;
     const bool valid = m2 <= N - 1;
     const bool hasb = valid && (m2 + 1 <= N - 1);
@@ -561,10 +567,9 @@ __device__ __forceinline__ void dst_row_body(const DstRowArgs<R>& a) {
     block_fft<R, -1, P>(buf, t, tw, load, update);
     // (reduced here, before the second transform, so the candidate's registers
     // are free during it)
-    // block maximum of eq. 3.25 in FP64, one atomic per block: each warp's
+    // block maximum of eq. 3.25 in FP64, one atomic per block: the block's
     // node with the largest ratio in the transform precision is re-evaluated
-    // in FP64 from its D and Y (as stored), and the block keeps the FP64 value
-    // of the warp with the largest transform-precision ratio.  With FP32
+    // in FP64 from its D and Y (as stored).  With FP32
     // ratios (two roundings of Y, 2 ulp of the quotient) the FP64 value found
     // is within 2^-20 relative of the exact FP64 maximum.
     for (int o = 16; o > 0; o >>= 1) {
@@ -575,17 +580,18 @@ __device__ __forceinline__ void dst_row_body(const DstRowArgs<R>& a) {
     }
     bad = __any_sync(0xffffffffu, bad);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
-    if (lane == 0) red[warp] = StopCand{(double)qmax, fabs((double)dsel) / fmax(1.0, fabs(st_dbl(ysel))), bad ? 1 : 0};
+    if (lane == 0) red[warp] = StopCand{(double)qmax, (double)dsel, st_dbl(ysel), bad ? 1 : 0, 0};
     __syncthreads();
     if (threadIdx.x == 0) {
         StopCand c = red[0];
         for (int w = 1; w < nwarp; ++w) {
             const StopCand o = red[w];
-            if (o.q > c.q) { c.q = o.q; c.v = o.v; }
+            if (o.q > c.q) { c.q = o.q; c.d = o.d; c.y = o.y; }
             c.bad |= o.bad;
         }
         // +inf for a non-finite block: the loop stops, not converged
-        const double v = c.bad ? __longlong_as_double(0x7ff0000000000000LL) : (c.q >= 0.0 ? c.v : 0.0);
+        const double v = c.bad ? __longlong_as_double(0x7ff0000000000000LL)
+                               : (c.q >= 0.0 ? fabs(c.d) / fmax(1.0, fabs(c.y)) : 0.0);
         atomicMax((unsigned long long*)a.resid, (unsigned long long)__double_as_longlong(v));
     }
     // packed R2C of the two increment rows -> spectrum rows rho = m2 + N/2 + 1, +1
@@ -616,11 +622,11 @@ __device__ __forceinline__ void dst_row_body(const DstRowArgs<R>& a) {
     }
 }
 template <typename R, int P>
-PIDE_FFT_KERNEL(R, P) k_dst_row(const __grid_constant__ DstRowArgs<R> a) { dst_row_body<R, P>(a); }
+PIDE_FFT_KERNEL(R, P) k_dst_row(const __grid_constant__ DstRowArgs<R> a) { dst_row_body<R, P>(a, Cfg<R, P>::UNITS); }
 template <typename R, int P>
-PIDE_FFT_KERNEL(R, P) k_dst_row_jobs(const DstRowArgs<R>* __restrict__ arr, JobsCtl jc) {
+PIDE_FFT_JOBS_KERNEL(R, P) k_dst_row_jobs(const DstRowArgs<R>* __restrict__ arr, JobsCtl jc) {
     if (jc.skip(blockIdx.y)) return;
-    dst_row_body<R, P>(arr[blockIdx.y]);
+    dst_row_body<R, P>(arr[blockIdx.y], blockDim.x / Cfg<R, P>::NT);
 }
 
 // ---------------------------------------------------------------------------
@@ -1033,51 +1039,66 @@ cudaError_t launch_fft_kernel(K kernel, const A& a, int work_units, size_t extra
     return cudaGetLastError();
 }
 
+// units per block of a multi-job launch: upb <= 0 selects the single-job shape
+template <typename R, int P>
+int jobs_units(int upb) {
+    using CF = Cfg<R, P>;
+    if (upb <= 0) return CF::UNITS;
+    const int mx = CF::MAXT / CF::NT;
+    return upb < mx ? upb : mx;
+}
+
 template <typename R, int P, class K, class A>
 cudaError_t launch_fft_kernel_jobs(K kernel, const A* arr, int njobs, JobsCtl jc, int work_units, size_t extra_smem,
-                                   cudaStream_t s) {
+                                   int upb, cudaStream_t s) {
     using CF = Cfg<R, P>;
-    const size_t smem = CF::SMEM + extra_smem;
+    const int u = jobs_units<R, P>(upb);
+    const size_t smem = (size_t)u * CF::ULEN * sizeof(cpx<R>) + extra_smem;
     set_smem(kernel, smem);
-    const dim3 grid((work_units + CF::UNITS - 1) / CF::UNITS, njobs);
-    kernel<<<grid, CF::THREADS, smem, s>>>(arr, jc);
+    const dim3 grid((work_units + u - 1) / u, njobs);
+    kernel<<<grid, u * CF::NT, smem, s>>>(arr, jc);
     return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t launch_row_forward_jobs(const FwdArgs<R>& a0, const FwdArgs<R>* arr, int K, JobsCtl jc, cudaStream_t s) {
-#define CASE(PP) return launch_fft_kernel_jobs<R, PP>(k_row_forward_jobs<R, PP>, arr, K, jc, a0.npairs, 0, s);
+cudaError_t launch_row_forward_jobs(const FwdArgs<R>& a0, const FwdArgs<R>* arr, int K, JobsCtl jc, int upb,
+                              cudaStream_t s) {
+#define CASE(PP) return launch_fft_kernel_jobs<R, PP>(k_row_forward_jobs<R, PP>, arr, K, jc, a0.npairs, 0, upb, s);
     PIDE_SWITCH_P(a0.g.P, CASE)
 #undef CASE
 }
 template <typename R>
-cudaError_t launch_col_jobs(const ColArgs<R>& a0, const ColArgs<R>* arr, int K, JobsCtl jc, cudaStream_t s) {
+cudaError_t launch_col_jobs(const ColArgs<R>& a0, const ColArgs<R>* arr, int K, JobsCtl jc, int upb,
+                              cudaStream_t s) {
 #define CASE(PP)                                                                                             \
-    if constexpr (LoopSize<R, PP>::ok) return launch_fft_kernel_jobs<R, PP>(k_col_jobs<R, PP>, arr, K, jc, PP / 2 + 1, 0, s); \
+    if constexpr (LoopSize<R, PP>::ok) return launch_fft_kernel_jobs<R, PP>(k_col_jobs<R, PP>, arr, K, jc, PP / 2 + 1, 0, upb, s); \
     else return cudaErrorInvalidValue;
     PIDE_SWITCH_P(a0.g.P, CASE)
 #undef CASE
 }
 template <typename R>
-cudaError_t launch_row_inverse_jobs(const InvArgs<R>& a0, const InvArgs<R>* arr, int K, JobsCtl jc, cudaStream_t s) {
+cudaError_t launch_row_inverse_jobs(const InvArgs<R>& a0, const InvArgs<R>* arr, int K, JobsCtl jc, int upb,
+                              cudaStream_t s) {
 #define CASE(PP)                                                                                             \
-    if constexpr (LoopSize<R, PP>::ok) return launch_fft_kernel_jobs<R, PP>(k_row_inverse_jobs<R, PP>, arr, K, jc, PP / 4, 0, s); \
+    if constexpr (LoopSize<R, PP>::ok) return launch_fft_kernel_jobs<R, PP>(k_row_inverse_jobs<R, PP>, arr, K, jc, PP / 4, 0, upb, s); \
     else return cudaErrorInvalidValue;
     PIDE_SWITCH_P(a0.g.P, CASE)
 #undef CASE
 }
 template <typename R>
-cudaError_t launch_dst_col_jobs(const DstColArgs<R>& a0, const DstColArgs<R>* arr, int K, JobsCtl jc, cudaStream_t s) {
+cudaError_t launch_dst_col_jobs(const DstColArgs<R>& a0, const DstColArgs<R>* arr, int K, JobsCtl jc, int upb,
+                              cudaStream_t s) {
 #define CASE(PP)                                                                                             \
-    if constexpr (LoopSize<R, PP>::ok) return launch_fft_kernel_jobs<R, PP>(k_dst_col_jobs<R, PP>, arr, K, jc, PP / 4, 0, s); \
+    if constexpr (LoopSize<R, PP>::ok) return launch_fft_kernel_jobs<R, PP>(k_dst_col_jobs<R, PP>, arr, K, jc, PP / 4, 0, upb, s); \
     else return cudaErrorInvalidValue;
     PIDE_SWITCH_P(a0.g.P, CASE)
 #undef CASE
 }
 template <typename R>
-cudaError_t launch_dst_row_jobs(const DstRowArgs<R>& a0, const DstRowArgs<R>* arr, int K, JobsCtl jc, cudaStream_t s) {
+cudaError_t launch_dst_row_jobs(const DstRowArgs<R>& a0, const DstRowArgs<R>* arr, int K, JobsCtl jc, int upb,
+                              cudaStream_t s) {
 #define CASE(PP)                                                                                             \
-    if constexpr (LoopSize<R, PP>::ok) return launch_fft_kernel_jobs<R, PP>(k_dst_row_jobs<R, PP>, arr, K, jc, PP / 4, 32 * sizeof(StopCand), s); \
+    if constexpr (LoopSize<R, PP>::ok) return launch_fft_kernel_jobs<R, PP>(k_dst_row_jobs<R, PP>, arr, K, jc, PP / 4, 32 * sizeof(StopCand), upb, s); \
     else return cudaErrorInvalidValue;
     PIDE_SWITCH_P(a0.g.P, CASE)
 #undef CASE

@@ -18,7 +18,8 @@ def test_batch_workspace_bytes_and_arguments():
     jobs = [gpu_job(with_(w, n=n)) for w, n in zip(batch_draw(3), (64, 256, 128))]
     one = B.pide2d_workspace_bytes(jobs[1].grid)
     nb = B.pide2d_batch_workspace_bytes(jobs, 2)
-    assert nb >= 2 * one and nb < 2 * one + 64 * 1024      # two lanes + the multi-job argument arrays
+    # two lanes + the multi-job argument arrays of every theta step of the longest job (64 steps + 3)
+    assert nb >= 2 * one and nb < 2 * one + 1024 * 1024
     assert B.pide2d_batch_workspace_bytes(jobs, 8) == B.pide2d_batch_workspace_bytes(jobs, 3)
     with pytest.raises(B.PideError):
         B.pide2d_batch_workspace_bytes(jobs, 0)
@@ -114,3 +115,27 @@ def test_batch_fp32_bulk_prices_within_1e5_of_fp64():
         s.close()
         errs.append(abs(p32 - p64) / abs(p64))
     assert max(errs) <= 1e-5, [(w.name, e) for w, e in zip(ws, errs) if e > 1e-5]
+
+
+@pytest.mark.gpu
+def test_batch_launch_shape_trials_report_and_keep_prices():
+    """The timed trials pick a launch shape per geometry group (FFT units per
+    block, jobs per chunk) and report it; the shape changes how FFT units
+    share blocks, not what they compute, so the prices agree with the fixed
+    single-job shapes (up to a stop decision at the rounding level)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_02700_gb300 import binding as B
+    ws = [with_(w, n=(64, 128)[i % 2], steps=8) for i, w in enumerate(batch_draw(40, seed=21))]
+    jobs = [gpu_job(w) for w in ws]
+    p_fixed, s_fixed, st_fixed = B.solve_batch(jobs, lanes=40, fixed_shapes=True)
+    p_tuned, s_tuned, st_tuned = B.solve_batch(jobs, lanes=40)
+    assert all(x == 0 for x in s_fixed + s_tuned)
+    assert st_fixed.tuned == 0
+    tun = st_tuned.tuning()
+    assert st_tuned.tuned == 2 and sorted(t["n"] for t in tun) == [64, 128]
+    for t in tun:
+        assert t["units_per_block"] >= 1 and 1 <= t["lanes"] <= 20 and t["us_per_job_column_pass"] > 0
+    for a, b in zip(p_fixed, p_tuned):
+        assert abs(a - b) <= 1e-10 * abs(b), (a, b)

@@ -123,3 +123,29 @@ def test_large_workload_fp32_bulk_matches_fp64():
     roi = roi_mask(w32.n)
     assert abs(p32 - p64) <= 1e-5 * abs(p64), (p32, p64)
     assert np.abs(V32 - V64)[roi].max() <= 1e-5 * np.abs(V64[roi]).max()
+
+
+@pytest.mark.slow
+def test_single_asset_reduction_converges_at_the_prop31_rate():
+    """Payoff max(K - S1, 0) on the convergence-sweep option, FP64 mode,
+    N = 256 .. 2048 with N/4 steps: the error against the 1D Fourier price of
+    the oracle (Table A6 exponent) decreases at every refinement, and its
+    order over the finest pair reaches Prop. 3.1's rate 2 - 2 alpha (within
+    0.1) for alpha = 0.25, 0.5, 0.75 -- the integral-term quadrature error
+    dominates; the time error (second order) and the cubic interpolation
+    error are of higher order."""
+    import oracle as O
+    from paper_2511_02700_gb300.workloads import Workload
+    for alpha in (0.25, 0.5, 0.75):
+        m = O.model_from_subordinated_bm(alpha, 0.5, (-0.10, -0.05), (0.20, 0.25), 0.3, 0.03)
+        exact = O.put_price_1d(m, 0, 100.0, 100.0, 1.0)
+        errs = []
+        for n in (256, 512, 1024, 2048):
+            s = gpu_solver(Workload("sa", n=n, steps=n // 4, alpha=alpha, tol=1e-11, precision="fp64"), payoff=2)
+            p, _, _, st = s.solve()
+            s.close()
+            assert st == 0
+            errs.append(p - exact)
+        assert all(e > 0 for e in errs) and all(errs[i + 1] < errs[i] for i in range(3)), (alpha, errs)
+        order = math.log2(errs[2] / errs[3])
+        assert order >= 2.0 - 2.0 * alpha - 0.1, (alpha, errs, order)

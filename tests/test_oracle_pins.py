@@ -404,18 +404,26 @@ def test_table4_price_at_the_money(name):
 
 def test_single_asset_reduction_converges_to_fourier_price():
     """Payoff max(K - S1, 0): the 2D scheme is constant in s2 and its price
-    approaches the 1D NTS put by Fourier inversion (Table A6 exponent)."""
+    approaches the 1D NTS put by Fourier inversion (Table A6 exponent), at the
+    rate Prop. 3.1 gives for the integral term, 2 - 2 alpha = 1.5 at
+    alpha = 0.25 (time error O(h_t^2) with h_t = 4h/5 is of higher order, and
+    cubic interpolation contributes O(h^3)).  The grids N = 32..256 are in the
+    asymptotic range: successive error ratios stay near 2^1.5 (the observed
+    orders are 1.64, 1.75, 1.64 here and 1.58, 1.55, 1.53 up to N = 2048)."""
     m = wl_model(0.25)
     c = Contract(PUT_ASSET1, 100.0, 1.0)
     exact = put_price_1d(m, 0, 100.0, 100.0, 1.0)
     errs = []
-    for n in (32, 64, 128):
+    for n in (32, 64, 128, 256):
         res = Scheme(m, Grid(n), c, n // 4, tol=1e-11, sl_order=3).solve()
         # [m2, m1]: constant along s2 away from the s2 edges, where the far
         # field (discounted intrinsic value) is imposed on the whole edge
         assert np.ptp(res.V[3 * n // 8: 5 * n // 8 + 1, n // 2]) < 1e-6 * res.price
-        errs.append(abs(res.price - exact))
-    assert errs[2] < 0.03 and errs[2] < errs[1] < errs[0], errs
+        errs.append(res.price - exact)
+    assert all(e > 0 for e in errs), errs                  # the scheme prices from above here
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(3)]
+    assert all(1.4 < p < 1.9 for p in orders), (errs, orders)
+    assert errs[-1] < 0.006, errs
 
 
 def test_put_call_parity_and_positivity():
