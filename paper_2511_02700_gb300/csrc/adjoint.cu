@@ -213,6 +213,30 @@ __global__ void __launch_bounds__(kBX* kBY) k_sl_shift_dots(Geometry g, SlShiftA
     block_partials<2>(v, part);
 }
 
+// dst (R field, pitch ldR) = src (FP64 field, pitch ldS) at the interior nodes
+template <typename R>
+__global__ void k_field_to_r(Geometry g, const double* src, R* dst) {
+    const int m1 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int m2 = blockIdx.y * blockDim.y + threadIdx.y;
+    if (m1 < 1 || m2 < 1 || m1 > g.N - 1 || m2 > g.N - 1) return;
+    dst[(size_t)m2 * g.ldR + m1] = (R)src[(size_t)m2 * g.ldS + m1];
+}
+
+// per-block partial sums of a[i] b[i], i < n (grid-stride, a fixed number of blocks)
+__global__ void k_dot_plain(const double* a, const double* b, size_t n, double* part) {
+    __shared__ double red[256];
+    double x = 0.0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        x += a[i] * b[i];
+    red[threadIdx.x] = x;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
 // acc[d] += scale * sum_b part[b][d], one block, fixed order
 __global__ void k_reduce_add(const double* part, int nblocks, int nd, double* acc, double scale) {
     __shared__ double red[256];
@@ -292,6 +316,20 @@ cudaError_t launch_dot_field(const Geometry& g, const double* xi, const double* 
 }
 
 template <typename R>
+cudaError_t launch_field_to_r(const Geometry& g, const double* src, R* dst, cudaStream_t s) {
+    k_field_to_r<R><<<node_grid(g.N), dim3(kBX, kBY), 0, s>>>(g, src, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dot_plain(const Geometry& g, const double* a, const double* b, size_t n, double* part, double* acc,
+                             cudaStream_t s) {
+    const int nb = adjoint_dot_blocks(g.N);
+    k_dot_plain<<<nb, 256, 0, s>>>(a, b, n, part);
+    k_reduce_add<<<1, 256, 0, s>>>(part, nb, 1, acc, 1.0);
+    return cudaGetLastError();
+}
+
+template <typename R>
 cudaError_t launch_sl_shift_dots(const Geometry& g, const SlShiftArgs<R>& a, double* part, double* acc, double scale,
                                  cudaStream_t s) {
     const int nb = adjoint_dot_blocks(g.N);
@@ -310,7 +348,8 @@ cudaError_t launch_sl_shift_dots(const Geometry& g, const SlShiftArgs<R>& a, dou
     template cudaError_t launch_dots_state<R>(const Geometry&, const double*, const St<R>*, double*, double*,     \
                                               double, cudaStream_t);                                               \
     template cudaError_t launch_sl_shift_dots<R>(const Geometry&, const SlShiftArgs<R>&, double*, double*, double, \
-                                                 cudaStream_t);
+                                                 cudaStream_t);                                                    \
+    template cudaError_t launch_field_to_r<R>(const Geometry&, const double*, R*, cudaStream_t);
 PIDE_ADJ_INSTANTIATE(float)
 PIDE_ADJ_INSTANTIATE(double)
 #undef PIDE_ADJ_INSTANTIATE

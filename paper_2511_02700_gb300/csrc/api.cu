@@ -245,7 +245,7 @@ constexpr int kAdjAcc = 6;        // <xi,V>, <xi,dxx V>, <xi,dxy V>, <xi,dyy V>,
 constexpr size_t kMomentBytes = (moment_doubles() * 8 + 255) / 256 * 256;   // moment buffer, 256-aligned
 
 struct TapeLayout {
-    size_t ckpt, seg, fin, adj, spec, scr, acc, total;
+    size_t ckpt, seg, fin, adj, spec, dw, specx, cacc, cfield, scr, acc, total;
     size_t field, spec1, omega, part, rows, nparts;
     int nckpt, seg_slots;
 };
@@ -266,7 +266,11 @@ TapeLayout tape_layout(const Layout& L, int n_steps, int interval, int ndirs) {
     t.seg = o;   o += (size_t)t.seg_slots * 2 * t.field;
     t.fin = o;   o += 5 * t.field;                    // the final state, put back after the adjoint
     t.adj = o;   o += (size_t)A_COUNT * t.field;
-    t.spec = o;  o += (size_t)(2 + ndirs) * t.spec1;  // flipped Wh, Whi; one Wh per direction
+    t.spec = o;  o += 2 * t.spec1;                    // flipped Wh, Whi
+    t.dw = o;    o += (size_t)ndirs * t.omega;         // the weights' derivative along each direction
+    t.specx = o; o += align256(L.size[R_S]);           // spectrum rows of the adjoint field xi
+    t.cacc = o;  o += align256((size_t)(L.g.P / 2 + 1) * L.g.P * 16);   // FP64 sum of conj(xi^) V^
+    t.cfield = o; o += t.omega;                        // its inverse: the correlation at the N x N lags
     t.scr = o;   o += 3 * t.omega + t.part + kMomentBytes + 2 * 256 + t.rows + t.nparts;
     t.acc = o;   o += align256((size_t)(kAdjAcc + ndirs) * 8);
     t.total = o;
@@ -1765,23 +1769,50 @@ struct SavedState {
 }  // namespace
 
 // the contributions of one stored state V^j (far field at tau_j) with the
-// coefficient field xi: <xi, V>, <xi, D-parts V> and <xi, B_{dw_k} V>
+// coefficient field xi: <xi, V>, <xi, D-parts V>, and for the weights the
+// spectral product conj(xi^) V~^ added to the FP64 accumulator: summed over
+// the states and inverted once, it gives C(l) = sum_j sum_m xi_j(m) V~_j(m+l+1/2),
+// and <xi_j, B_{dw} V_j> summed over j = sum_l dw(l) C(l) for every direction
 template <typename R>
 static pide2d_status state_dots(pide2d* H, const TapeLayout& t, const St<R>* V, double tau, int ndirs) {
     const Geometry g = H->L.g;
+    const int N = g.N;
     char* scr = H->tape.base + t.scr;
     double* part = reinterpret_cast<double*>(scr + 3 * t.omega + t.part + kMomentBytes + 2 * 256 + t.rows);
     double* acc = reinterpret_cast<double*>(H->tape.base + t.acc);
     const double* xi = reinterpret_cast<const double*>(H->tape.base + t.adj + A_XI * t.field);
     PIDE_CUDA(launch_dots_state<R>(g, xi, V, part, acc, 1.0, H->stream));
-    const double Kd = H->contract.strike * std::exp(-H->model.r * tau);
-    double* out = H->at<double>(R_OUT);
-    for (int k = 0; k < ndirs; ++k) {
-        const void* Whk = H->tape.base + t.spec + (size_t)(2 + k) * t.spec1;
-        const pide2d_status js = jump_apply<R>(H, V, 1, Kd, Whk, out);
-        if (js != PIDE2D_OK) return js;
-        PIDE_CUDA(launch_dot_field(g, xi, out, part, acc + kAdjAcc + k, H->stream));
-    }
+    if (ndirs == 0) return PIDE2D_OK;
+    const void* tw = H->at<void>(R_TWR);
+    // V~ (midpoints, far field at tau) into the handle's spectrum buffer
+    FwdArgs<R> fa{};
+    fa.g = g;
+    fa.mode = FWD_FULL;
+    fa.Y = V;
+    fa.E1 = (const R*)(sizeof(R) == 4 ? (const void*)H->at<float>(R_E1F) : (const void*)H->at<double>(R_E1D));
+    fa.E2 = (const R*)(sizeof(R) == 4 ? (const void*)H->at<float>(R_E2F) : (const void*)H->at<double>(R_E2D));
+    fa.Kd = (R)(H->contract.strike * std::exp(-H->model.r * tau));
+    fa.payoff = H->contract.payoff;
+    fa.S = H->at<void>(R_S);
+    fa.pair0 = 0;
+    fa.npairs = N + 1;
+    fa.tw = tw;
+    PIDE_LAUNCH(PIDE2D_KERNEL_ROW_FORWARD_FULL, launch_row_forward<R>(fa, H->stream));
+    // xi (raw, at the increment positions) into the adjoint's spectrum rows
+    R* xr = H->at<R>(R_DLT);
+    PIDE_CUDA(launch_field_to_r<R>(g, xi, xr, H->stream));
+    FwdArgs<R> fx{};
+    fx.g = g;
+    fx.mode = FWD_INCR;
+    fx.D = xr;
+    fx.S = H->tape.base + t.specx;
+    fx.pair0 = N / 4 + 1;
+    fx.npairs = N / 2;
+    fx.tw = tw;
+    PIDE_LAUNCH(PIDE2D_KERNEL_ROW_FORWARD_INCR, launch_row_forward<R>(fx, H->stream));
+    PIDE_LAUNCH(PIDE2D_KERNEL_COL_FULL,
+                launch_corr_col<R>(g, H->at<void>(R_S), H->tape.base + t.specx, N / 2 + 2, N / 2 + N + 2,
+                                   reinterpret_cast<double*>(H->tape.base + t.cacc), tw, H->stream));
     return PIDE2D_OK;
 }
 
@@ -1834,7 +1865,7 @@ static pide2d_status do_adjoint(pide2d* H, const pide2d_model* dirs, int ndirs, 
         for (int i = 0; i < 7; ++i) ratio = std::fmax(ratio, std::fabs(fields[i]) / std::fmax(std::fabs(base[i]), 1e-3));
         if (!(ratio > 0.0) || !std::isfinite(ratio)) {
             for (int i = 0; i < 9; ++i) dpar[(size_t)k * 9 + i] = 0.0;
-            PIDE_CUDA(cudaMemsetAsync(tb + t.spec + (size_t)(2 + k) * t.spec1, 0, t.spec1, s));
+            PIDE_CUDA(cudaMemsetAsync(tb + t.dw + (size_t)k * t.omega, 0, (size_t)N * N * 8, s));
             continue;
         }
         const double eps = 1e-5 / ratio;
@@ -1847,13 +1878,11 @@ static pide2d_status do_adjoint(pide2d* H, const pide2d_model* dirs, int ndirs, 
         if (ps != PIDE2D_OK) return ps;
         ps = run_precompute(H, mm, om_m, part, moment, par_m);
         if (ps != PIDE2D_OK) return ps;
-        PIDE_CUDA(launch_central_difference(om_p, om_m, 0.5 / eps, om_d, (size_t)N * N, s));
+        PIDE_CUDA(launch_central_difference(om_p, om_m, 0.5 / eps, reinterpret_cast<double*>(tb + t.dw + (size_t)k * t.omega),
+                                            (size_t)N * N, s));
         double hp[9], hm[9];
         PIDE_CUDA(cudaMemcpyAsync(hp, par_p, 9 * 8, cudaMemcpyDeviceToHost, s));
         PIDE_CUDA(cudaMemcpyAsync(hm, par_m, 9 * 8, cudaMemcpyDeviceToHost, s));
-        const pide2d_status ws =
-            weight_spectrum<R>(H, om_d, tb + t.spec + (size_t)(2 + k) * t.spec1, nullptr, rows);
-        if (ws != PIDE2D_OK) return ws;
         PIDE_CUDA(cudaStreamSynchronize(s));
         for (int i = 0; i < 9; ++i) dpar[(size_t)k * 9 + i] = (hp[i] - hm[i]) * (0.5 / eps);
     }
@@ -1869,6 +1898,7 @@ static pide2d_status do_adjoint(pide2d* H, const pide2d_model* dirs, int ndirs, 
     // lambda^{S} = e_{S0}; everything else zero
     for (int i = 0; i < A_COUNT; ++i) PIDE_CUDA(cudaMemsetAsync(afield(i), 0, t.field, s));
     PIDE_CUDA(cudaMemsetAsync(acc, 0, (size_t)(kAdjAcc + ndirs) * 8, s));
+    PIDE_CUDA(cudaMemsetAsync(tb + t.cacc, 0, (size_t)(N + 1) * (2 * N) * 16, s));
     {
         const St<R> one = st_host_one<R>();
         PIDE_CUDA(cudaMemcpyAsync(lam + (size_t)(N / 2) * g.ldS + N / 2, &one, sizeof one, cudaMemcpyHostToDevice, s));
@@ -1975,6 +2005,15 @@ static pide2d_status do_adjoint(pide2d* H, const pide2d_model* dirs, int ndirs, 
         if (rs != PIDE2D_OK) { H->force_host_loop = false; return rs; }
     }
     H->force_host_loop = false;
+    // the correlation at the lags, and <dw_k, C> for every direction
+    if (ndirs > 0) {
+        double* C = reinterpret_cast<double*>(tb + t.cfield);
+        double* dp = reinterpret_cast<double*>(scr + 3 * t.omega + t.part + kMomentBytes + 2 * 256 + t.rows);
+        PIDE_CUDA(launch_corr_finish<double>(g, reinterpret_cast<double*>(tb + t.cacc), C, H->at<void>(R_TWD), s));
+        for (int k = 0; k < ndirs; ++k)
+            PIDE_CUDA(launch_dot_plain(g, reinterpret_cast<const double*>(tb + t.dw + (size_t)k * t.omega), C,
+                                       (size_t)N * N, dp, acc + kAdjAcc + k, s));
+    }
 
     // put the final state back
     for (size_t i = 0; i < sv.hist.size(); ++i)

@@ -147,6 +147,14 @@ template <typename R> cudaError_t launch_row_inverse(const InvArgs<R>& a, cudaSt
 template <typename R> cudaError_t launch_dst_col(const DstColArgs<R>& a, cudaStream_t s);
 template <typename R> cudaError_t launch_dst_row(const DstRowArgs<R>& a, cudaStream_t s);
 template <typename R> cudaError_t launch_prep(const PrepArgs<R>& a, cudaStream_t s);
+// the adjoint's weight contraction: acc[k1][k2] += conj(X) A for the spectra of the
+// midpoint field (SV, full rows) and of xi (SX, raw rows rlo..rhi-1), FP64 accumulator
+// (P/2 + 1) x P; corr_finish (FP64 handles' instantiation) inverts it into the N x N lag
+// array Cout [l2 + N/2][l1 + N/2]
+template <typename R> cudaError_t launch_corr_col(const Geometry& g, const void* SV, const void* SX, int rlo, int rhi,
+                                                 double* acc, const void* tw, cudaStream_t s);
+template <typename R> cudaError_t launch_corr_finish(const Geometry& g, double* acc, double* Cout, const void* twd,
+                                                    cudaStream_t s);
 // row DST-I of an FP64 interior field (pitch g.ldS) into the DST buffer E
 template <typename R> cudaError_t launch_row_dst(const Geometry& g, const double* src, R* E, const void* tw,
                                                 cudaStream_t s);
@@ -257,6 +265,10 @@ template <typename R> cudaError_t launch_dots_state(const Geometry& g, const dou
                                                    double* acc, double scale, cudaStream_t s);
 cudaError_t launch_dot_field(const Geometry& g, const double* xi, const double* out, double* part, double* acc,
                              cudaStream_t s);
+// *acc += sum_i a[i] b[i], i < n (adjoint_dot_blocks(g.N) partials in part)
+cudaError_t launch_dot_plain(const Geometry& g, const double* a, const double* b, size_t n, double* part, double* acc,
+                             cudaStream_t s);
+template <typename R> cudaError_t launch_field_to_r(const Geometry& g, const double* src, R* dst, cudaStream_t s);
 template <typename R> cudaError_t launch_sl_shift_dots(const Geometry& g, const SlShiftArgs<R>& a, double* part,
                                                       double* acc, double scale, cudaStream_t s);
 

@@ -12,6 +12,9 @@ namespace pide {
     template cudaError_t launch_dst_row<R>(const DstRowArgs<R>&, cudaStream_t);                     \
     template cudaError_t launch_prep<R>(const PrepArgs<R>&, cudaStream_t);                          \
     template cudaError_t launch_row_dst<R>(const Geometry&, const double*, R*, const void*, cudaStream_t); \
+    template cudaError_t launch_corr_col<R>(const Geometry&, const void*, const void*, int, int, double*, \
+                                            const void*, cudaStream_t);                             \
+    template cudaError_t launch_corr_finish<R>(const Geometry&, double*, double*, const void*, cudaStream_t); \
     template cudaError_t launch_ps_tin<R>(int, int, int, const int*, const double*, const double*, R*, cudaStream_t); \
     template cudaError_t launch_ps_rows_fwd<R>(int, const R*, int, void*, const void*, cudaStream_t); \
     template cudaError_t launch_ps_col<R>(int, void*, const void*, int, int, const void*, cudaStream_t); \

@@ -970,6 +970,105 @@ PIDE_FFT_KERNEL(double, P) k_weights_col(Geometry g, const double2* Sd, cpx<RO>*
     block_fft<double, -1, P>(buf, t, twd, load, store);
 }
 
+// ---------------------------------------------------------------------------
+// the adjoint's weight contraction: C(l) = sum_j sum_m xi_j(m) V~_j(m + l + 1/2)
+// (V~ the midpoints of T_in with the far field), so that for every direction
+// <xi_j, B_{dw} V_j> summed over j equals sum_l dw(l) C(l).  The spectra of
+// xi_j (raw rows at the increment positions) and of V~_j (midpoint rows)
+// meet column by column; conj(xi^) V^ is accumulated in FP64 over all
+// states, and one inverse transform at the end gives C.
+// ---------------------------------------------------------------------------
+// column k1: forward FFT of the V~ column (midpoints along s2, rows 0..P+1)
+// and of the xi column (raw rows rlo..rhi-1); acc[k1][k2] += conj(X) A
+template <typename R, int P>
+PIDE_FFT_KERNEL(R, P) k_corr_col(Geometry g, const void* SV, const void* SX, int rlo, int rhi, double2* acc,
+                                 const void* twv) {
+    using C = cpx<R>;
+    using CF = Cfg<R, P>;
+    constexpr int NT = CF::NT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int unit = threadIdx.x / NT, t = threadIdx.x - unit * NT;
+    C* bufA = reinterpret_cast<C*>(smem_raw) + (size_t)unit * 2 * CF::ULEN;
+    C* bufX = bufA + CF::ULEN;
+    const int k1 = blockIdx.x * CF::UNITS + unit;
+    const bool valid = k1 <= P / 2;
+    constexpr int Gc = cgroup<R>();
+    const int gq = k1 / Gc, c = k1 - gq * Gc;
+    const C* colA = (const C*)SV + (size_t)gq * g.rows * Gc + c;
+    const C* colX = (const C*)SX + (size_t)gq * g.rows * Gc + c;
+    const C* tw = (const C*)twv;
+    for (int rho = t; rho < P + 2; rho += NT) bufA[padi(rho)] = valid ? colA[(size_t)rho * Gc] : mk<R>(0, 0);
+    __syncthreads();
+    auto loadA = [&](int i) -> C {
+        if (i > P - 2) return mk<R>(0, 0);
+        const C x0 = bufA[padi(i)], x1 = bufA[padi(i + 1)], x2 = bufA[padi(i + 2)], x3 = bufA[padi(i + 3)];
+        return mk<R>(R(-0.0625) * (x0.x + x3.x) + R(0.5625) * (x1.x + x2.x),
+                     R(-0.0625) * (x0.y + x3.y) + R(0.5625) * (x1.y + x2.y));
+    };
+    block_fft<R, -1, P>(bufA, t, tw, loadA, SmemStore<R>{bufA});
+    auto loadX = [&](int rho) -> C {
+        return (valid && rho >= rlo && rho < rhi) ? colX[(size_t)rho * Gc] : mk<R>(0, 0);
+    };
+    auto accum = [&](int k2, C x) {
+        if (!valid) return;
+        const C a = bufA[padi(k2)];
+        double2* d = acc + (size_t)k1 * P + k2;
+        const double xr = (double)x.x, xi = (double)x.y, ar = (double)a.x, ai = (double)a.y;
+        double2 v = *d;
+        v.x += xr * ar + xi * ai;           // conj(x) a
+        v.y += xr * ai - xi * ar;
+        *d = v;
+    };
+    block_fft<R, -1, P>(bufX, t, tw, loadX, accum);
+}
+
+// in place, column k1 of the FP64 accumulator: inverse FFT over k2
+template <int P>
+PIDE_FFT_KERNEL(double, P) k_corr_icol(double2* acc, const double2* twd) {
+    using CF = Cfg<double, P>;
+    constexpr int NT = CF::NT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int unit = threadIdx.x / NT, t = threadIdx.x - unit * NT;
+    double2* buf = reinterpret_cast<double2*>(smem_raw) + (size_t)unit * CF::ULEN;
+    const int k1 = blockIdx.x * CF::UNITS + unit;
+    const bool valid = k1 <= P / 2;
+    double2* col = acc + (size_t)k1 * P;
+    auto load = [&](int k2) -> double2 { return valid ? col[k2] : mk<double>(0, 0); };
+    auto store = [&](int q2, double2 v) {
+        if (valid) col[q2] = v;
+    };
+    block_fft<double, +1, P>(buf, t, twd, load, store);
+}
+
+// lag row l2 (q2 = l2 - 1 mod P): Hermitian C2R over k1, C[l2 + N/2][l1 + N/2] = out(q1 = l1 - 1) / P^2
+template <int P>
+PIDE_FFT_KERNEL(double, P) k_corr_rows(const double2* acc, double* Cout, const double2* twd) {
+    using CF = Cfg<double, P>;
+    constexpr int NT = CF::NT, N = P / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int unit = threadIdx.x / NT, t = threadIdx.x - unit * NT;
+    double2* buf = reinterpret_cast<double2*>(smem_raw) + (size_t)unit * CF::ULEN;
+    const int r = blockIdx.x * CF::UNITS + unit;        // 0..N-1: l2 = r - N/2
+    const bool valid = r < N;
+    const int q2 = (r - N / 2 - 1 + P) & (P - 1);
+    auto load = [&](int k) -> double2 {
+        if (!valid) return mk<double>(0, 0);
+        const bool hi = k > P / 2;
+        const int kk = hi ? P - k : k;
+        double2 v = acc[(size_t)kk * P + q2];
+        if (kk == 0 || kk == P / 2) v.y = 0.0;
+        if (hi) v.y = -v.y;
+        return v;
+    };
+    const double inv = 1.0 / ((double)P * (double)P);
+    auto store = [&](int q1, double2 v) {
+        const int l1 = ((q1 + 1) & (P - 1));                 // l1 = q1 + 1 (mod P), wanted in [-N/2, N/2)
+        const int i1 = l1 < N / 2 ? l1 + N / 2 : (l1 >= P - N / 2 ? l1 - (P - N / 2) : -1);
+        if (valid && i1 >= 0) Cout[(size_t)r * N + i1] = v.x * inv;
+    };
+    block_fft<double, +1, P>(buf, t, twd, load, store);
+}
+
 // Greeks (Sec. 4, central differences) at interior nodes, in price space:
 // which = 0: dV/dS1, 1: dV/dS2, 2: d2V/dS1^2, 3: d2V/dS1dS2, 4: d2V/dS2^2
 template <typename R>
@@ -1239,6 +1338,44 @@ cudaError_t launch_weights_col(const Geometry& g, const void* Sd, void* Wh, void
     }
     PIDE_SWITCH_P(g.P, CASE)
 #undef CASE
+}
+template <typename R>
+cudaError_t launch_corr_col(const Geometry& g, const void* SV, const void* SX, int rlo, int rhi, double* acc,
+                            const void* tw, cudaStream_t s) {
+#define CASE(PP)                                                                                      \
+    {                                                                                                 \
+        using CF = Cfg<R, PP>;                                                                        \
+        const size_t sm = 2 * CF::SMEM;                                                               \
+        if (sm > 227 * 1024) return cudaErrorInvalidValue;      /* two FP64 8192-point units */      \
+        set_smem(k_corr_col<R, PP>, sm);                                                              \
+        k_corr_col<R, PP><<<(PP / 2 + 1 + CF::UNITS - 1) / CF::UNITS, CF::THREADS, sm, s>>>(          \
+            g, SV, SX, rlo, rhi, (double2*)acc, tw);                                                  \
+        return cudaGetLastError();                                                                    \
+    }
+    PIDE_SWITCH_P(g.P, CASE)
+#undef CASE
+}
+template <typename R>
+cudaError_t launch_corr_finish(const Geometry& g, double* acc, double* Cout, const void* twd, cudaStream_t s) {
+    if constexpr (sizeof(R) == 8) {
+#define CASE(PP)                                                                                      \
+        {                                                                                             \
+            using CF = Cfg<double, PP>;                                                               \
+            set_smem(k_corr_icol<PP>, CF::SMEM);                                                      \
+            k_corr_icol<PP><<<(PP / 2 + 1 + CF::UNITS - 1) / CF::UNITS, CF::THREADS, CF::SMEM, s>>>(  \
+                (double2*)acc, (const double2*)twd);                                                  \
+            cudaError_t e = cudaGetLastError();                                                       \
+            if (e != cudaSuccess) return e;                                                           \
+            set_smem(k_corr_rows<PP>, CF::SMEM);                                                      \
+            k_corr_rows<PP><<<(PP / 2 + CF::UNITS - 1) / CF::UNITS, CF::THREADS, CF::SMEM, s>>>(      \
+                (const double2*)acc, Cout, (const double2*)twd);                                      \
+            return cudaGetLastError();                                                                \
+        }
+        PIDE_SWITCH_P(g.P, CASE)
+#undef CASE
+    } else {
+        return cudaErrorInvalidValue;       // the FP64 transforms are instantiated with the FP64 kernels
+    }
 }
 template <typename R>
 cudaError_t launch_greeks(const Geometry& g, const St<R>* V, const double* E1d, const double* E2d, double h,
