@@ -84,10 +84,8 @@ __device__ __forceinline__ R diff_state(const S* Y, size_t idx, int ld, R d11, R
 // the B D of this sweep and the mixed difference of D, with no cancellation
 // between r(Y) and M D.  (The residual is formed from the full operator at the
 // start of every step, so rounding in the DST does not accumulate across steps.)
-template <typename R>
-__device__ __forceinline__ R mixed_plain(const R* D, size_t idx, int ld) {
-    return (D[idx + ld + 1] - D[idx - ld + 1]) - (D[idx + ld - 1] - D[idx - ld - 1]);
-}
+// The mixed difference of D at (row, x) is f(x + 1) - f(x - 1) with
+// f(x) = D[row + 1][x] - D[row - 1][x] (dcol below).
 
 // |d| / max(1, |y|) to select the node of a block's eq. 3.25 maximum: in FP32
 // the fast division (2 ulp; max(1, |y|) stays far below 2^126), since the
@@ -297,7 +295,92 @@ __device__ __forceinline__ void prefetch_inverse_rows(const InvArgs<R>& a, const
     }
 }
 
+// f(x) = D[row + 1][x] - D[row - 1][x] at column x (the mixed difference of an
+// increment at (row, x +- 1) is f(x + 1) - f(x - 1))
+template <typename R>
+__device__ __forceinline__ R dcol(const R* D, int ldR, int row, int x) {
+    const R* c = D + (size_t)row * ldR + x;
+    return c[ldR] - c[-ldR];
+}
+
+// Epilogue of the increment inverse row pass in coalesced order: outputs
+// m1 = t + NT b (b = 0..7) of rows m2 and m2 + 1, their C2R values in buf.
+// B_w Y += zz; the residual h_t theta (zz + a12 d12 D) of the increment
+// identity goes to buf as the odd extension for the row DST.  The loads of
+// four outputs are issued together, and the neighbours x -+ 1 of the mixed
+// difference come from the adjacent lanes (direct loads at warp edges).
 template <typename R, int P>
+__device__ __forceinline__ void incr_epilogue(const InvArgs<R>& a, St<R>* BYv, cpx<R>* buf, int t, int m2, bool valid,
+                                              bool hasb, bool do_resid) {
+    using C = cpx<R>;
+    using S_ = St<R>;
+    constexpr int NT = P / 16, N = P / 2, NB = N / NT;
+    constexpr bool SHFL = NT >= 32;
+    constexpr int EB = 4;             // outputs whose loads go out together
+    const int ld = a.g.ldS, ldR = a.g.ldR;
+    const int lane = threadIdx.x & 31;
+    const S_ zero = st_from_r<S_, R>(R(0));
+#pragma unroll
+    for (int b0 = 0; b0 < NB; b0 += EB) {
+        S_ ya[EB], yb[EB];
+        R fa[EB], fb[EB];
+#pragma unroll
+        for (int i = 0; i < EB; ++i) {
+            const int m1 = t + NT * (b0 + i);
+            const size_t idx = (size_t)m2 * ld + m1;
+            ya[i] = valid ? BYv[idx] : zero;
+            yb[i] = hasb ? BYv[idx + ld] : zero;
+            fa[i] = (do_resid && valid) ? dcol(a.D, ldR, m2, m1) : R(0);
+            fb[i] = (do_resid && hasb) ? dcol(a.D, ldR, m2 + 1, m1) : R(0);
+        }
+#pragma unroll
+        for (int i = 0; i < EB; ++i) {
+            const int m1 = t + NT * (b0 + i);
+            R fal, far_, fbl, fbr;
+            if constexpr (SHFL) {
+                fal = __shfl_up_sync(0xffffffffu, fa[i], 1);
+                far_ = __shfl_down_sync(0xffffffffu, fa[i], 1);
+                fbl = __shfl_up_sync(0xffffffffu, fb[i], 1);
+                fbr = __shfl_down_sync(0xffffffffu, fb[i], 1);
+                if (lane == 0 && m1 >= 1 && do_resid) {
+                    fal = valid ? dcol(a.D, ldR, m2, m1 - 1) : R(0);
+                    fbl = hasb ? dcol(a.D, ldR, m2 + 1, m1 - 1) : R(0);
+                }
+                if (lane == 31 && do_resid) {
+                    far_ = valid ? dcol(a.D, ldR, m2, m1 + 1) : R(0);
+                    fbr = hasb ? dcol(a.D, ldR, m2 + 1, m1 + 1) : R(0);
+                }
+            } else {
+                const bool in = do_resid && m1 >= 1;
+                fal = (in && valid) ? dcol(a.D, ldR, m2, m1 - 1) : R(0);
+                far_ = (in && valid) ? dcol(a.D, ldR, m2, m1 + 1) : R(0);
+                fbl = (in && hasb) ? dcol(a.D, ldR, m2 + 1, m1 - 1) : R(0);
+                fbr = (in && hasb) ? dcol(a.D, ldR, m2 + 1, m1 + 1) : R(0);
+            }
+            if (m1 < 1) continue;
+            R rra = R(0), rrb = R(0);
+            if (valid) {
+                const size_t idx = (size_t)m2 * ld + m1;
+                const C zz = buf[padi(m1)];
+                const R zva = zz.x, zvb = zz.y;
+                BYv[idx] = st_add(ya[i], zva);
+                if (do_resid) rra = a.htt * (zva + a.d12 * (far_ - fal));
+                if (hasb) {
+                    BYv[idx + ld] = st_add(yb[i], zvb);
+                    if (do_resid) rrb = a.htt * (zvb + a.d12 * (fbr - fbl));
+                }
+            }
+            if (do_resid) {
+                buf[padi(m1)] = mk<R>(rra, rrb);
+                buf[padi(P - m1)] = mk<R>(-rra, -rrb);
+            }
+        }
+    }
+}
+
+// INCR: compiled for the increment mode only (INV_INCR), else for INV_FULL / INV_OUT,
+// so the two epilogues do not share one register allocation
+template <typename R, int P, bool INCR>
 __device__ __forceinline__ void row_inverse_body(const InvArgs<R>& a, int upb) {
     using C = cpx<R>;
     using S_ = St<R>;
@@ -361,7 +444,6 @@ __device__ __forceinline__ void row_inverse_body(const InvArgs<R>& a, int upb) {
                 const int row = m2 + half;
                 const R zv = half == 0 ? zz.x : zz.y;
                 const size_t idx = (size_t)row * ld + m1;
-                const size_t idr = (size_t)row * ldR + m1;
                 if (a.mode == INV_OUT) {
                     a.out[idx] = (double)zv;
                 } else if (a.mode == INV_FULL) {
@@ -382,9 +464,6 @@ __device__ __forceinline__ void row_inverse_body(const InvArgs<R>& a, int upb) {
                                        + a.htt * diff_state(a.Y, idx, ld, a.d11, a.d22, a.d12);
                         }
                     }
-                } else {  // INV_INCR
-                    BYv[idx] = st_add(BYv[idx], zv);
-                    if (do_resid) rr[half] = a.htt * (zv + a.d12 * mixed_plain(a.D, idr, ldR));
                 }
             }
         }
@@ -393,7 +472,21 @@ __device__ __forceinline__ void row_inverse_body(const InvArgs<R>& a, int upb) {
             buf[padi(P - m1)] = mk<R>(-rr[0], -rr[1]);
         }
     };
-    block_fft<R, +1, P, false>(buf, t, tw, load, epilogue);
+    if constexpr (INCR) {
+        // the C2R into buf in natural order, then the epilogue in coalesced order
+        // (each thread reads the C2R values at its own m1 < N and writes the
+        // residual at m1 and P - m1 > N, whose C2R values nobody reads, and
+        // at 0 and N: no thread reads another thread's overwritten value)
+        block_fft<R, +1, P, false>(buf, t, tw, load, SmemStore<R>{buf});
+        incr_epilogue<R, P>(a, BYv, buf, t, m2, valid, hasb, do_resid);
+        if (do_resid && t == 0) {
+            buf[padi(0)] = mk<R>(0, 0);
+            buf[padi(N)] = mk<R>(0, 0);
+        }
+        __syncthreads();
+    } else {
+        block_fft<R, +1, P, false>(buf, t, tw, load, epilogue);
+    }
     if (!do_resid) return;   // uniform across the block
     constexpr int GE = rgroup<R>();
     auto store_e = [&](int k, C zz) {
@@ -409,17 +502,17 @@ __device__ __forceinline__ void row_inverse_body(const InvArgs<R>& a, int upb) {
 // The single-job kernel reads its arguments from a shared-memory copy: inlined
 // from the parameter block itself, this FFT kernel needed several times the
 // spill traffic (register allocation differs with the arguments' address space).
-template <typename R, int P>
+template <typename R, int P, bool INCR>
 PIDE_FFT_KERNEL(R, P) k_row_inverse(const __grid_constant__ InvArgs<R> a0) {
     __shared__ InvArgs<R> sa;
     if (threadIdx.x == 0) sa = a0;
     __syncthreads();
-    row_inverse_body<R, P>(sa, Cfg<R, P>::UNITS);
+    row_inverse_body<R, P, INCR>(sa, Cfg<R, P>::UNITS);
 }
-template <typename R, int P>
+template <typename R, int P, bool INCR>
 PIDE_FFT_JOBS_KERNEL(R, P) k_row_inverse_jobs(const InvArgs<R>* __restrict__ arr, JobsCtl jc) {
     if (jc.skip(blockIdx.y)) return;
-    row_inverse_body<R, P>(arr[blockIdx.y], blockDim.x / Cfg<R, P>::NT);
+    row_inverse_body<R, P, INCR>(arr[blockIdx.y], blockDim.x / Cfg<R, P>::NT);
 }
 
 // ---------------------------------------------------------------------------
@@ -535,14 +628,15 @@ __device__ __forceinline__ void dst_row_body(const DstRowArgs<R>& a, int upb) {
     // the state rows updated after the DST arrive in L2 while it runs
     if (t == 0 && valid) l2_prefetch(Yv + (size_t)m2 * ld, (size_t)(hasb ? 2 : 1) * ld * sizeof(St<R>));
     // the increment also enters the next B_w sweep: it is laid out at its
-    // R2C position p = m1 + N/2 + 1 (zero elsewhere) for the second transform
-    auto update = [&](int m1, C zz) {
+    // R2C position p = m1 + N/2 + 1 (zero elsewhere) for the second transform.
+    // y0, y1: the states at (m2, m1) and (m2 + 1, m1), loaded beforehand
+    auto update = [&](int m1, C zz, St<R> y0, St<R> y1) {
         R da = 0, db = 0;
         if (valid && m1 >= 1 && m1 < N) {
             da = R(-0.5) * zz.y;
             {
                 const size_t idx = (size_t)m2 * ld + m1;
-                const St<R> y = st_add(Yv[idx], da);
+                const St<R> y = st_add(y0, da);
                 Yv[idx] = y;
                 a.D[(size_t)m2 * ldR + m1] = da;
                 const R yr = st_r(y);
@@ -553,7 +647,7 @@ __device__ __forceinline__ void dst_row_body(const DstRowArgs<R>& a, int upb) {
             if (hasb) {
                 db = R(0.5) * zz.x;
                 const size_t idx = (size_t)(m2 + 1) * ld + m1;
-                const St<R> y = st_add(Yv[idx], db);
+                const St<R> y = st_add(y1, db);
                 Yv[idx] = y;
                 a.D[(size_t)(m2 + 1) * ldR + m1] = db;
                 const R yr = st_r(y);
@@ -564,7 +658,33 @@ __device__ __forceinline__ void dst_row_body(const DstRowArgs<R>& a, int upb) {
         }
         buf[padi((m1 + N / 2 + 1) & (P - 1))] = mk<R>(da, db);
     };
-    block_fft<R, -1, P>(buf, t, tw, load, update);
+    // the DST back into buf in natural order; then the update in coalesced
+    // order (m1 = t + NT b), the state loads of four outputs issued together
+    block_fft<R, -1, P>(buf, t, tw, load, SmemStore<R>{buf});
+    {
+        constexpr int NB = N / NT;
+        C zz[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) zz[b] = buf[padi(t + NT * b)];
+        __syncthreads();                    // every DST value is read before buf takes the R2C input
+#pragma unroll
+        for (int b = 0; b < NB; ++b) buf[padi((N + t + NT * b + N / 2 + 1) & (P - 1))] = mk<R>(0, 0);
+        const St<R> zero = st_from_r<St<R>, R>(R(0));
+#pragma unroll
+        for (int b0 = 0; b0 < NB; b0 += 4) {
+            St<R> y0[4], y1[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int m1 = t + NT * (b0 + i);
+                const size_t idx = (size_t)m2 * ld + m1;
+                y0[i] = (valid && m1 >= 1) ? Yv[idx] : zero;
+                y1[i] = (hasb && m1 >= 1) ? Yv[idx + ld] : zero;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) update(t + NT * (b0 + i), zz[b0 + i], y0[i], y1[i]);
+        }
+        __syncthreads();
+    }
     // (reduced here, before the second transform, so the candidate's registers
     // are free during it)
     // block maximum of eq. 3.25 in FP64, one atomic per block: the block's
@@ -1179,8 +1299,11 @@ template <typename R>
 cudaError_t launch_row_inverse_jobs(const InvArgs<R>& a0, const InvArgs<R>* arr, int K, JobsCtl jc, int upb,
                               cudaStream_t s) {
 #define CASE(PP)                                                                                             \
-    if constexpr (LoopSize<R, PP>::ok) return launch_fft_kernel_jobs<R, PP>(k_row_inverse_jobs<R, PP>, arr, K, jc, PP / 4, 0, upb, s); \
-    else return cudaErrorInvalidValue;
+    if constexpr (LoopSize<R, PP>::ok) {                                                                     \
+        if (a0.mode == INV_INCR)                                                                             \
+            return launch_fft_kernel_jobs<R, PP>(k_row_inverse_jobs<R, PP, true>, arr, K, jc, PP / 4, 0, upb, s); \
+        return launch_fft_kernel_jobs<R, PP>(k_row_inverse_jobs<R, PP, false>, arr, K, jc, PP / 4, 0, upb, s); \
+    } else return cudaErrorInvalidValue;
     PIDE_SWITCH_P(a0.g.P, CASE)
 #undef CASE
 }
@@ -1233,8 +1356,10 @@ cudaError_t launch_col(const ColArgs<R>& a, cudaStream_t s) {
 template <typename R>
 cudaError_t launch_row_inverse(const InvArgs<R>& a, cudaStream_t s) {
 #define CASE(PP)                                                                       \
-    if constexpr (LoopSize<R, PP>::ok) return launch_fft_kernel<R, PP>(k_row_inverse<R, PP>, a, PP / 4, 0, s); \
-    else return cudaErrorInvalidValue;
+    if constexpr (LoopSize<R, PP>::ok) {                                               \
+        if (a.mode == INV_INCR) return launch_fft_kernel<R, PP>(k_row_inverse<R, PP, true>, a, PP / 4, 0, s); \
+        return launch_fft_kernel<R, PP>(k_row_inverse<R, PP, false>, a, PP / 4, 0, s); \
+    } else return cudaErrorInvalidValue;
     PIDE_SWITCH_P(a.g.P, CASE)
 #undef CASE
 }
