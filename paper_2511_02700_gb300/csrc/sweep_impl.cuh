@@ -157,14 +157,45 @@ __device__ __forceinline__ void row_forward_body(const FwdArgs<R>& a, int upb) {
         block_fft<R, -1, P>(buf, t, tw, load, SmemStore<R>{buf});
     } else {
         const int m2a = rho - N / 2 - 1;
-        // a compile-time trip count lets the loop unroll and its loads go out together
+        const bool ina = valid && m2a >= 1 && m2a <= N - 1;          // row m2a has interior nodes
+        const bool inb = valid && m2a + 1 >= 1 && m2a + 1 <= N - 1;
+        // far-field (halo) positions first: no state loads; a compile-time trip
+        // count lets the loop unroll
 #pragma unroll
         for (int q = 0; q < (P + 2 + NT - 1) / NT; ++q) {
             const int idx = t + q * NT;
             if (idx < P + 2) {
                 const int m1 = idx - N / 2 - 1;
-                nodes[idx] = valid ? node_value(a, m1, m2a) : R(0);
-                nodes[P + 2 + idx] = valid ? node_value(a, m1, m2a + 1) : R(0);
+                const bool colin = m1 >= 1 && m1 <= N - 1;
+                if (!(ina && colin)) nodes[idx] = valid ? node_value(a, m1, m2a) : R(0);
+                if (!(inb && colin)) nodes[P + 2 + idx] = valid ? node_value(a, m1, m2a + 1) : R(0);
+            }
+        }
+        // interior positions m1 = 1 + t + NT b: the state loads of four columns of
+        // both rows go out together
+        const St<R>* Ya = a.Y + (size_t)m2a * a.g.ldS;
+        const St<R>* Ra = a.mode == FWD_DIFF ? a.Yref + (size_t)m2a * a.g.ldS : nullptr;
+        const int ldS = a.g.ldS;
+#pragma unroll
+        for (int b0 = 0; b0 < N / NT; b0 += 4) {
+            St<R> ya[4], yb[4], za[4], zb[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int m1 = 1 + t + NT * (b0 + i);
+                const bool ok = m1 <= N - 1;
+                const St<R> zero = st_from_r<St<R>, R>(R(0));
+                ya[i] = (ina && ok) ? Ya[m1] : zero;
+                yb[i] = (inb && ok) ? Ya[ldS + m1] : zero;
+                za[i] = (Ra && ina && ok) ? Ra[m1] : zero;
+                zb[i] = (Ra && inb && ok) ? Ra[ldS + m1] : zero;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int m1 = 1 + t + NT * (b0 + i);
+                if (m1 > N - 1) continue;
+                const int idx = m1 + N / 2 + 1;
+                if (ina) nodes[idx] = Ra ? st_diff(ya[i], za[i]) : st_r(ya[i]);
+                if (inb) nodes[P + 2 + idx] = Ra ? st_diff(yb[i], zb[i]) : st_r(yb[i]);
             }
         }
         __syncthreads();
@@ -405,18 +436,20 @@ __device__ __forceinline__ void row_inverse_body(const InvArgs<R>& a, int upb) {
     // the two spectrum rows, each value read once (the Hermitian extension uses
     // every k twice): k at plain indices 2k, 2k + 1 of buf, which the first stage
     // reads completely before it writes
+    // (a constant trip count with a guard, so the loop unrolls and its loads go out together)
 #pragma unroll
     for (int q = 0; q < (P / 2 + NT) / NT; ++q) {
         const int k = t + q * NT;
-        if (k > P / 2) break;
-        C xa = mk<R>(0, 0), xb = mk<R>(0, 0);
-        if (valid) {
-            const int g = k / Gc, c = k - g * Gc;
-            xa = S[((size_t)g * rows + (m2 - 1)) * Gc + c];
-            xb = S[((size_t)g * rows + m2) * Gc + c];
+        if (k <= P / 2) {
+            C xa = mk<R>(0, 0), xb = mk<R>(0, 0);
+            if (valid) {
+                const int g = k / Gc, c = k - g * Gc;
+                xa = S[((size_t)g * rows + (m2 - 1)) * Gc + c];
+                xb = S[((size_t)g * rows + m2) * Gc + c];
+            }
+            buf[2 * k] = xa;
+            buf[2 * k + 1] = xb;
         }
-        buf[2 * k] = xa;
-        buf[2 * k + 1] = xb;
     }
     __syncthreads();
     auto load = [&](int pos) -> C {
@@ -597,17 +630,19 @@ __device__ __forceinline__ void dst_row_body(const DstRowArgs<R>& a, int upb) {
     const C* tw = (const C*)a.tw;
     // the two DST rows, each value read once (the odd extension uses every j
     // twice), at plain indices of buf, which the first stage reads before it writes
+    // (constant trip count with a guard: the loop unrolls and its loads go out together)
 #pragma unroll
     for (int q = 0; q < (N + NT) / NT; ++q) {
         const int j = t + q * NT;
-        if (j > N) break;
-        R ea = 0, eb = 0;
-        if (valid && j >= 1 && j <= N - 1) {
-            const int gE = j / GE, c = j - gE * GE;
-            ea = a.E[((size_t)gE * N + m2) * GE + c];
-            if (hasb) eb = a.E[((size_t)gE * N + m2 + 1) * GE + c];
+        if (j <= N) {
+            R ea = 0, eb = 0;
+            if (valid && j >= 1 && j <= N - 1) {
+                const int gE = j / GE, c = j - gE * GE;
+                ea = a.E[((size_t)gE * N + m2) * GE + c];
+                if (hasb) eb = a.E[((size_t)gE * N + m2 + 1) * GE + c];
+            }
+            buf[j] = mk<R>(ea, eb);
         }
-        buf[j] = mk<R>(ea, eb);
     }
     __syncthreads();
     auto load = [&](int i) -> C {
