@@ -238,7 +238,8 @@ PIDE_FFT_JOBS_KERNEL(R, P) k_row_forward_jobs(const FwdArgs<R>* __restrict__ arr
 // column pass: staged column, T_in along s2 in the first stage, product with
 // conj(w^)/P^2 in the last forward stage, inverse FFT writing rows 1..N
 // ---------------------------------------------------------------------------
-template <typename R, int P>
+// INCR: compiled for COL_INCR only, else for COL_FULL (each with its own register allocation)
+template <typename R, int P, bool INCR>
 __device__ __forceinline__ void col_body(const ColArgs<R>& a, int upb) {
     using C = cpx<R>;
     using CF = Cfg<R, P>;
@@ -271,15 +272,20 @@ __device__ __forceinline__ void col_body(const ColArgs<R>& a, int upb) {
         const C w = valid ? __ldg(&wh[(size_t)k2 * Gc]) : mk<R>(0, 0);
         buf[padi(k2)] = cmul(v, w);
     };
-    if (a.mode == COL_INCR) {
+    if constexpr (INCR) {
         // raw rows; the midpoint interpolation along s2 is in the weight spectrum
         auto load = [&](int rho) -> C {
             return (valid && rho >= a.rlo && rho < a.rhi) ? col[(size_t)rho * Gc] : mk<R>(0, 0);
         };
         block_fft<R, -1, P>(buf, t, tw, load, store_mul);
     } else {
-        for (int rho = t; rho < P + 2; rho += NT)
-            buf[padi(rho)] = (valid && rho >= a.rlo && rho < a.rhi) ? col[(size_t)rho * Gc] : mk<R>(0, 0);
+        // (constant trip count with a guard: the loop unrolls and its loads go out together)
+#pragma unroll
+        for (int q = 0; q < (P + 2 + NT - 1) / NT; ++q) {
+            const int rho = t + q * NT;
+            if (rho < P + 2)
+                buf[padi(rho)] = (valid && rho >= a.rlo && rho < a.rhi) ? col[(size_t)rho * Gc] : mk<R>(0, 0);
+        }
         __syncthreads();
         auto load = [&](int i) -> C {
             if (i > P - 2) return mk<R>(0, 0);
@@ -294,12 +300,12 @@ __device__ __forceinline__ void col_body(const ColArgs<R>& a, int upb) {
     };
     block_fft<R, +1, P>(buf, t, tw, SmemLoad<R>{buf}, store_out);
 }
-template <typename R, int P>
-PIDE_FFT_KERNEL(R, P) k_col(const __grid_constant__ ColArgs<R> a) { col_body<R, P>(a, Cfg<R, P>::UNITS); }
-template <typename R, int P>
+template <typename R, int P, bool INCR>
+PIDE_FFT_KERNEL(R, P) k_col(const __grid_constant__ ColArgs<R> a) { col_body<R, P, INCR>(a, Cfg<R, P>::UNITS); }
+template <typename R, int P, bool INCR>
 PIDE_FFT_JOBS_KERNEL(R, P) k_col_jobs(const ColArgs<R>* __restrict__ arr, JobsCtl jc) {
     if (jc.skip(blockIdx.y)) return;
-    col_body<R, P>(arr[blockIdx.y], blockDim.x / Cfg<R, P>::NT);
+    col_body<R, P, INCR>(arr[blockIdx.y], blockDim.x / Cfg<R, P>::NT);
 }
 
 // ---------------------------------------------------------------------------
@@ -1325,8 +1331,11 @@ template <typename R>
 cudaError_t launch_col_jobs(const ColArgs<R>& a0, const ColArgs<R>* arr, int K, JobsCtl jc, int upb,
                               cudaStream_t s) {
 #define CASE(PP)                                                                                             \
-    if constexpr (LoopSize<R, PP>::ok) return launch_fft_kernel_jobs<R, PP>(k_col_jobs<R, PP>, arr, K, jc, PP / 2 + 1, 0, upb, s); \
-    else return cudaErrorInvalidValue;
+    if constexpr (LoopSize<R, PP>::ok) {                                                                     \
+        if (a0.mode == COL_INCR)                                                                             \
+            return launch_fft_kernel_jobs<R, PP>(k_col_jobs<R, PP, true>, arr, K, jc, PP / 2 + 1, 0, upb, s); \
+        return launch_fft_kernel_jobs<R, PP>(k_col_jobs<R, PP, false>, arr, K, jc, PP / 2 + 1, 0, upb, s); \
+    } else return cudaErrorInvalidValue;
     PIDE_SWITCH_P(a0.g.P, CASE)
 #undef CASE
 }
@@ -1383,8 +1392,10 @@ cudaError_t launch_row_forward(const FwdArgs<R>& a, cudaStream_t s) {
 template <typename R>
 cudaError_t launch_col(const ColArgs<R>& a, cudaStream_t s) {
 #define CASE(PP)                                                                       \
-    if constexpr (LoopSize<R, PP>::ok) return launch_fft_kernel<R, PP>(k_col<R, PP>, a, PP / 2 + 1, 0, s); \
-    else return cudaErrorInvalidValue;
+    if constexpr (LoopSize<R, PP>::ok) {                                               \
+        if (a.mode == COL_INCR) return launch_fft_kernel<R, PP>(k_col<R, PP, true>, a, PP / 2 + 1, 0, s); \
+        return launch_fft_kernel<R, PP>(k_col<R, PP, false>, a, PP / 2 + 1, 0, s); \
+    } else return cudaErrorInvalidValue;
     PIDE_SWITCH_P(a.g.P, CASE)
 #undef CASE
 }
