@@ -196,11 +196,12 @@ __device__ __forceinline__ void dft_small(C* v) {
 // multiples of 16 (or step < 16 with base a multiple of 16 and r*step < 16)
 // the padding distributes, padi(base + r*step) = padi(base) + r*padi(step),
 // and the stage uses the *_at forms with one padded base per thread.
-template <typename R> struct SmemLoad {
+template <typename R, unsigned ZM = 0u> struct SmemLoad {
     cpx<R>* buf;
     __device__ __forceinline__ cpx<R> operator()(int i) const { return buf[padi(i)]; }
     __device__ __forceinline__ cpx<R> at(int pbase, int poff) const { return buf[pbase + poff]; }
     static constexpr bool smem = true;
+    static constexpr unsigned zero_mask = ZM;     // see zero_mask_of below
 };
 template <typename R> struct SmemStore {
     cpx<R>* buf;
@@ -210,6 +211,13 @@ template <typename R> struct SmemStore {
 };
 template <class T, class = void> struct is_smem_io { static constexpr bool value = false; };
 template <class T> struct is_smem_io<T, decltype((void)T::smem, void())> { static constexpr bool value = T::smem; };
+// A first-stage loader may declare `zero_mask`: bit r set means that input
+// j + r P/16 of every radix-16 butterfly is zero, so the stage skips the load
+// and the transform folds the zero at compile time.
+template <class T, class = void> struct zero_mask_of { static constexpr unsigned value = 0u; };
+template <class T> struct zero_mask_of<T, decltype((void)T::zero_mask, void())> {
+    static constexpr unsigned value = T::zero_mask;
+};
 
 // One Stockham stage of radix RAD (compile-time P and span NS); t in [0, P/16)
 // is the thread's index in its FFT unit.  The stage reads its inputs through
@@ -225,15 +233,22 @@ __device__ __forceinline__ void fft_stage(int t, const cpx<R>* __restrict__ tw, 
     constexpr int TWS = P / (NS * RAD);
     cpx<R> v[16];
 #pragma unroll
+    constexpr unsigned ZM = (RAD == 16 && NS == 1) ? zero_mask_of<L>::value : 0u;
     for (int b = 0; b < NB; ++b) {
         const int j = t + b * NT;
         if constexpr (is_smem_io<L>::value && STRIDE % 16 == 0) {
             const int pj = padi(j);
 #pragma unroll
-            for (int r = 0; r < RAD; ++r) v[b * RAD + r] = load.at(pj, r * (STRIDE + STRIDE / 16));
+            for (int r = 0; r < RAD; ++r) {
+                if ((ZM >> r) & 1u) v[b * RAD + r] = mk<R>(R(0), R(0));
+                else v[b * RAD + r] = load.at(pj, r * (STRIDE + STRIDE / 16));
+            }
         } else {
 #pragma unroll
-            for (int r = 0; r < RAD; ++r) v[b * RAD + r] = load(j + r * STRIDE);
+            for (int r = 0; r < RAD; ++r) {
+                if ((ZM >> r) & 1u) v[b * RAD + r] = mk<R>(R(0), R(0));
+                else v[b * RAD + r] = load(j + r * STRIDE);
+            }
         }
     }
 #pragma unroll

@@ -238,6 +238,18 @@ PIDE_FFT_JOBS_KERNEL(R, P) k_row_forward_jobs(const FwdArgs<R>* __restrict__ arr
 // column pass: staged column, T_in along s2 in the first stage, product with
 // conj(w^)/P^2 in the last forward stage, inverse FFT writing rows 1..N
 // ---------------------------------------------------------------------------
+// loader of an increment column: rows rlo..rhi-1 of the column group (zero elsewhere)
+template <typename R, int P>
+struct IncrColLoad {
+    static constexpr unsigned zero_mask = P >= 32 ? 0xE00Fu : 0u;   // r in {0..3, 13..15}
+    const cpx<R>* col;
+    int rlo, rhi;
+    bool valid;
+    __device__ __forceinline__ cpx<R> operator()(int rho) const {
+        return (valid && rho >= rlo && rho < rhi) ? col[(size_t)rho * cgroup<R>()] : mk<R>(0, 0);
+    }
+};
+
 // INCR: compiled for COL_INCR only, else for COL_FULL (each with its own register allocation)
 template <typename R, int P, bool INCR>
 __device__ __forceinline__ void col_body(const ColArgs<R>& a, int upb) {
@@ -273,11 +285,10 @@ __device__ __forceinline__ void col_body(const ColArgs<R>& a, int upb) {
         buf[padi(k2)] = cmul(v, w);
     };
     if constexpr (INCR) {
-        // raw rows; the midpoint interpolation along s2 is in the weight spectrum
-        auto load = [&](int rho) -> C {
-            return (valid && rho >= a.rlo && rho < a.rhi) ? col[(size_t)rho * Gc] : mk<R>(0, 0);
-        };
-        block_fft<R, -1, P>(buf, t, tw, load, store_mul);
+        // raw rows; the midpoint interpolation along s2 is in the weight spectrum.
+        // Rows outside [N/2 + 2, 3N/2 + 2) are zero, so first-stage inputs
+        // j + r P/16 with r in {0..3, 13..15} always are (P >= 32)
+        block_fft<R, -1, P>(buf, t, tw, IncrColLoad<R, P>{col, a.rlo, a.rhi, valid}, store_mul);
     } else {
         // (constant trip count with a guard: the loop unrolls and its loads go out together)
 #pragma unroll
@@ -756,8 +767,10 @@ __device__ __forceinline__ void dst_row_body(const DstRowArgs<R>& a, int upb) {
         atomicMax((unsigned long long*)a.resid, (unsigned long long)__double_as_longlong(v));
     }
     // packed R2C of the two increment rows -> spectrum rows rho = m2 + N/2 + 1, +1
-    // (the midpoint interpolation is a factor of the increment weight spectrum)
-    block_fft<R, -1, P>(buf, t, tw, SmemLoad<R>{buf}, SmemStore<R>{buf});
+    // (the midpoint interpolation is a factor of the increment weight spectrum);
+    // positions outside [N/2 + 2, 3N/2] are zero, so first-stage inputs
+    // j + r P/16 with r in {0..3, 13..15} always are (P >= 32)
+    block_fft<R, -1, P>(buf, t, tw, SmemLoad<R, (P >= 32 ? 0xE00Fu : 0u)>{buf}, SmemStore<R>{buf});
     {
         constexpr int Gc = cgroup<R>();
         C* S = (C*)a.S;
