@@ -61,7 +61,7 @@ enum Region {
     R_V0, R_V1, R_V2, R_V3, R_V4, R_BV, R_BY, R_W, R_X, R_OUT,   // 10 state-sized fields
     R_RES, R_DLT,                                                 // R fields
     R_S, R_WH, R_WHI, R_E, R_TWR, R_TWD,
-    R_E1D, R_E2D, R_E1F, R_E2F, R_SIN2D, R_SIN2R,
+    R_E1D, R_E2D, R_E1F, R_E2F, R_E1L, R_E2L, R_SIN2D, R_SIN2R,
     R_OMEGA, R_PART, R_PARAMS, R_MOMENT, R_GL, R_RESID, R_CTL,
     R_COUNT
 };
@@ -97,6 +97,7 @@ void fill_layout(int N, Layout& L) {
     const size_t tl = (size_t)(2 * N + 7);
     L.size[R_E1D] = L.size[R_E2D] = tl * 8;
     L.size[R_E1F] = L.size[R_E2F] = tl * 4;
+    L.size[R_E1L] = L.size[R_E2L] = tl * 4;
     L.size[R_SIN2D] = (size_t)(N + 1) * 8;
     L.size[R_SIN2R] = (size_t)(N + 1) * sizeof(R);
     L.size[R_OMEGA] = (size_t)N * N * 8;
@@ -773,8 +774,16 @@ static pide2d_status build_theta_step(pide2d* H, const int* list, int cnt, doubl
     }
     pa.E1d = H->at<double>(R_E1D);
     pa.E2d = H->at<double>(R_E2D);
+    pa.E1h = H->at<float>(R_E1F);
+    pa.E2h = H->at<float>(R_E2F);
+    pa.E1l = H->at<float>(R_E1L);
+    pa.E2l = H->at<float>(R_E2L);
     pa.Kd_prev = Kd_prev;
     pa.Kd_now = Kd_now;
+    pa.Kdp_h = (float)Kd_prev;
+    pa.Kdp_l = (float)(Kd_prev - (double)pa.Kdp_h);
+    pa.Kdn_h = (float)Kd_now;
+    pa.Kdn_l = (float)(Kd_now - (double)pa.Kdn_h);
     pa.payoff = H->contract.payoff;
 
     SolveSpec<R>& sp = *sp_out;
@@ -1070,7 +1079,8 @@ static pide2d_status do_create(pide2d* H) {
 
     // tables
     PIDE_CUDA(launch_tables(N, H->s_lo1, H->s_lo2, H->h, H->at<double>(R_E1D), H->at<double>(R_E2D),
-                            H->at<float>(R_E1F), H->at<float>(R_E2F), H->at<double>(R_SIN2D), s));
+                            H->at<float>(R_E1F), H->at<float>(R_E2F), H->at<float>(R_E1L), H->at<float>(R_E2L),
+                            H->at<double>(R_SIN2D), s));
     PIDE_CUDA(launch_twiddles<R>(g.P, H->at<void>(R_TWR), s));
     PIDE_CUDA(launch_twiddles<double>(g.P, H->at<void>(R_TWD), s));
 

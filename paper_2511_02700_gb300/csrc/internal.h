@@ -118,7 +118,10 @@ template <typename R> struct PrepArgs {
     int o1, o2, nt;          // SL: first tap offsets, taps per axis (2 or 4)
     R w1[4], w2[4];          // SL weights per axis
     const double* E1d; const double* E2d;   // e^{s} in FP64
+    const float* E1h; const float* E1l;     // e^{s} as double-float pairs (FP32-bulk far field)
+    const float* E2h; const float* E2l;
     double Kd_prev, Kd_now;  // K e^{-r tau_{n-1}}, K e^{-r tau_n}
+    float Kdp_h, Kdp_l, Kdn_h, Kdn_l;        // the same as double-float pairs
     int payoff;
 };
 
@@ -337,7 +340,7 @@ cudaError_t launch_moment(const LevyParams& L, double H, const double* glx, cons
 cudaError_t launch_finalize(const double* partials, int nblocks, const double* moment, double r,
                             const double* sigma_cov, double* params, cudaStream_t s);
 cudaError_t launch_tables(int N, double s_lo1, double s_lo2, double h, double* E1d, double* E2d,
-                          float* E1f, float* E2f, double* sin2, cudaStream_t s);
+                          float* E1f, float* E2f, float* E1l, float* E2l, double* sin2, cudaStream_t s);
 template <typename R> cudaError_t launch_twiddles(int P, void* tw, cudaStream_t s);
 template <typename R> cudaError_t launch_payoff(const Geometry& g, const double* E1d, const double* E2d,
                                                double s_lo1, double s_lo2, double h, double K, int payoff,

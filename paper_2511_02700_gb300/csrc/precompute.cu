@@ -219,7 +219,7 @@ __global__ void k_finalize(const double* partials, int nblocks, const double* mo
 
 // e^{s_m} tables for m in [-N/2-3, N+N/2+3] and sin^2(pi k/(2N)), k = 0..N
 __global__ void k_tables(int N, double s1, double s2, double h, double* E1d, double* E2d, float* E1f, float* E2f,
-                         double* sin2) {
+                         float* E1l, float* E2l, double* sin2) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int len = 2 * N + 7;
     if (i < len) {
@@ -229,6 +229,9 @@ __global__ void k_tables(int N, double s1, double s2, double h, double* E1d, dou
         E2d[i] = b;
         E1f[i] = (float)a;
         E2f[i] = (float)b;
+        // the FP32 rounding errors: (E1f, E1l) is e^{s} to about 48 bits
+        E1l[i] = (float)(a - (double)E1f[i]);
+        E2l[i] = (float)(b - (double)E2f[i]);
     }
     if (i <= N) {
         const double s = sinpi(0.5 * i / N);
@@ -371,9 +374,9 @@ cudaError_t launch_finalize(const double* partials, int nblocks, const double* m
     return cudaGetLastError();
 }
 cudaError_t launch_tables(int N, double s_lo1, double s_lo2, double h, double* E1d, double* E2d, float* E1f,
-                          float* E2f, double* sin2, cudaStream_t s) {
+                          float* E2f, float* E1l, float* E2l, double* sin2, cudaStream_t s) {
     const int len = 2 * N + 7;   // nodes m = -N/2-3 .. N+N/2+3
-    k_tables<<<(len + 255) / 256, 256, 0, s>>>(N, s_lo1, s_lo2, h, E1d, E2d, E1f, E2f, sin2);
+    k_tables<<<(len + 255) / 256, 256, 0, s>>>(N, s_lo1, s_lo2, h, E1d, E2d, E1f, E2f, E1l, E2l, sin2);
     return cudaGetLastError();
 }
 template <typename R>

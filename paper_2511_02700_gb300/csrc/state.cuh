@@ -62,6 +62,39 @@ __device__ __forceinline__ R far_value(int payoff, R Kd, R e1, R e2) {
     return fmax(Kd - e1, R(0));
 }
 
+// The far field g(s, tau) as a double-float pair from double-float inputs: e^{s1}
+// = e1h + e1l, e^{s2} = e2h + e2l, K e^{-r tau} = kh + kl.  Knuth's two-sum keeps
+// every sum exact to about 48 bits, so the value matches the FP64 evaluation to
+// the pair's precision without an FP64 instruction.
+__device__ __forceinline__ float2 df_two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return make_float2(s, (a - (s - bb)) + (b - bb));
+}
+__device__ __forceinline__ float2 df_norm(float hi, float lo) {
+    const float s = hi + lo;
+    return make_float2(s, lo - (s - hi));
+}
+__device__ __forceinline__ float2 far_value_df(int payoff, float kh, float kl, float e1h, float e1l, float e2h,
+                                               float e2l) {
+    float ah, al;                            // the payoff's argument a: (e1 + e2)/2, or e1
+    if (payoff == 2) {
+        ah = e1h;
+        al = e1l;
+    } else {
+        const float2 t = df_two_sum(e1h, e2h);
+        const float2 u = df_norm(t.x, t.y + (e1l + e2l));
+        ah = 0.5f * u.x;
+        al = 0.5f * u.y;
+    }
+    // g = k - a (puts) or a - k (call), then max(g, 0)
+    const float sgn = payoff == 1 ? -1.0f : 1.0f;
+    const float2 d = df_two_sum(sgn * kh, -sgn * ah);
+    const float2 g = df_norm(d.x, d.y + sgn * (kl - al));
+    if (g.x < 0.0f || (g.x == 0.0f && g.y <= 0.0f)) return make_float2(0.0f, 0.0f);
+    return g;
+}
+
 // g(s, tau) - g(s, tau_prev) with k0 = K e^{-r tau}, k1 = K e^{-r tau_prev} and
 // dk = k0 - k1 rounded once from FP64: piecewise in the payoff's argument a,
 // so no difference of two nearby far-field values is rounded

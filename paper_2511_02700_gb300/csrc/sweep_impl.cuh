@@ -854,6 +854,19 @@ template <typename R>
 __device__ __forceinline__ double far_dbl(const PrepArgs<R>& a, int q1, int q2, double Kd) {
     return (double)far_value<double>(a.payoff, Kd, a.E1d[q1 + a.g.eoff], a.E2d[q2 + a.g.eoff]);
 }
+// the far field at node (q1, q2) as a state value: FP64 in FP64 mode, a
+// double-float pair from the split e^{s} tables in FP32-bulk mode (no FP64
+// instruction in the step's preparation); prev selects tau_{n-1}, else tau_n
+template <typename R>
+__device__ __forceinline__ St<R> far_state(const PrepArgs<R>& a, int q1, int q2, bool prev) {
+    if constexpr (sizeof(R) == 4) {
+        const int i1 = q1 + a.g.eoff, i2 = q2 + a.g.eoff;
+        return far_value_df(a.payoff, prev ? a.Kdp_h : a.Kdn_h, prev ? a.Kdp_l : a.Kdn_l, a.E1h[i1], a.E1l[i1],
+                            a.E2h[i2], a.E2l[i2]);
+    } else {
+        return far_dbl(a, q1, q2, prev ? a.Kd_prev : a.Kd_now);
+    }
+}
 
 // cz = h_t (1-theta) (D V - r_w V + B V) at interior nodes (Z - V of Algorithm 1 step 2)
 template <typename R>
@@ -886,7 +899,7 @@ __device__ __forceinline__ void prep_body(const PrepArgs<R>& a) {
     const size_t idx = (size_t)m2 * ld + m1;
     using S_ = St<R>;
     if (m1 == 0 || m2 == 0 || m1 == N || m2 == N) {
-        a.Y[idx] = st_make<S_>(far_dbl(a, m1, m2, a.Kd_now));
+        a.Y[idx] = far_state(a, m1, m2, false);
         return;
     }
     const S_* V = a.V[0];
@@ -935,7 +948,7 @@ __device__ __forceinline__ void prep_body(const PrepArgs<R>& a) {
                     dz = st_diff(V[(size_t)q2 * ld + q1], v) - czm;
                     if (expl) dz += a.cz[(size_t)q2 * ldR + q1];
                 } else {
-                    dz = (R)(far_dbl(a, q1, q2, a.Kd_prev) - st_dbl(v)) - czm;
+                    dz = st_diff(far_state(a, q1, q2, true), v) - czm;
                 }
                 row += w1[c] * dz;
             }
