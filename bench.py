@@ -152,7 +152,7 @@ def algorithmic_bytes(cls, n, hcount=4):
 
 
 KERNEL_NAMES = ["k_prep", "k_row_forward(full)", "k_row_forward(incr)", "k_col(full)", "k_col(incr)",
-                "k_row_inverse(full)", "k_row_inverse(incr)", "k_dst_col", "k_dst_row+fwd"]
+                "k_row_inverse(full)", "k_row_inverse(incr)", "k_col_solve", "k_dst_row+fwd"]
 # the kernels of one fixed-point iteration (the B_w sweep of an increment fused with the DST solve)
 ITERATION_KERNELS = (7, 8, 4, 6)
 # SURVEY's algorithmic bytes of one cell-iteration of the FFT sweep alone (FP32, P = 2N, pruned R2C):
@@ -378,7 +378,7 @@ def run_ours(a):
     ck = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     # kernels launched in the timed region.  Device loop: per step k_explicit + k_prep and the
-    # difference sweep (5), setup and tally (2), per iteration dst_col, dst_row, check, col,
+    # difference sweep (5), setup and tally (2), per iteration col_solve, dst_row, check, col,
     # row_inverse (5).  Host loop: 5 per step, 4 per iteration.
     gpu_launches = sum(5 + 4 * k for k in iters) if a.host_loop else sum(7 + 5 * k for k in iters)
     # roofline pass: the next `steps` time steps with per-kernel CUDA events (host-driven loop,

@@ -199,13 +199,14 @@ pide2d_status pide2d_apply_jump(pide2d_t* h, const double* U, double tau, int fa
  *   M = (1 + ht theta r_w) I - ht theta (a11/2 d11 + a22/2 d22)
  * on the interior nodes (zero Dirichlet ring; the eq. 3.24 operator without
  * its mixed term, which the loop carries in the fixed point), it computes
- *   delta  = M^{-1} r         (DST-I along rows, then columns, and back),
+ *   delta  = M^{-1} r         (DST-I along rows, tridiagonal solves along
+ *                              columns for each row mode, DST-I back),
  *   bdelta = B_w delta        (the increment sweep of eq. 3.17: zero far field,
  *                              the midpoint interpolation of T_in folded into
  *                              the weight spectrum),
  *   *stop  = max |delta| / max(1, |delta|)  (eq. 3.25 for an iterate from 0),
  * through the same kernels and launch shapes as the time loop (row DST of r,
- * column DST pass, row DST pass with the R2C rows of delta, column pass,
+ * column solve pass, row DST pass with the R2C rows of delta, column pass,
  * inverse row pass).
  *   r           (N+1)^2 doubles [m2][m1], device or host; interior nodes used
  *   ht, theta   ht > 0, 0 < theta <= 1
@@ -227,7 +228,7 @@ enum {
     PIDE2D_KERNEL_COL_INCR,            /* column pass of an increment                          */
     PIDE2D_KERNEL_ROW_INVERSE_FULL,    /* inverse row pass + first residual + row DST          */
     PIDE2D_KERNEL_ROW_INVERSE_INCR,    /* inverse row pass + residual update + row DST         */
-    PIDE2D_KERNEL_DST_COL,             /* column DST, eigenvalue division, column DST          */
+    PIDE2D_KERNEL_COL_SOLVE,           /* tridiagonal solves along s2 of the row-DST modes    */
     PIDE2D_KERNEL_DST_ROW,             /* row DST back, state update, eq. 3.25 maximum, and   */
                                        /* the row pass of the increment's B_w sweep         */
     PIDE2D_KERNEL_CLASSES = 9
@@ -254,7 +255,7 @@ pide2d_status pide2d_profile_read(pide2d_t* h, pide2d_kernel_times* out);
  * the fixed-point tolerance).  Going backwards through the theta steps, each
  * step solves the transposed system of eq. 3.23 with the same fixed-point
  * machinery (the transposed jump sum is the correlation with the weights
- * flipped in both axes; the DST diffusion solve is symmetric), applies the
+ * flipped in both axes; the diffusion solve is symmetric), applies the
  * transposed departure interpolation (the mirrored stencil of eq. 3.22) and
  * contracts the adjoint fields with the derivatives of the weights (eq. 3.5),
  * of sigma_w sigma_w^T, r_w and kappa_w (eqs. 3.3, 3.6) and of the departure

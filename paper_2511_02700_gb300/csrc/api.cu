@@ -334,7 +334,7 @@ static pide2d_status record_theta_step(pide2d* H, int res, double theta, double 
 
 // ---------------------------------------------------------------------------
 // the fixed-point loop of one theta step as a CUDA graph:
-//   reset(FpCtl.k, FpCtl.conv) -> while(cond) { dst_col, dst_row, check, col, inv } -> tally
+//   reset(FpCtl.k, FpCtl.conv) -> while(cond) { col_solve, dst_row, check, col, inv } -> tally
 // k_fp_check clears the condition at convergence, at kmax or on a non-finite
 // residual, so every launch of the graph ends.
 // ---------------------------------------------------------------------------
@@ -342,7 +342,7 @@ namespace {
 constexpr size_t kMaxLoopGraphs = 24;
 
 template <typename R>
-cudaError_t record_loop_graph(pide2d* H, cudaGraph_t g, const DstColArgs<R>& da, const DstRowArgs<R>& ra,
+cudaError_t record_loop_graph(pide2d* H, cudaGraph_t g, const ColSolveArgs<R>& da, const DstRowArgs<R>& ra,
                               const ColArgs<R>& ca, const InvArgs<R>& ia, const char** where) {
     cudaStream_t cs = H->cap;
     FpCtl* ctl = H->at<FpCtl>(R_CTL);
@@ -377,7 +377,7 @@ cudaError_t record_loop_graph(pide2d* H, cudaGraph_t g, const DstColArgs<R>& da,
     PIDE_GTRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     auto iteration = [&]() -> cudaError_t {
         cudaError_t x;
-        if ((x = launch_dst_col<R>(da, cs)) != cudaSuccess) return x;
+        if ((x = launch_col_solve<R>(da, cs)) != cudaSuccess) return x;
         if ((x = cudaMemsetAsync(H->at<void>(R_RESID), 0, 16, cs)) != cudaSuccess) return x;
         if ((x = launch_dst_row<R>(ra, cs)) != cudaSuccess) return x;
         if ((x = launch_fp_check<R>(H->at<void>(R_RESID), ctl, H->tol, H->kmax, (unsigned long long)hnd, cs)) !=
@@ -405,7 +405,7 @@ cudaError_t record_loop_graph(pide2d* H, cudaGraph_t g, const DstColArgs<R>& da,
 }  // namespace
 
 template <typename R>
-static pide2d_status loop_graph(pide2d* H, const DstColArgs<R>& da, const DstRowArgs<R>& ra, const ColArgs<R>& ca,
+static pide2d_status loop_graph(pide2d* H, const ColSolveArgs<R>& da, const DstRowArgs<R>& ra, const ColArgs<R>& ca,
                                 const InvArgs<R>& ia, cudaGraphExec_t* exec) {
     std::string key;
     key.append(reinterpret_cast<const char*>(&da), sizeof da);
@@ -542,7 +542,7 @@ struct SolveArgs {
     FwdArgs<R> fa;
     ColArgs<R> caf, cai;
     InvArgs<R> iaf, iai;
-    DstColArgs<R> da;
+    ColSolveArgs<R> da;
     DstRowArgs<R> ra;
 };
 
@@ -623,19 +623,14 @@ static void build_solve_args(pide2d* H, const SolveSpec<R>& sp, SolveArgs<R>* ou
     ia.BV = diff ? sp.BVprev : nullptr;
     ia.E = H->at<R>(R_E);
     ia.tw = tw;
-    DstColArgs<R>& da = out->da;
+    ColSolveArgs<R>& da = out->da;
     da.g = g;
     da.E = H->at<R>(R_E);
     da.sin2 = H->at<R>(R_SIN2R);
-    da.c0 = 1.0 + htt * rw;
-    da.c1 = 2.0 * htt * a11 / (hg * hg);
-    da.c2 = 2.0 * htt * a22 / (hg * hg);
-    da.scale = (2.0 / N) * (2.0 / N);
-    da.rc0 = (R)da.c0;
-    da.rc1 = (R)da.c1;
-    da.rc2 = (R)da.c2;
-    da.rscale = (R)da.scale;
-    da.tw = tw;
+    da.rc0 = (R)(1.0 + htt * rw);
+    da.rc1 = (R)(2.0 * htt * a11 / (hg * hg));
+    da.rc2 = (R)(2.0 * htt * a22 / (hg * hg));
+    da.rscale = (R)(2.0 / N);
     DstRowArgs<R>& ra = out->ra;
     ra.g = g;
     ra.E = H->at<R>(R_E);
@@ -666,7 +661,7 @@ static pide2d_status fixed_point_solve(pide2d* H, const SolveSpec<R>& sp, int* i
     PIDE_LAUNCH(PIDE2D_KERNEL_ROW_FORWARD_FULL, launch_row_forward<R>(A.fa, H->stream));
     PIDE_LAUNCH(PIDE2D_KERNEL_COL_FULL, launch_col<R>(A.caf, H->stream));
     PIDE_LAUNCH(PIDE2D_KERNEL_ROW_INVERSE_FULL, launch_row_inverse<R>(A.iaf, H->stream));
-    DstColArgs<R>& da = A.da;
+    ColSolveArgs<R>& da = A.da;
     DstRowArgs<R>& ra = A.ra;
     ColArgs<R>& ca = A.cai;
     InvArgs<R>& ia = A.iai;
@@ -698,7 +693,7 @@ static pide2d_status fixed_point_solve(pide2d* H, const SolveSpec<R>& sp, int* i
     double resid = 0.0;
     bool conv = false;
     for (k = 1; k <= H->kmax; ++k) {
-        PIDE_LAUNCH(PIDE2D_KERNEL_DST_COL, launch_dst_col<R>(da, H->stream));
+        PIDE_LAUNCH(PIDE2D_KERNEL_COL_SOLVE, launch_col_solve<R>(da, H->stream));
         PIDE_CUDA(cudaMemsetAsync(H->at<void>(R_RESID), 0, 16, H->stream));
         PIDE_LAUNCH(PIDE2D_KERNEL_DST_ROW, launch_dst_row<R>(ra, H->stream));
         double rhost = 0.0;
@@ -1250,7 +1245,7 @@ static pide2d_status do_iteration_probe(pide2d* H, const double* r, double ht, d
     sp.device_loop = false;
     SolveArgs<R> A;
     build_solve_args<R>(H, sp, &A);
-    PIDE_CUDA(launch_dst_col<R>(A.da, s));
+    PIDE_CUDA(launch_col_solve<R>(A.da, s));
     PIDE_CUDA(cudaMemsetAsync(H->at<void>(R_RESID), 0, 16, s));
     PIDE_CUDA(launch_dst_row<R>(A.ra, s));
     PIDE_CUDA(launch_col<R>(A.cai, s));
@@ -1338,7 +1333,7 @@ struct GroupLayout {
         fa = o;      o += arr_bytes(sizeof(FwdArgs<R>), K);
         caf = o;     o += arr_bytes(sizeof(ColArgs<R>), K);
         iaf = o;     o += arr_bytes(sizeof(InvArgs<R>), K);
-        da = o;      o += arr_bytes(sizeof(DstColArgs<R>), K);
+        da = o;      o += arr_bytes(sizeof(ColSolveArgs<R>), K);
         ra = o;      o += arr_bytes(sizeof(DstRowArgs<R>), K);
         cai = o;     o += arr_bytes(sizeof(ColArgs<R>), K);
         iai = o;     o += arr_bytes(sizeof(InvArgs<R>), K);
@@ -1598,7 +1593,7 @@ static pide2d_status group_solve(pide2d* const* hs, int K, char* scratch, int up
             {
                 const JobsCtl head{st.conv, st.kconv, st.iter, 1};
                 const JobsCtl tail{st.conv, st.kconv, st.iter, 2};
-                cudaError_t x = launch_dst_col_jobs<R>(A0.da, (const DstColArgs<R>*)arr(L.da), K, head, upb, cs);
+                cudaError_t x = launch_col_solve_jobs<R>(A0.da, (const ColSolveArgs<R>*)arr(L.da), K, head, upb, cs);
                 if (x == cudaSuccess) x = launch_dst_row_jobs<R>(A0.ra, (const DstRowArgs<R>*)arr(L.ra), K, head, upb, cs);
                 if (x == cudaSuccess) x = launch_jobs_check(K, dchk, st, kmax_all, (unsigned long long)hin, cs);
                 if (x == cudaSuccess) x = launch_col_jobs<R>(A0.cai, (const ColArgs<R>*)arr(L.cai), K, tail, upb, cs);

@@ -84,13 +84,12 @@ template <typename R> struct InvArgs {
     const void* tw;
 };
 
-template <typename R> struct DstColArgs {
+template <typename R> struct ColSolveArgs {
     Geometry g;
-    R* E;
+    R* E;                    // row-DST modes, solved in place
     const R* sin2;           // sin^2(pi k / (2N)), k = 0..N
-    double c0, c1, c2, scale;// lambda = c0 + c1 sin2[k1] + c2 sin2[k2]; scale = (2/N)^2
-    R rc0, rc1, rc2, rscale; // the same, rounded once to the transform precision on the host
-    const void* tw;
+    R rc0, rc1, rc2;         // A_0's eigenvalues c0 + c1 sin2[k1] + c2 sin2[k2], rounded once on the host
+    R rscale;                // 2/N, the row DST pair's normalisation
 };
 
 template <typename R> struct DstRowArgs {
@@ -147,7 +146,7 @@ struct JobsCtl {
 template <typename R> cudaError_t launch_row_forward(const FwdArgs<R>& a, cudaStream_t s);
 template <typename R> cudaError_t launch_col(const ColArgs<R>& a, cudaStream_t s);
 template <typename R> cudaError_t launch_row_inverse(const InvArgs<R>& a, cudaStream_t s);
-template <typename R> cudaError_t launch_dst_col(const DstColArgs<R>& a, cudaStream_t s);
+template <typename R> cudaError_t launch_col_solve(const ColSolveArgs<R>& a, cudaStream_t s);
 template <typename R> cudaError_t launch_dst_row(const DstRowArgs<R>& a, cudaStream_t s);
 template <typename R> cudaError_t launch_prep(const PrepArgs<R>& a, cudaStream_t s);
 // the adjoint's weight contraction: acc[k1][k2] += conj(X) A for the spectra of the
@@ -169,7 +168,7 @@ template <typename R> cudaError_t launch_col_jobs(const ColArgs<R>& a0, const Co
                                                  int upb, cudaStream_t s);
 template <typename R> cudaError_t launch_row_inverse_jobs(const InvArgs<R>& a0, const InvArgs<R>* arr, int K,
                                                          JobsCtl jc, int upb, cudaStream_t s);
-template <typename R> cudaError_t launch_dst_col_jobs(const DstColArgs<R>& a0, const DstColArgs<R>* arr, int K,
+template <typename R> cudaError_t launch_col_solve_jobs(const ColSolveArgs<R>& a0, const ColSolveArgs<R>* arr, int K,
                                                      JobsCtl jc, int upb, cudaStream_t s);
 template <typename R> cudaError_t launch_dst_row_jobs(const DstRowArgs<R>& a0, const DstRowArgs<R>* arr, int K,
                                                      JobsCtl jc, int upb, cudaStream_t s);

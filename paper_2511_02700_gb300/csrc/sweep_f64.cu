@@ -8,7 +8,7 @@ namespace pide {
     template cudaError_t launch_row_forward<R>(const FwdArgs<R>&, cudaStream_t);                    \
     template cudaError_t launch_col<R>(const ColArgs<R>&, cudaStream_t);                            \
     template cudaError_t launch_row_inverse<R>(const InvArgs<R>&, cudaStream_t);                    \
-    template cudaError_t launch_dst_col<R>(const DstColArgs<R>&, cudaStream_t);                     \
+    template cudaError_t launch_col_solve<R>(const ColSolveArgs<R>&, cudaStream_t);                     \
     template cudaError_t launch_dst_row<R>(const DstRowArgs<R>&, cudaStream_t);                     \
     template cudaError_t launch_prep<R>(const PrepArgs<R>&, cudaStream_t);                          \
     template cudaError_t launch_row_dst<R>(const Geometry&, const double*, R*, const void*, cudaStream_t); \
@@ -22,7 +22,7 @@ namespace pide {
     template cudaError_t launch_row_forward_jobs<R>(const FwdArgs<R>&, const FwdArgs<R>*, int, JobsCtl, int, cudaStream_t); \
     template cudaError_t launch_col_jobs<R>(const ColArgs<R>&, const ColArgs<R>*, int, JobsCtl, int, cudaStream_t); \
     template cudaError_t launch_row_inverse_jobs<R>(const InvArgs<R>&, const InvArgs<R>*, int, JobsCtl, int, cudaStream_t); \
-    template cudaError_t launch_dst_col_jobs<R>(const DstColArgs<R>&, const DstColArgs<R>*, int, JobsCtl, int, cudaStream_t); \
+    template cudaError_t launch_col_solve_jobs<R>(const ColSolveArgs<R>&, const ColSolveArgs<R>*, int, JobsCtl, int, cudaStream_t); \
     template cudaError_t launch_dst_row_jobs<R>(const DstRowArgs<R>&, const DstRowArgs<R>*, int, JobsCtl, int, cudaStream_t); \
     template cudaError_t launch_prep_jobs<R>(const PrepArgs<R>&, const PrepArgs<R>*, int, bool, cudaStream_t); \
     template cudaError_t launch_weights_col<R>(const Geometry&, const void*, void*, void*, const void*, \

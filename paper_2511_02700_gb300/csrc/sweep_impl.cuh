@@ -1,6 +1,7 @@
 // Time-stepping kernels of pide2d (templates; instantiated per precision in
 // sweep_f32.cu and sweep_f64.cu): the jump sum B_w by zero-padded 2D FFT
-// cross-correlation (eqs. 3.10-3.17), the diffusion solve by DST-I, and the
+// cross-correlation (eqs. 3.10-3.17), the diffusion solve (row DST-I and
+// tridiagonal column solves), and the
 // semi-Lagrangian explicit part (Algorithm 1, steps 1-4).
 //
 // Data flow of one fixed-point iteration (all transforms length P = 2N):
@@ -10,12 +11,12 @@
 //                  product with conj(w^)/P^2, inverse FFT, keep rows 1..N
 //   k_row_inverse  per row pair: C2R, B_w at the interior nodes, state and
 //                  residual update, then the row DST-I of the residual -> E
-//   k_dst_col      per column pair: DST-I, divide by the eigenvalues of the
-//                  diffusion operator, DST-I back
+//   k_col_solve    per column pair of row-DST modes: the tridiagonal solve of
+//                  the diffusion operator along s2 (two block scans)
 //   k_dst_row      per row pair: DST-I back to nodes = increment, state
 //                  update and the eq. 3.25 maximum
 // DST-I of length N-1 is the imaginary part of the length-2N DFT of the
-// odd extension, so every pass uses the same block FFT.
+// odd extension, so every transform uses the same block FFT.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -566,64 +567,251 @@ PIDE_FFT_JOBS_KERNEL(R, P) k_row_inverse_jobs(const InvArgs<R>* __restrict__ arr
 }
 
 // ---------------------------------------------------------------------------
-// column DST pass with the eigenvalue division between the two transforms
+// column solve of the non-mixed diffusion operator in the row-DST basis.
+// After the row DST, mode k1 of A_0 acts along s2 as the constant-coefficient
+// tridiagonal matrix T = c tridiag(-1, 2 + s, -1) on rows 1..N-1 (Dirichlet
+// rows 0 and N), c = c2/4, s = (c0 + c1 sin^2(pi k1/2N))/c: its eigenvalues in
+// the column DST basis are c0 + c1 sin^2(pi k1/2N) + c2 sin^2(pi k2/2N).  Its LU
+// factors have a closed form: with q = e^{-th}, th = 2 asinh(sqrt(s)/2) (so
+// q + 1/q = 2 + s) and psi_m = 1 - q^{2m}, the pivots are u_i = (c/q)
+// psi_{i+1}/psi_i.  Scaled by psi, both substitutions become recursions with
+// the constant multiplier q,
+//     z_i = psi_i b_i + q z_{i-1}                       (z_0 = 0, rows upward)
+//     t_i = (q/c) z_i / (psi_i psi_{i+1}) + q t_{i+1}   (t_N = 0, rows downward)
+//     x_i = psi_i t_i,
+// which a block evaluates as two scans over its threads' row chunks.  It is the
+// Thomas algorithm with exact pivots (backward stable for the diagonally
+// dominant T), equal to the column DST-I eigen-solve of the same matrix.
 // ---------------------------------------------------------------------------
+template <typename R, int P> struct ColSolveCfg {
+    static constexpr int N = P / 2;
+    static constexpr int RPT = N >= 512 ? 16 : (N >= 64 ? N / 32 : 1);  // rows per thread
+    static constexpr int NTH = N / RPT >= 32 ? N / RPT : 32;             // threads (rows >= N are zero)
+    static constexpr int NW = NTH / 32;
+    // FP32: 64 registers (four 256-thread blocks per SM at N = 4096)
+    static constexpr int MINB = sizeof(R) == 4 ? 1024 / NTH : 1;
+    // the column pair staged in shared memory, one pad pair per 16 rows
+    static constexpr int ROWS = NTH * RPT;
+    static constexpr size_t SMEM = (size_t)(ROWS + ROWS / 16) * sizeof(cpx<R>);
+};
+__device__ __forceinline__ int col_pad(int row) { return row + (row >> 4); }
+
+// The recursion y_t = v_t + Q y_{t-1} over the block's threads, in increasing
+// thread order (REV = false) or decreasing (REV = true), for two columns at once
+// (x and y of the pair): returns y at the previous thread's chunk end (0 for the
+// first thread).  wsum: NW pairs of shared memory; one block barrier.
+template <typename R, int NW, bool REV>
+__device__ __forceinline__ cpx<R> chunk_carry(cpx<R> v, R Qa, R Qb, cpx<R>* wsum) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int l = REV ? 31 - lane : lane;
+    const int wp = REV ? NW - 1 - w : w;
+    R pa = Qa, pb = Qb, la = R(1), lb = R(1);   // Q^off, and Q^l accumulated bit by bit
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const R ua = REV ? __shfl_down_sync(0xffffffffu, v.x, off) : __shfl_up_sync(0xffffffffu, v.x, off);
+        const R ub = REV ? __shfl_down_sync(0xffffffffu, v.y, off) : __shfl_up_sync(0xffffffffu, v.y, off);
+        if (l >= off) {
+            v.x += pa * ua;
+            v.y += pb * ub;
+        }
+        if (l & off) {
+            la *= pa;
+            lb *= pb;
+        }
+        pa *= pa;
+        pb *= pb;
+    }
+    // v: inclusive value at position l; pa, pb: Q^32
+    R ea = REV ? __shfl_down_sync(0xffffffffu, v.x, 1) : __shfl_up_sync(0xffffffffu, v.x, 1);
+    R eb = REV ? __shfl_down_sync(0xffffffffu, v.y, 1) : __shfl_up_sync(0xffffffffu, v.y, 1);
+    if (l == 0) ea = eb = R(0);
+    if constexpr (NW > 1) {
+        if (l == 31) wsum[wp] = v;
+        __syncthreads();
+        R sa = R(0), sb = R(0);                 // the value at the end of warp position wp - 1
+        for (int u = 0; u < wp; ++u) {
+            const cpx<R> W = wsum[u];
+            sa = sa * pa + W.x;
+            sb = sb * pb + W.y;
+        }
+        ea += la * sa;
+        eb += lb * sb;
+    }
+    return mk<R>(ea, eb);
+}
+
+// a / b: the fast FP32 quotient (2 ulp; the solve is the fixed point's
+// preconditioner, so it sets only the contraction), exact in FP64
+template <typename R> __device__ __forceinline__ R pc_div(R a, R b) {
+    if constexpr (sizeof(R) == 4) return __fdividef(a, b);
+    else return a / b;
+}
+
+// per column of the pair: th, q = e^{-th}, q^2, psi_1, q^RPT and q/c
+template <typename R> struct ColConst {
+    R th, q, qq, p1, Q, g;
+};
+
 template <typename R, int P>
-__device__ __forceinline__ void dst_col_body(const DstColArgs<R>& a, int upb) {
+__device__ __forceinline__ void col_solve_body(const ColSolveArgs<R>& a, int pair) {
     using C = cpx<R>;
-    using CF = Cfg<R, P>;
-    constexpr int NT = CF::NT, N = P / 2;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int unit = threadIdx.x / NT, t = threadIdx.x - unit * NT;
-    C* buf = reinterpret_cast<C*>(smem_raw) + (size_t)unit * CF::ULEN;
-    const int u = blockIdx.x * upb + unit;
-    const int ka = 2 * u, kb = ka + 1;
-    const bool valid = ka < N;
+    using SC = ColSolveCfg<R, P>;
+    constexpr int N = SC::N, RPT = SC::RPT, NW = SC::NW;
+    __shared__ C wsum[2][NW];
+    __shared__ ColConst<R> kc[2];
+    const int ka = 2 * pair;                    // columns ka, ka + 1 (mode k1 = column index)
+    if (ka >= N) return;                        // uniform across the block
     constexpr int GE = rgroup<R>();
-    const int gE = ka / GE, ca = ka - gE * GE, cb = ca + 1;
-    R* col = a.E + (size_t)gE * N * GE;
-    const C* tw = (const C*)a.tw;
-    auto load = [&](int i) -> C {
-        const int j = i <= N ? i : P - i;
-        const R sg = i <= N ? R(1) : R(-1);
-        R xa = 0, xb = 0;
-        if (valid && j >= 1 && j <= N - 1) {
-            xa = sg * col[(size_t)j * GE + ca];
-            xb = sg * col[(size_t)j * GE + cb];
+    const int gE = ka / GE, ce = ka - gE * GE;
+    C* col = reinterpret_cast<C*>(a.E + (size_t)gE * N * GE + ce);   // row i at col[i * GE / 2]
+    constexpr int RS = GE / 2;
+    const int i0 = threadIdx.x * RPT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* stage = reinterpret_cast<C*>(smem_raw);
+    // per column: q = e^{-th} and psi_1 once per block; psi_{m+1} = psi_m +
+    // q^{2m} psi_1 (a sum of positive terms) regenerates a chunk's psi from
+    // psi_{i0} and q^{2 i0} in each pass
+    if (threadIdx.x < 2) {
+        const R cc = R(0.25) * a.rc2;
+        const R sv = (a.rc0 + a.rc1 * a.sin2[ka + threadIdx.x]) / cc;
+        ColConst<R> k;
+        k.th = R(2) * asinh(sqrt(sv) * R(0.5));
+        k.q = exp(-k.th);
+        k.qq = k.q * k.q;
+        k.p1 = -expm1(R(-2) * k.th);
+        k.Q = exp(-(R)RPT * k.th);
+        k.g = k.q / cc;
+        kc[threadIdx.x] = k;
+    }
+    // coalesced load of the pair (rows outside 1..N-1 are zero), then each
+    // thread takes its chunk of RPT consecutive rows
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+        const int i = (int)threadIdx.x + r * SC::NTH;
+        stage[col_pad(i)] = (i >= 1 && i <= N - 1) ? col[(size_t)i * RS] : mk<R>(R(0), R(0));
+    }
+    __syncthreads();
+    C v[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) v[r] = stage[col_pad(i0 + r)];
+    const ColConst<R> ka_ = kc[0], kb_ = kc[1];
+    const R q_a = ka_.q, q_b = kb_.q;
+    const R Qa = ka_.Q, Qb = kb_.Q;             // q^RPT
+    // psi_i = 1 to working precision once q^{2i} < 2^-25 (FP32; 2^-54 in FP64):
+    // then the chunk's recursions need neither psi nor the quotient
+    const R thmin = ka_.th < kb_.th ? ka_.th : kb_.th;
+    const bool plain = R(2) * (R)i0 * thmin > (sizeof(R) == 4 ? R(18) : R(38));
+    // forward: z_i = psi_i b_i + q z_{i-1}
+    C acc = mk<R>(R(0), R(0));
+    if (plain) {
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            acc.x = v[r].x + q_a * acc.x;
+            acc.y = v[r].y + q_b * acc.y;
+            v[r] = acc;
         }
-        return mk<R>(xa, xb);
-    };
-    const R c0 = a.rc0, c1 = a.rc1, c2 = a.rc2, sc = a.rscale;
-    const R sa = valid ? a.sin2[ka] : R(0);
-    const R sb = valid ? a.sin2[kb] : R(0);
-    auto divide = [&](int k2, C zz) {
-        if (k2 == 0) {
-            buf[padi(0)] = mk<R>(0, 0);
-            buf[padi(N)] = mk<R>(0, 0);
-            return;
+    } else {
+        R pa = -expm1(R(-2) * (R)i0 * ka_.th), pb = -expm1(R(-2) * (R)i0 * kb_.th);
+        R ea = exp(R(-2) * (R)i0 * ka_.th), eb = exp(R(-2) * (R)i0 * kb_.th);
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            acc.x = pa * v[r].x + q_a * acc.x;
+            acc.y = pb * v[r].y + q_b * acc.y;
+            v[r] = acc;
+            pa += ea * ka_.p1;
+            pb += eb * kb_.p1;
+            ea *= ka_.qq;
+            eb *= kb_.qq;
         }
-        if (k2 >= N) return;
-        const R s2 = a.sin2[k2];
-        const R ta = R(-0.5) * zz.y * sc / (c0 + c1 * sa + c2 * s2);
-        const R tb = R(0.5) * zz.x * sc / (c0 + c1 * sb + c2 * s2);
-        buf[padi(k2)] = mk<R>(ta, tb);
-        buf[padi(P - k2)] = mk<R>(-ta, -tb);
-    };
-    block_fft<R, -1, P>(buf, t, tw, load, divide);
-    auto store = [&](int m2, C zz) {
-        if (valid && m2 >= 1 && m2 <= N - 1) {
-            col[(size_t)m2 * GE + ca] = R(-0.5) * zz.y;
-            col[(size_t)m2 * GE + cb] = R(0.5) * zz.x;
+    }
+    {
+        const C cin = chunk_carry<R, NW, false>(acc, Qa, Qb, wsum[0]);
+        R fa = q_a, fb = q_b;
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            v[r].x += fa * cin.x;
+            v[r].y += fb * cin.y;
+            fa *= q_a;
+            fb *= q_b;
         }
-    };
-    block_fft<R, -1, P>(buf, t, tw, SmemLoad<R>{buf}, store);
+    }
+    // backward: t_i = (q/c) z_i / (psi_i psi_{i+1}) + q t_{i+1}
+    if (plain) {
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            const bool in = i0 + r <= N - 1;
+            v[r].x = in ? ka_.g * v[r].x : R(0);
+            v[r].y = in ? kb_.g * v[r].y : R(0);
+        }
+    } else {
+        R pa = -expm1(R(-2) * (R)i0 * ka_.th), pb = -expm1(R(-2) * (R)i0 * kb_.th);
+        R ea = exp(R(-2) * (R)i0 * ka_.th), eb = exp(R(-2) * (R)i0 * kb_.th);
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            const int i = i0 + r;
+            const R na = pa + ea * ka_.p1, nb = pb + eb * kb_.p1;
+            const bool in = i >= 1 && i <= N - 1;
+            v[r].x = in ? pc_div(ka_.g * v[r].x, pa * na) : R(0);
+            v[r].y = in ? pc_div(kb_.g * v[r].y, pb * nb) : R(0);
+            pa = na;
+            pb = nb;
+            ea *= ka_.qq;
+            eb *= kb_.qq;
+        }
+    }
+    acc = mk<R>(R(0), R(0));
+#pragma unroll
+    for (int r = RPT - 1; r >= 0; --r) {
+        acc.x = v[r].x + q_a * acc.x;
+        acc.y = v[r].y + q_b * acc.y;
+        v[r] = acc;
+    }
+    {
+        const C cin = chunk_carry<R, NW, true>(acc, Qa, Qb, wsum[1]);
+        R fa = q_a, fb = q_b;
+#pragma unroll
+        for (int r = RPT - 1; r >= 0; --r) {
+            v[r].x += fa * cin.x;
+            v[r].y += fb * cin.y;
+            fa *= q_a;
+            fb *= q_b;
+        }
+    }
+    // x_i = psi_i t_i, with the row DST pair's normalisation, staged for a
+    // coalesced store of rows 1..N-1 (the chunk reads of every thread ended
+    // before the first scan's barrier)
+    const R sc = a.rscale;
+    if (plain) {
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) stage[col_pad(i0 + r)] = mk<R>(sc * v[r].x, sc * v[r].y);
+    } else {
+        R pa = -expm1(R(-2) * (R)i0 * ka_.th), pb = -expm1(R(-2) * (R)i0 * kb_.th);
+        R ea = exp(R(-2) * (R)i0 * ka_.th), eb = exp(R(-2) * (R)i0 * kb_.th);
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            stage[col_pad(i0 + r)] = mk<R>(sc * pa * v[r].x, sc * pb * v[r].y);
+            pa += ea * ka_.p1;
+            pb += eb * kb_.p1;
+            ea *= ka_.qq;
+            eb *= kb_.qq;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+        const int i = (int)threadIdx.x + r * SC::NTH;
+        if (i >= 1 && i <= N - 1) col[(size_t)i * RS] = stage[col_pad(i)];
+    }
 }
 template <typename R, int P>
-PIDE_FFT_KERNEL(R, P) k_dst_col(const __grid_constant__ DstColArgs<R> a) { dst_col_body<R, P>(a, Cfg<R, P>::UNITS); }
+__global__ void __launch_bounds__(ColSolveCfg<R, P>::NTH, ColSolveCfg<R, P>::MINB) k_col_solve(const __grid_constant__ ColSolveArgs<R> a) {
+    col_solve_body<R, P>(a, blockIdx.x);
+}
 template <typename R, int P>
-PIDE_FFT_JOBS_KERNEL(R, P) k_dst_col_jobs(const DstColArgs<R>* __restrict__ arr, JobsCtl jc) {
+__global__ void __launch_bounds__(ColSolveCfg<R, P>::NTH, ColSolveCfg<R, P>::MINB) k_col_solve_jobs(const ColSolveArgs<R>* __restrict__ arr,
+                                                                           JobsCtl jc) {
     if (jc.skip(blockIdx.y)) return;
-    dst_col_body<R, P>(arr[blockIdx.y], blockDim.x / Cfg<R, P>::NT);
+    col_solve_body<R, P>(arr[blockIdx.y], blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1378,11 +1566,17 @@ cudaError_t launch_row_inverse_jobs(const InvArgs<R>& a0, const InvArgs<R>* arr,
 #undef CASE
 }
 template <typename R>
-cudaError_t launch_dst_col_jobs(const DstColArgs<R>& a0, const DstColArgs<R>* arr, int K, JobsCtl jc, int upb,
-                              cudaStream_t s) {
-#define CASE(PP)                                                                                             \
-    if constexpr (LoopSize<R, PP>::ok) return launch_fft_kernel_jobs<R, PP>(k_dst_col_jobs<R, PP>, arr, K, jc, PP / 4, 0, upb, s); \
-    else return cudaErrorInvalidValue;
+cudaError_t launch_col_solve_jobs(const ColSolveArgs<R>& a0, const ColSolveArgs<R>* arr, int K, JobsCtl jc, int upb,
+                                  cudaStream_t s) {
+    (void)upb;                               // one block per column pair
+#define CASE(PP)                                                                                      \
+    {                                                                                                 \
+        using SC = ColSolveCfg<R, PP>;                                                                \
+        set_smem(k_col_solve_jobs<R, PP>, SC::SMEM);                                                  \
+        const dim3 grid(PP / 4, K);                                                                   \
+        k_col_solve_jobs<R, PP><<<grid, SC::NTH, SC::SMEM, s>>>(arr, jc);                             \
+        return cudaGetLastError();                                                                    \
+    }
     PIDE_SWITCH_P(a0.g.P, CASE)
 #undef CASE
 }
@@ -1436,10 +1630,14 @@ cudaError_t launch_row_inverse(const InvArgs<R>& a, cudaStream_t s) {
 #undef CASE
 }
 template <typename R>
-cudaError_t launch_dst_col(const DstColArgs<R>& a, cudaStream_t s) {
-#define CASE(PP)                                                                       \
-    if constexpr (LoopSize<R, PP>::ok) return launch_fft_kernel<R, PP>(k_dst_col<R, PP>, a, PP / 4, 0, s); \
-    else return cudaErrorInvalidValue;
+cudaError_t launch_col_solve(const ColSolveArgs<R>& a, cudaStream_t s) {
+#define CASE(PP)                                                                                      \
+    {                                                                                                 \
+        using SC = ColSolveCfg<R, PP>;                                                                \
+        set_smem(k_col_solve<R, PP>, SC::SMEM);                                                       \
+        k_col_solve<R, PP><<<PP / 4, SC::NTH, SC::SMEM, s>>>(a);                                      \
+        return cudaGetLastError();                                                                    \
+    }
     PIDE_SWITCH_P(a.g.P, CASE)
 #undef CASE
 }
