@@ -146,7 +146,7 @@ def algorithmic_bytes(cls, n, hcount=4):
         4: spec_n + wh + spec_n,                               # column pass incr
         5: spec_n + 8 * cells + 8 * cells + 16 * cells + 4 * cells,   # inverse full: S, BV, BY, W+Y, E
         6: spec_n + 16 * cells + 4 * cells + 4 * cells,        # inverse incr: S, BY, D, E
-        7: 8 * cells,                                          # column DST
+        7: 8 * cells,                                          # column solve (E in, E out)
         8: 4 * cells + 16 * cells + 4 * cells + spec_n,        # row DST back (E, Y, D) + increment R2C rows
     }[cls]
 
