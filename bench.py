@@ -155,7 +155,7 @@ KERNEL_NAMES = ["k_prep", "k_row_forward(full)", "k_row_forward(incr)", "k_col(f
                 "k_row_inverse(full)", "k_row_inverse(incr)", "k_col_solve", "k_dst_row+fwd"]
 # the kernels of one fixed-point iteration (the B_w sweep of an increment fused with the DST solve)
 ITERATION_KERNELS = (7, 8, 4, 6)
-# SURVEY's algorithmic bytes of one cell-iteration of the FFT sweep alone (FP32, P = 2N, pruned R2C):
+# algorithmic bytes of one cell-iteration of the FFT sweep alone (FP32, P = 2N, pruned R2C):
 # read Y 4, two round trips of the N x (P/2+1) intermediate 32, read w^ 16, read W + write RHS 8
 SWEEP_BYTES_PER_CELL = 60
 
