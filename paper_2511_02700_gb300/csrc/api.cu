@@ -104,7 +104,7 @@ void fill_layout(int N, Layout& L) {
     L.size[R_PART] = (size_t)((N * N + 255) / 256) * 3 * 8;
     L.size[R_PARAMS] = 16 * 8;
     L.size[R_MOMENT] = moment_doubles() * 8;
-    L.size[R_GL] = (size_t)kGlTotal * 8;
+    L.size[R_GL] = (size_t)(kGlTotal + kKtabMax) * 8;     // quadrature nodes, then the K_nu table
     L.size[R_RESID] = 16;
     L.size[R_CTL] = sizeof(FpCtl);
     size_t o = 0;
@@ -905,7 +905,7 @@ static std::vector<double> quadrature_nodes() {
 }
 
 // the precompute on a z-lattice of N x N cells of width hz (N_z = N/2)
-static cudaError_t precompute_core(int N, double hz, const double* dgl, const pide2d_model& m, double* omega,
+static cudaError_t precompute_core(int N, double hz, double* dgl, const pide2d_model& m, double* omega,
                                    double* part, double* moment, double* params, cudaStream_t s) {
     // Levy density constants (Sec. 4)
     const double r11 = m.rho[0], r12 = m.rho[1], r22 = m.rho[2];
@@ -923,6 +923,31 @@ static cudaError_t precompute_core(int N, double hz, const double* dgl, const pi
     L.logpref = std::log(m.delta / kPi) + L.nu * std::log(L.c1) - 0.5 * std::log(det);
     L.pref0 = m.delta / (kPi * std::sqrt(det));
     L.gamma_nu = std::tgamma(L.nu);
+    // the density's ln(e^x K_nu(x)) from a table over every x = c1 |z|_{rho^-1} that a
+    // quadrature node outside R_I can take (|z|_inf > 2 hz up to the lattice corner)
+    {
+        const double tr = 0.5 * (L.Ri11 + L.Ri22);
+        const double dd = std::sqrt(0.25 * (L.Ri11 - L.Ri22) * (L.Ri11 - L.Ri22) + L.Ri12 * L.Ri12);
+        const double x_lo = 0.9 * L.c1 * std::sqrt(tr - dd) * 2.0 * hz;
+        const double x_hi = 1.1 * L.c1 * std::sqrt(tr + dd) * std::sqrt(2.0) * (N / 2 + 1) * hz;
+        double du = 0.01;
+        const double span = std::log(x_hi / x_lo);
+        int n = (int)std::ceil(span / du) + 14;
+        if (n > kKtabMax) {
+            du = span / (kKtabMax - 14);
+            n = kKtabMax;
+        }
+        // nodes on the lattice du Z: models with the same nu (the perturbed ones of
+        // the adjoint's central differences) read the same interpolant of x
+        const double u0 = du * std::floor(std::log(x_lo) / du - 5.0);
+        double* tab = dgl + kGlTotal;
+        const cudaError_t te = launch_ktab(L.nu, u0, du, n, tab, s);
+        if (te != cudaSuccess) return te;
+        L.ktab = tab;
+        L.ku0 = u0;
+        L.kidu = 1.0 / du;
+        L.kn = n;
+    }
 
     WeightJob j{};
     j.N = N;
@@ -2133,7 +2158,7 @@ void price_layout(pide2d_price* H) {
         o += align256(bytes);
         return at;
     };
-    H->off_gl = take((size_t)kGlTotal * 8);
+    H->off_gl = take((size_t)(kGlTotal + kKtabMax) * 8);
     H->off_omega = take((size_t)nzz * nzz * 8);
     H->off_pad = take((size_t)(P / 2) * (P / 2) * 8);
     H->off_part = take((size_t)((nzz * nzz + 255) / 256) * 3 * 8);

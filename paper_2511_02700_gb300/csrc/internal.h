@@ -319,7 +319,13 @@ struct LevyParams {
     double alpha, nu, c1, logpref, Ri11, Ri12, Ri22, b1, b2;  // l(z) pieces
     double pref0;            // delta / (pi sqrt(det rho))
     double gamma_nu;         // Gamma(nu)
+    // ln(e^x K_nu(x)) at u = ku0 + i / kidu, i < kn (NULL: no table)
+    const double* ktab;
+    double ku0, kidu;
+    int kn;
 };
+constexpr int kKtabMax = 4096;          // entries of the K_nu table (after the quadrature nodes)
+cudaError_t launch_ktab(double nu, double u0, double du, int n, double* tab, cudaStream_t s);
 struct WeightJob {
     int N;
     double h;
