@@ -923,12 +923,13 @@ static cudaError_t precompute_core(int N, double hz, double* dgl, const pide2d_m
     L.logpref = std::log(m.delta / kPi) + L.nu * std::log(L.c1) - 0.5 * std::log(det);
     L.pref0 = m.delta / (kPi * std::sqrt(det));
     L.gamma_nu = std::tgamma(L.nu);
-    // the density's ln(e^x K_nu(x)) from a table over every x = c1 |z|_{rho^-1} that a
-    // quadrature node outside R_I can take (|z|_inf > 2 hz up to the lattice corner)
+    // ln(e^x K_nu(x)) from a table over every x = c1 |z|_{rho^-1} that a quadrature
+    // node can take: from 1e-8 (below it the R_I moment uses the x -> 0 limit of
+    // x^nu K_nu) up to the lattice corner
     {
         const double tr = 0.5 * (L.Ri11 + L.Ri22);
         const double dd = std::sqrt(0.25 * (L.Ri11 - L.Ri22) * (L.Ri11 - L.Ri22) + L.Ri12 * L.Ri12);
-        const double x_lo = 0.9 * L.c1 * std::sqrt(tr - dd) * 2.0 * hz;
+        const double x_lo = 1e-8;
         const double x_hi = 1.1 * L.c1 * std::sqrt(tr + dd) * std::sqrt(2.0) * (N / 2 + 1) * hz;
         double du = 0.01;
         const double span = std::log(x_hi / x_lo);

@@ -38,11 +38,6 @@ __device__ double bessel_k_scaled(double nu, double x) {
     return s * h;
 }
 
-// x^nu K_nu(x), bounded as x -> 0 (limit 2^(nu-1) Gamma(nu))
-__device__ double xnu_knu(double nu, double x, double gamma_nu) {
-    if (x < 1e-8) return exp2(nu - 1.0) * gamma_nu;
-    return exp(nu * log(x) - x) * bessel_k_scaled(nu, x);
-}
 
 // ln(e^x K_nu(x)): 8-point Lagrange interpolation in u = ln x on the
 // model's table (nodes base..base+7 around u), else the trapezoidal sum.  In u
@@ -73,6 +68,12 @@ __device__ double log_ek(const LevyParams& L, double x) {
         }
     }
     return log(bessel_k_scaled(L.nu, x));
+}
+
+// x^nu K_nu(x), bounded as x -> 0 (limit 2^(nu-1) Gamma(nu))
+__device__ double xnu_knu(const LevyParams& L, double x) {
+    if (x < 1e-8) return exp2(L.nu - 1.0) * L.gamma_nu;
+    return exp(L.nu * log(x) - x + log_ek(L, x));
 }
 
 // l(z), Sec. 4
@@ -184,7 +185,7 @@ __global__ void k_moment(LevyParams L, double H, const double* glx, const double
         const double dn = sqrt(L.Ri11 * d1 * d1 + 2.0 * L.Ri12 * d1 * d2 + L.Ri22 * d2 * d2);
         const double ed = L.b1 * d1 + L.b2 * d2;
         // rho^3 d d^T l(rho d) = rho^(1-2 alpha) d d^T F, F = rho^(2 nu) l(rho d)
-        const double F = L.pref0 * xnu_knu(L.nu, L.c1 * dn * rho, L.gamma_nu) * pow(dn, -2.0 * L.nu) * exp(rho * ed);
+        const double F = L.pref0 * xnu_knu(L, L.c1 * dn * rho) * pow(dn, -2.0 * L.nu) * exp(rho * ed);
         const double g = wr * glw[ti] * pow(rho, 1.0 - 2.0 * L.alpha) * F;
         m11 += g * d1 * d1;
         m12 += g * d1 * d2;
