@@ -117,6 +117,50 @@ void set_smem(K kernel, size_t bytes) {
 #define PIDE_FFT_KERNEL(R, P) __global__ void __launch_bounds__(Cfg<R, P>::THREADS, Cfg<R, P>::MINB)
 #define PIDE_FFT_JOBS_KERNEL(R, P) __global__ void __launch_bounds__(Cfg<R, P>::MAXT, Cfg<R, P>::JMINB)
 
+// Split the packed transform of two real rows in buf (natural order) into the
+// two rows' spectra (Hermitian symmetry) and write them as spectrum rows rho and
+// rho + 1 of S [group][row][c].  In FP32 a group's two columns of one row are 16
+// contiguous bytes, written with one store.
+template <typename R, int P>
+__device__ __forceinline__ void store_spectrum_rows(const cpx<R>* buf, cpx<R>* S, int rows, int ng, int rho, int t,
+                                                    bool valid) {
+    using C = cpx<R>;
+    constexpr int NT = P / 16;
+    constexpr int Gc = cgroup<R>();
+    auto split = [&](int k, C& xa, C& xb) {
+        xa = mk<R>(0, 0);
+        xb = mk<R>(0, 0);
+        if (k <= P / 2) {
+            const C zk = buf[padi(k)];
+            const C zm = buf[padi((P - k) & (P - 1))];
+            xa = mk<R>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
+            xb = mk<R>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
+        }
+    };
+    for (int g = t; g < ng; g += NT) {
+        if constexpr (sizeof(R) == 4 && Gc == 2) {
+            C a0, b0, a1, b1;
+            split(2 * g, a0, b0);
+            split(2 * g + 1, a1, b1);
+            if (valid) {
+                float4* row = reinterpret_cast<float4*>(S + ((size_t)g * rows + rho) * Gc);
+                row[0] = make_float4(a0.x, a0.y, a1.x, a1.y);
+                row[1] = make_float4(b0.x, b0.y, b1.x, b1.y);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < Gc; ++c) {
+                C xa, xb;
+                split(g * Gc + c, xa, xb);
+                if (valid) {
+                    S[((size_t)g * rows + rho) * Gc + c] = xa;
+                    S[((size_t)g * rows + rho + 1) * Gc + c] = xb;
+                }
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // forward row pass: T_in along s1 (from staged nodes) + packed R2C
 // ---------------------------------------------------------------------------
@@ -206,26 +250,7 @@ __device__ __forceinline__ void row_forward_body(const FwdArgs<R>& a, int upb) {
         };
         block_fft<R, -1, P>(buf, t, tw, load, SmemStore<R>{buf});
     }
-    constexpr int Gc = cgroup<R>();
-    C* S = (C*)a.S;
-    const int rows = a.g.rows;
-    for (int g = t; g < a.g.ng; g += NT) {
-#pragma unroll
-        for (int c = 0; c < Gc; ++c) {
-            const int k = g * Gc + c;
-            C xa = mk<R>(0, 0), xb = mk<R>(0, 0);
-            if (k <= P / 2) {
-                const C zk = buf[padi(k)];
-                const C zm = buf[padi((P - k) & (P - 1))];
-                xa = mk<R>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
-                xb = mk<R>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
-            }
-            if (valid) {
-                S[((size_t)g * rows + rho) * Gc + c] = xa;
-                S[((size_t)g * rows + rho + 1) * Gc + c] = xb;
-            }
-        }
-    }
+    store_spectrum_rows<R, P>(buf, (C*)a.S, a.g.rows, a.g.ng, rho, t, valid);
 }
 template <typename R, int P>
 PIDE_FFT_KERNEL(R, P) k_row_forward(const __grid_constant__ FwdArgs<R> a) { row_forward_body<R, P>(a, Cfg<R, P>::UNITS); }
@@ -959,29 +984,7 @@ __device__ __forceinline__ void dst_row_body(const DstRowArgs<R>& a, int upb) {
     // positions outside [N/2 + 2, 3N/2] are zero, so first-stage inputs
     // j + r P/16 with r in {0..3, 13..15} always are (P >= 32)
     block_fft<R, -1, P>(buf, t, tw, SmemLoad<R, (P >= 32 ? 0xE00Fu : 0u)>{buf}, SmemStore<R>{buf});
-    {
-        constexpr int Gc = cgroup<R>();
-        C* S = (C*)a.S;
-        const int rows = a.g.rows;
-        const int rho = m2 + N / 2 + 1;
-        for (int g = t; g < a.g.ng; g += NT) {
-#pragma unroll
-            for (int c = 0; c < Gc; ++c) {
-                const int k = g * Gc + c;
-                C xa = mk<R>(0, 0), xb = mk<R>(0, 0);
-                if (k <= P / 2) {
-                    const C zk = buf[padi(k)];
-                    const C zm = buf[padi((P - k) & (P - 1))];
-                    xa = mk<R>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
-                    xb = mk<R>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
-                }
-                if (valid) {
-                    S[((size_t)g * rows + rho) * Gc + c] = xa;
-                    S[((size_t)g * rows + rho + 1) * Gc + c] = xb;
-                }
-            }
-        }
-    }
+    store_spectrum_rows<R, P>(buf, (C*)a.S, a.g.rows, a.g.ng, m2 + N / 2 + 1, t, valid);
 }
 template <typename R, int P>
 PIDE_FFT_KERNEL(R, P) k_dst_row(const __grid_constant__ DstRowArgs<R> a) { dst_row_body<R, P>(a, Cfg<R, P>::UNITS); }
