@@ -232,8 +232,8 @@ __device__ __forceinline__ void fft_stage(int t, const cpx<R>* __restrict__ tw, 
     constexpr int STRIDE = P / RAD;
     constexpr int TWS = P / (NS * RAD);
     cpx<R> v[16];
-#pragma unroll
     constexpr unsigned ZM = (RAD == 16 && NS == 1) ? zero_mask_of<L>::value : 0u;
+#pragma unroll
     for (int b = 0; b < NB; ++b) {
         const int j = t + b * NT;
         if constexpr (is_smem_io<L>::value && STRIDE % 16 == 0) {

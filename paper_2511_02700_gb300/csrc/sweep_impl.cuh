@@ -291,10 +291,10 @@ __device__ __forceinline__ void col_body(const ColArgs<R>& a, int upb) {
     const int g = k1 / Gc, c = k1 - g * Gc;
     C* col = (C*)a.S + (size_t)g * a.g.rows * Gc + c;
     const C* tw = (const C*)a.tw;
-    const C* wh = (const C*)a.Wh + (size_t)g * P * Gc + c;
-    // the four blocks of a column group each bring a quarter of the group's
-    // weight spectrum into L2 while the forward transform runs
-    if (t == 0 && valid) l2_prefetch((const C*)a.Wh + ((size_t)g * P + (size_t)c * (P / Gc)) * Gc, (size_t)P * sizeof(C));
+    // the weight spectrum is column-major (column k1 at Wh + k1 P): the block's
+    // column is contiguous, and comes into L2 while the forward transform runs
+    const C* wh = (const C*)a.Wh + (size_t)k1 * P;
+    if (t == 0 && valid) l2_prefetch(wh, (size_t)P * sizeof(C));
     // look ahead: the column a block resident one wave later (MINB blocks on each
     // of 152 SMs) will transform; its group's input rows come into L2 now, a
     // quarter from each of the group's blocks
@@ -307,7 +307,7 @@ __device__ __forceinline__ void col_body(const ColArgs<R>& a, int upb) {
         }
     }
     auto store_mul = [&](int k2, C v) {
-        const C w = valid ? __ldg(&wh[(size_t)k2 * Gc]) : mk<R>(0, 0);
+        const C w = valid ? __ldg(&wh[k2]) : mk<R>(0, 0);
         buf[padi(k2)] = cmul(v, w);
     };
     if constexpr (INCR) {
@@ -1252,11 +1252,11 @@ PIDE_FFT_KERNEL(R, P) k_ps_col(void* Sv, const void* Whv, int rows, int nin, int
     constexpr int Gc = cgroup<R>();
     const int g = k1 / Gc, c = k1 - g * Gc;
     C* col = (C*)Sv + (size_t)g * rows * Gc + c;
-    const C* wh = (const C*)Whv + (size_t)g * P * Gc + c;
+    const C* wh = (const C*)Whv + (size_t)k1 * P;      // column-major weight spectrum
     const C* tw = (const C*)twv;
     auto load = [&](int rho) -> C { return (valid && rho < nin) ? col[(size_t)rho * Gc] : mk<R>(0, 0); };
     auto store_mul = [&](int k2, C v) {
-        const C w = valid ? __ldg(&wh[(size_t)k2 * Gc]) : mk<R>(0, 0);
+        const C w = valid ? __ldg(&wh[k2]) : mk<R>(0, 0);
         buf[padi(k2)] = cmul(v, w);
     };
     block_fft<R, -1, P>(buf, t, tw, load, store_mul);
@@ -1327,8 +1327,6 @@ PIDE_FFT_KERNEL(double, P) k_weights_col(Geometry g, const double2* Sd, cpx<RO>*
         // rows >= N of the zero-padded Omega are zero
         return (valid && i < N) ? Sd[((size_t)gd * P + i) * Gd + cd] : mk<double>(0, 0);
     };
-    constexpr int Go = cgroup<RO>();
-    const int go = k1 / Go, co = k1 - go * Go;
     const double inv = 1.0 / ((double)P * (double)P);
     auto chat = [&](int k) -> double2 {
         const double2 a1 = twd[k], a2 = twd[(2 * k) & (P - 1)], a3 = twd[(3 * k) & (P - 1)];
@@ -1336,9 +1334,10 @@ PIDE_FFT_KERNEL(double, P) k_weights_col(Geometry g, const double2* Sd, cpx<RO>*
                           0.5625 * a1.y + 0.5625 * a2.y - 0.0625 * a3.y);
     };
     const double2 c1 = valid ? chat(k1) : mk<double>(0, 0);
+    // column-major: column k1 at k1 P, contiguous for the column pass that reads it
     auto store = [&](int k2, double2 w) {
         if (!valid) return;
-        const size_t o = ((size_t)go * P + k2) * Go + co;
+        const size_t o = (size_t)k1 * P + k2;
         Wh[o] = mk<RO>((RO)(w.x * inv), (RO)(-w.y * inv));
         if (Whi) {
             const double2 wc = cmul(cmul(w, c1), chat(k2));
