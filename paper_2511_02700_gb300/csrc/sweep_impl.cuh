@@ -106,6 +106,14 @@ __device__ __forceinline__ float2 shfl_xor_state(float2 y, int o) {
     return make_float2(__shfl_xor_sync(0xffffffffu, y.x, o), __shfl_xor_sync(0xffffffffu, y.y, o));
 }
 __device__ __forceinline__ double shfl_xor_state(double y, int o) { return __shfl_xor_sync(0xffffffffu, y, o); }
+__device__ __forceinline__ float2 shfl_up_state(float2 y, int o) {
+    return make_float2(__shfl_up_sync(0xffffffffu, y.x, o), __shfl_up_sync(0xffffffffu, y.y, o));
+}
+__device__ __forceinline__ double shfl_up_state(double y, int o) { return __shfl_up_sync(0xffffffffu, y, o); }
+__device__ __forceinline__ float2 shfl_down_state(float2 y, int o) {
+    return make_float2(__shfl_down_sync(0xffffffffu, y.x, o), __shfl_down_sync(0xffffffffu, y.y, o));
+}
+__device__ __forceinline__ double shfl_down_state(double y, int o) { return __shfl_down_sync(0xffffffffu, y, o); }
 
 template <typename K>
 void set_smem(K kernel, size_t bytes) {
@@ -452,6 +460,139 @@ __device__ __forceinline__ void incr_epilogue(const InvArgs<R>& a, St<R>* BYv, c
     }
 }
 
+// Epilogue of the full inverse row pass (INV_FULL, INV_OUT) in coalesced order:
+// outputs m1 = t + NT b of rows m2 and m2 + 1, their C2R values zz in buf.
+// INV_OUT writes zz.  INV_FULL sets B_w Y (= B_w V^{n-1} + zz after a difference
+// sweep, else zz) and forms the step's first residual with the full operator,
+//     W - Y + h_t theta (B_w Y - r_w Y) + h_t theta D Y,
+// as the odd extension for the row DST.  Each column's four state rows
+// m2 - 1 .. m2 + 2 are loaded once; the stencil's neighbours m1 -+ 1 (the
+// states of rows m2, m2 + 1 and the vertical differences of the mixed term)
+// come from the adjacent lanes, with direct loads at the warp edges.
+template <typename R, int P>
+__device__ __forceinline__ void full_epilogue(const InvArgs<R>& a, St<R>* BYv, cpx<R>* buf, int t, int m2,
+                                              bool valid, bool hasb, bool do_resid) {
+    using C = cpx<R>;
+    using S_ = St<R>;
+    constexpr int NT = P / 16, N = P / 2, NB = N / NT;
+    constexpr bool SHFL = NT >= 32;
+    constexpr int EB = 1;             // outputs whose loads go out together
+    const int ld = a.g.ldS;
+    const int lane = threadIdx.x & 31;
+    const S_ zero = st_from_r<S_, R>(R(0));
+    const bool full = a.mode == INV_FULL;
+    const bool stencil = full && do_resid;
+    const S_* Y = a.Y;
+    // the column at m1 of rows m2 - 1 .. m2 + 2 (rows beyond the grid read as zero)
+    auto column = [&](int m1, S_& ym, S_& y0, S_& y1, S_& y2) {
+        const size_t idx = (size_t)m2 * ld + m1;
+        ym = valid ? Y[idx - ld] : zero;
+        y0 = valid ? Y[idx] : zero;
+        y1 = valid ? Y[idx + ld] : zero;
+        y2 = hasb ? Y[idx + 2 * ld] : zero;
+    };
+#pragma unroll
+    for (int b0 = 0; b0 < NB; b0 += EB) {
+        S_ ym[EB], y0[EB], y1[EB], y2[EB], w0[EB], w1[EB], v0[EB], v1[EB];
+#pragma unroll
+        for (int i = 0; i < EB; ++i) {
+            const int m1 = t + NT * (b0 + i);
+            const size_t idx = (size_t)m2 * ld + m1;
+            ym[i] = y0[i] = y1[i] = y2[i] = w0[i] = w1[i] = v0[i] = v1[i] = zero;
+            if (stencil) {
+                column(m1, ym[i], y0[i], y1[i], y2[i]);
+                w0[i] = valid ? a.W[idx] : zero;
+                w1[i] = hasb ? a.W[idx + ld] : zero;
+            }
+            if (full && a.BV) {
+                v0[i] = valid ? a.BV[idx] : zero;
+                v1[i] = hasb ? a.BV[idx + ld] : zero;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < EB; ++i) {
+            const int m1 = t + NT * (b0 + i);
+            // the neighbours' states of rows m2, m2 + 1 and vertical differences
+            // f0 = Y[m2 + 1] - Y[m2 - 1], f1 = Y[m2 + 2] - Y[m2]
+            S_ aL = zero, aR = zero, bL = zero, bR = zero;
+            R f0L = 0, f0R = 0, f1L = 0, f1R = 0;
+            if (stencil) {
+                const R f0 = st_diff(y1[i], ym[i]), f1 = st_diff(y2[i], y0[i]);
+                if constexpr (SHFL) {
+                    f0L = __shfl_up_sync(0xffffffffu, f0, 1);
+                    f0R = __shfl_down_sync(0xffffffffu, f0, 1);
+                    f1L = __shfl_up_sync(0xffffffffu, f1, 1);
+                    f1R = __shfl_down_sync(0xffffffffu, f1, 1);
+                    aL = shfl_up_state(y0[i], 1);
+                    aR = shfl_down_state(y0[i], 1);
+                    bL = shfl_up_state(y1[i], 1);
+                    bR = shfl_down_state(y1[i], 1);
+                    if (lane == 0 && m1 >= 1) {
+                        S_ q0, q1, q2, q3;
+                        column(m1 - 1, q0, q1, q2, q3);
+                        f0L = st_diff(q2, q0);
+                        f1L = st_diff(q3, q1);
+                        aL = q1;
+                        bL = q2;
+                    }
+                    if (lane == 31) {
+                        S_ q0, q1, q2, q3;
+                        column(m1 + 1, q0, q1, q2, q3);
+                        f0R = st_diff(q2, q0);
+                        f1R = st_diff(q3, q1);
+                        aR = q1;
+                        bR = q2;
+                    }
+                } else if (m1 >= 1) {
+                    S_ q0, q1, q2, q3;
+                    column(m1 - 1, q0, q1, q2, q3);
+                    f0L = st_diff(q2, q0);
+                    f1L = st_diff(q3, q1);
+                    aL = q1;
+                    bL = q2;
+                    column(m1 + 1, q0, q1, q2, q3);
+                    f0R = st_diff(q2, q0);
+                    f1R = st_diff(q3, q1);
+                    aR = q1;
+                    bR = q2;
+                }
+            }
+            if (m1 < 1) continue;
+            const C zz = buf[padi(m1)];
+            R rr0 = R(0), rr1 = R(0);
+            if (valid) {
+                const size_t idx = (size_t)m2 * ld + m1;
+                if (!full) {
+                    a.out[idx] = (double)zz.x;
+                    if (hasb) a.out[idx + ld] = (double)zz.y;
+                } else {
+                    BYv[idx] = a.BV ? st_add(v0[i], zz.x) : st_from_r<S_, R>(zz.x);
+                    if (hasb) BYv[idx + ld] = a.BV ? st_add(v1[i], zz.y) : st_from_r<S_, R>(zz.y);
+                    if (do_resid) {
+                        // D Y as in diff_state: d11 dxx + d22 dyy + d12 dxy
+                        const R dy0 = a.d11 * (st_diff(aR, y0[i]) + st_diff(aL, y0[i])) +
+                                      a.d22 * (st_diff(y1[i], y0[i]) + st_diff(ym[i], y0[i])) + a.d12 * (f0R - f0L);
+                        const R jb0 = a.BV ? jump_gen(v0[i], y0[i], a.rw, a.rw_lo) + zz.x
+                                           : zz.x - a.rw * st_r(y0[i]);
+                        rr0 = st_diff(w0[i], y0[i]) + a.htt * jb0 + a.htt * dy0;
+                        if (hasb) {
+                            const R dy1 = a.d11 * (st_diff(bR, y1[i]) + st_diff(bL, y1[i])) +
+                                          a.d22 * (st_diff(y2[i], y1[i]) + st_diff(y0[i], y1[i])) + a.d12 * (f1R - f1L);
+                            const R jb1 = a.BV ? jump_gen(v1[i], y1[i], a.rw, a.rw_lo) + zz.y
+                                               : zz.y - a.rw * st_r(y1[i]);
+                            rr1 = st_diff(w1[i], y1[i]) + a.htt * jb1 + a.htt * dy1;
+                        }
+                    }
+                }
+            }
+            if (do_resid) {
+                buf[padi(m1)] = mk<R>(rr0, rr1);
+                buf[padi(P - m1)] = mk<R>(-rr0, -rr1);
+            }
+        }
+    }
+}
+
 // INCR: compiled for the increment mode only (INV_INCR), else for INV_FULL / INV_OUT,
 // so the two epilogues do not share one register allocation
 template <typename R, int P, bool INCR>
@@ -503,51 +644,6 @@ __device__ __forceinline__ void row_inverse_body(const InvArgs<R>& a, int upb) {
         if (hi) { xa.y = -xa.y; xb.y = -xb.y; }
         return mk<R>(xa.x - xb.y, xa.y + xb.x);
     };
-    auto epilogue = [&](int m1, C zz) {
-        if (m1 == 0) {
-            if (do_resid) {
-                buf[padi(0)] = mk<R>(0, 0);
-                buf[padi(N)] = mk<R>(0, 0);
-            }
-            return;
-        }
-        if (m1 >= N) return;
-        R rr[2] = {R(0), R(0)};
-        if (valid) {
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                if (half == 1 && !hasb) break;
-                const int row = m2 + half;
-                const R zv = half == 0 ? zz.x : zz.y;
-                const size_t idx = (size_t)row * ld + m1;
-                if (a.mode == INV_OUT) {
-                    a.out[idx] = (double)zv;
-                } else if (a.mode == INV_FULL) {
-                    if (a.BV) {
-                        // the sweep transformed Y - V^{n-1}: B_w Y = B_w V^{n-1} + zv
-                        const S_ bv = a.BV[idx];
-                        BYv[idx] = st_add(bv, zv);
-                        if (do_resid) {
-                            const S_ y = a.Y[idx];
-                            rr[half] = st_diff(a.W[idx], y) + a.htt * (jump_gen(bv, y, a.rw, a.rw_lo) + zv)
-                                       + a.htt * diff_state(a.Y, idx, ld, a.d11, a.d22, a.d12);
-                        }
-                    } else {
-                        BYv[idx] = st_from_r<S_, R>(zv);
-                        if (do_resid) {
-                            const S_ y = a.Y[idx];
-                            rr[half] = st_diff(a.W[idx], y) + a.htt * zv - a.htt * a.rw * st_r(y)
-                                       + a.htt * diff_state(a.Y, idx, ld, a.d11, a.d22, a.d12);
-                        }
-                    }
-                }
-            }
-        }
-        if (do_resid) {
-            buf[padi(m1)] = mk<R>(rr[0], rr[1]);
-            buf[padi(P - m1)] = mk<R>(-rr[0], -rr[1]);
-        }
-    };
     if constexpr (INCR) {
         // the C2R into buf in natural order, then the epilogue in coalesced order
         // (each thread reads the C2R values at its own m1 < N and writes the
@@ -561,7 +657,13 @@ __device__ __forceinline__ void row_inverse_body(const InvArgs<R>& a, int upb) {
         }
         __syncthreads();
     } else {
-        block_fft<R, +1, P, false>(buf, t, tw, load, epilogue);
+        block_fft<R, +1, P, false>(buf, t, tw, load, SmemStore<R>{buf});
+        full_epilogue<R, P>(a, BYv, buf, t, m2, valid, hasb, do_resid);
+        if (do_resid && t == 0) {
+            buf[padi(0)] = mk<R>(0, 0);
+            buf[padi(N)] = mk<R>(0, 0);
+        }
+        __syncthreads();
     }
     if (!do_resid) return;   // uniform across the block
     constexpr int GE = rgroup<R>();
