@@ -1402,7 +1402,7 @@ size_t group_scratch_bytes(int K, int n_steps) {
 //     steps -- k_step_select copies the step's blob into the argument arrays,
 //     then W and Y^{n,0} (prep), the difference sweep, the reset of the
 //     per-job stopping state, an inner while-node over the fixed-point
-//     iterations (column DST, row DST with the eq. 3.25 maxima, the per-job
+//     iterations (column solve, row DST with the eq. 3.25 maxima, the per-job
 //     check that ends the inner loop when no job iterates any more, column
 //     pass and inverse row pass of the jobs still iterating) and
 //     k_step_tally, which folds the counts into per-job statistics and ends

@@ -1098,7 +1098,7 @@ PIDE_FFT_JOBS_KERNEL(R, P) k_dst_row_jobs(const DstRowArgs<R>* __restrict__ arr,
 
 // ---------------------------------------------------------------------------
 // row DST-I of an FP64 interior field into the DST buffer E: the same
-// transform k_row_inverse applies to the residual before the column DST, here
+// transform k_row_inverse applies to the residual before the column solve, here
 // for a residual handed in by the caller (pide2d_iteration_probe)
 // ---------------------------------------------------------------------------
 template <typename R, int P>

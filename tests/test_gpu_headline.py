@@ -6,7 +6,7 @@ through the C ABI.
   the region of interest (S_i <= 3K), element by element.
 * One fixed-point iteration of the increment loop (pide2d_iteration_probe):
   at N = 4096, the 8192-point FP32-bulk kernels and launch shapes of the
-  benchmark's timed loop (column DST pass, row DST pass with the R2C rows of
+  benchmark's timed loop (column solve pass, row DST pass with the R2C rows of
   the increment, column pass with the increment weight spectrum, inverse row
   pass), and at N = 256 in FP64.  The increment is checked at every interior
   node against the oracle's sine-basis solve, B_w of the increment at every
