@@ -2090,7 +2090,23 @@ struct pide2d_price {
     double par[9];
     std::string err;
     bool broken = false;
+    // instantiated BiCGSTAB graphs, one per system (c0, c1), and their capture stream
+    struct BicgGraph {
+        double c0, c1;
+        cudaGraph_t g;
+        cudaGraphExec_t ex;
+    };
+    std::vector<BicgGraph> bicg;
+    cudaStream_t cap = nullptr;
     template <typename T> T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
+    ~pide2d_price() {
+        if (!bicg.empty()) cudaStreamSynchronize(stream);
+        for (auto& b : bicg) {
+            cudaGraphExecDestroy(b.ex);
+            cudaGraphDestroy(b.g);
+        }
+        if (cap) cudaStreamDestroy(cap);
+    }
 };
 
 namespace {
@@ -2332,7 +2348,7 @@ static size_t ps_field_bytes(int nx1) { return align256((size_t)nx1 * nx1 * 8); 
 
 static size_t ps_loop_bytes(int nx1) {
     return (size_t)F_COUNT * ps_field_bytes(nx1) + 3 * align256((size_t)nx1 * 3 * 8) + 2 * align256((size_t)nx1 * 4) +
-           2 * align256((size_t)nx1 * 4 * 8) + align256((size_t)ps_reduction_blocks() * 3 * 8) + 256;
+           2 * align256((size_t)nx1 * 4 * 8) + align256((size_t)ps_reduction_blocks() * 3 * 8) + 256 + 256;
 }
 
 static pide2d_status price_solve(pide2d_price* H, const pide2d_contract* c, double theta, int n_steps, double tol,
@@ -2357,6 +2373,7 @@ static pide2d_status price_solve(pide2d_price* H, const pide2d_contract* c, doub
     double* dw2 = reinterpret_cast<double*>(take((size_t)n1 * 4 * 8));
     double* part = reinterpret_cast<double*>(take((size_t)ps_reduction_blocks() * 3 * 8));
     double* res = reinterpret_cast<double*>(q);
+    PsBicg* bst = reinterpret_cast<PsBicg*>(q + 256);
     const std::vector<double>& x = H->x;
     // central differences on the non-uniform grid (Sec. 3.2.1); row 0 zero, last row:
     // second difference zero, first difference backward
@@ -2405,70 +2422,47 @@ static pide2d_status price_solve(pide2d_price* H, const pide2d_contract* c, doub
     auto apply_jump = [&](const double* V, double* out) -> pide2d_status {
         return H->precision == PIDE2D_FP64 ? price_apply<double>(H, V, out) : price_apply<float>(H, V, out);
     };
-    auto dots = [&](int nd, PsDots dp, double* out) -> pide2d_status {
-        PIDE_PCUDA(launch_ps_dots(n, nd, dp, part, res, s));
-        PIDE_PCUDA(cudaMemcpyAsync(out, res, nd * 8, cudaMemcpyDeviceToHost, s));
-        PIDE_PCUDA(cudaStreamSynchronize(s));
-        return PIDE2D_OK;
-    };
-    // BiCGSTAB with Jacobi preconditioning for (c0 I - c1 D) X = B, X holding the start
+    // BiCGSTAB with Jacobi preconditioning for (c0 I - c1 D) X = B, X holding the
+    // start: one graph launch (set-up and a while-node over the iterations, the
+    // scalars on the device), then one read of the solver state
+    constexpr int kBicgMaxIt = 20000;
+    constexpr size_t kBicgGraphs = 8;
     auto bicgstab = [&](double c0, double c1, const double* Bv, double* X, int* its) -> pide2d_status {
-        double* r = fld(F_R);
-        double* rh = fld(F_RH);
-        double* p = fld(F_P);
-        double* v = fld(F_VV);
-        double* y = fld(F_YY);
-        double* sv = fld(F_S);
-        double* z = fld(F_ZZ);
-        double* t = fld(F_T);
-        const double* dinv = fld(F_DINV);
-        PIDE_PCUDA(launch_ps_diff(d, X, c0, -c1, nullptr, 0.0, r, s));
-        PIDE_PCUDA(launch_ps_axpy(n, 1.0, Bv, -1.0, r, 0.0, nullptr, nullptr, r, s));
-        PIDE_PCUDA(cudaMemcpyAsync(rh, r, n * 8, cudaMemcpyDeviceToDevice, s));
-        double h2[2];
-        pide2d_status st = dots(2, PsDots{{Bv, r, nullptr}, {Bv, r, nullptr}}, h2);
-        if (st != PIDE2D_OK) return st;
-        const double bn = std::sqrt(h2[0]);
-        double rn = std::sqrt(h2[1]);
-        const double lim = 1e-13 * (bn > 0.0 ? bn : 1.0);
-        double rho = 1.0, alpha = 1.0, omega = 1.0, rho_new = h2[1];
-        *its = 0;
-        for (int it = 0; it < 20000 && rn > lim; ++it) {
-            if (it == 0) {
-                PIDE_PCUDA(cudaMemcpyAsync(p, r, n * 8, cudaMemcpyDeviceToDevice, s));
-            } else {
-                const double beta = (rho_new / rho) * (alpha / omega);
-                PIDE_PCUDA(launch_ps_axpy(n, 1.0, r, beta, p, -beta * omega, v, nullptr, p, s));
+        cudaGraphExec_t ex = nullptr;
+        for (const auto& bg : H->bicg)
+            if (bg.c0 == c0 && bg.c1 == c1) ex = bg.ex;
+        if (!ex) {
+            if (!H->cap) PIDE_PCUDA(cudaStreamCreateWithFlags(&H->cap, cudaStreamNonBlocking));
+            cudaGraph_t g = nullptr;
+            PIDE_PCUDA(cudaGraphCreate(&g, 0));
+            const PsBicgArgs ba{d, n, c0, c1, Bv, X, fld(F_R), fld(F_RH), fld(F_P), fld(F_VV), fld(F_YY), fld(F_S),
+                                fld(F_ZZ), fld(F_T), fld(F_DINV), part, res, bst, kBicgMaxIt};
+            const char* where = "";
+            cudaError_t e = record_ps_bicg(g, H->cap, ba, &where);
+            if (e == cudaSuccess) {
+                e = cudaGraphInstantiate(&ex, g, 0);
+                where = "cudaGraphInstantiate";
             }
-            PIDE_PCUDA(launch_ps_axpy(n, 1.0, p, 0.0, nullptr, 0.0, nullptr, dinv, y, s));
-            PIDE_PCUDA(launch_ps_diff(d, y, c0, -c1, nullptr, 0.0, v, s));
-            double rv;
-            st = dots(1, PsDots{{rh, nullptr, nullptr}, {v, nullptr, nullptr}}, &rv);
-            if (st != PIDE2D_OK) return st;
-            alpha = rho_new / rv;
-            PIDE_PCUDA(launch_ps_axpy(n, 1.0, r, -alpha, v, 0.0, nullptr, nullptr, sv, s));
-            PIDE_PCUDA(launch_ps_axpy(n, 1.0, sv, 0.0, nullptr, 0.0, nullptr, dinv, z, s));
-            PIDE_PCUDA(launch_ps_diff(d, z, c0, -c1, nullptr, 0.0, t, s));
-            double ts3[3];
-            st = dots(3, PsDots{{t, t, sv}, {sv, t, sv}}, ts3);
-            if (st != PIDE2D_OK) return st;
-            *its = it + 1;
-            if (std::sqrt(ts3[2]) <= lim) {
-                PIDE_PCUDA(launch_ps_axpy(n, 1.0, X, alpha, y, 0.0, nullptr, nullptr, X, s));
-                rn = std::sqrt(ts3[2]);
-                break;
+            if (e != cudaSuccess) {
+                cudaGraphDestroy(g);
+                H->err = std::string("price-space BiCGSTAB graph: ") + where + ": " + cudaGetErrorString(e);
+                H->broken = true;
+                return PIDE2D_ERR_CUDA;
             }
-            omega = ts3[0] / ts3[1];
-            PIDE_PCUDA(launch_ps_axpy(n, 1.0, X, alpha, y, omega, z, nullptr, X, s));
-            PIDE_PCUDA(launch_ps_axpy(n, 1.0, sv, -omega, t, 0.0, nullptr, nullptr, r, s));
-            rho = rho_new;
-            double rr2[2];
-            st = dots(2, PsDots{{r, rh, nullptr}, {r, r, nullptr}}, rr2);
-            if (st != PIDE2D_OK) return st;
-            rn = std::sqrt(rr2[0]);
-            rho_new = rr2[1];
+            if (H->bicg.size() >= kBicgGraphs) {
+                PIDE_PCUDA(cudaStreamSynchronize(s));       // the oldest may still be queued
+                cudaGraphExecDestroy(H->bicg.front().ex);
+                cudaGraphDestroy(H->bicg.front().g);
+                H->bicg.erase(H->bicg.begin());
+            }
+            H->bicg.push_back({c0, c1, g, ex});
         }
-        if (rn > lim) {
+        PIDE_PCUDA(cudaGraphLaunch(ex, s));
+        PsBicg hb{};
+        PIDE_PCUDA(cudaMemcpyAsync(&hb, bst, sizeof hb, cudaMemcpyDeviceToHost, s));
+        PIDE_PCUDA(cudaStreamSynchronize(s));
+        *its = hb.it;
+        if (!(hb.rn <= hb.lim)) {
             H->err = "price-space BiCGSTAB did not reach its tolerance";
             return PIDE2D_ERR_NOT_CONVERGED;
         }

@@ -206,6 +206,28 @@ struct PsDots {
     const double* y[3];
 };
 cudaError_t launch_ps_dots(size_t n, int nd, const PsDots& dp, double* part, double* res, cudaStream_t s);
+// one Jacobi-preconditioned BiCGSTAB solve of (c0 I - c1 D) X = B with its
+// scalars in device memory: record_ps_bicg builds it as a CUDA graph (set-up,
+// then a while-node over the iterations), so a solve is one graph launch
+struct PsBicg {
+    double rho, rho_new, alpha, omega;
+    double rn, lim;          // the residual norm and the stopping level 1e-13 |B|
+    int it, done;            // iterations done; 1 once the half-step residual met lim
+};
+struct PsBicgArgs {
+    PsDiff d;
+    size_t n;
+    double c0, c1;
+    const double* B;
+    double* X;               // the start in, the solution out
+    double *r, *rh, *p, *v, *y, *s, *z, *t;
+    const double* dinv;      // the Jacobi preconditioner
+    double* part;            // ps_reduction_blocks() x 3 partial sums
+    double* res;             // 3 doubles
+    PsBicg* st;
+    int maxit;
+};
+cudaError_t record_ps_bicg(cudaGraph_t g, cudaStream_t cap, const PsBicgArgs& a, const char** where);
 cudaError_t launch_ps_maxrel(size_t n, const double* a, const double* b, double* part, double* res, cudaStream_t s);
 cudaError_t launch_ps_sl(int n1, const int* s1, const double* w1, const int* s2, const double* w2, const double* Z,
                          double* W, cudaStream_t s);

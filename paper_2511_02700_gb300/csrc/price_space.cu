@@ -3,6 +3,8 @@
 // extrapolation below y_out is encoded in the tables as two taps).
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "internal.h"
 
 namespace pide {
@@ -181,6 +183,179 @@ cudaError_t launch_ps_dots(size_t n, int nd, const PsDots& dp, double* part, dou
     k_ps_finish<<<1, 256, 0, s>>>(part, kPsRedBlocks, nd, 0, res);
     return cudaGetLastError();
 }
+// ---------------------------------------------------------------------------
+// BiCGSTAB with the scalars on the device.  The vector updates read alpha,
+// beta and omega from PsBicg; each scalar step is one thread; the loop is a
+// CUDA-graph while-node whose condition the scalar steps set (no host round
+// trip per iteration).  Same recurrences and reductions as a host-driven loop.
+// ---------------------------------------------------------------------------
+__global__ void k_bicg_init(const double* __restrict__ res, PsBicg* __restrict__ st, int maxit,
+                            unsigned long long hnd) {
+    PsBicg q{};
+    const double bn = sqrt(res[0]);                   // res: <B, B>, <r, r>
+    q.lim = 1e-13 * (bn > 0.0 ? bn : 1.0);
+    q.rn = sqrt(res[1]);
+    q.rho = 1.0;
+    q.alpha = 1.0;
+    q.omega = 1.0;
+    q.rho_new = res[1];
+    *st = q;
+    cudaGraphSetConditional((cudaGraphConditionalHandle)hnd, (q.rn > q.lim && maxit > 0) ? 1u : 0u);
+}
+// p = r (first iteration) or r + beta p - beta omega v, beta = (rho_new / rho)(alpha / omega)
+__global__ void k_bicg_p(size_t n, const PsBicg* __restrict__ st, const double* __restrict__ r, double* p,
+                         const double* __restrict__ v) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const PsBicg q = *st;
+    if (q.it == 0) {
+        p[i] = r[i];
+    } else {
+        const double beta = (q.rho_new / q.rho) * (q.alpha / q.omega);
+        p[i] = 1.0 * r[i] + beta * p[i] + (-beta * q.omega) * v[i];
+    }
+}
+__global__ void k_bicg_alpha(const double* __restrict__ res, PsBicg* __restrict__ st) {
+    st->alpha = st->rho_new / res[0];                 // res: <rh, v>
+}
+// s = r - alpha v
+__global__ void k_bicg_s(size_t n, const PsBicg* __restrict__ st, const double* __restrict__ r,
+                         const double* __restrict__ v, double* __restrict__ s) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    s[i] = 1.0 * r[i] + (-st->alpha) * v[i];
+}
+// res: <t, s>, <t, t>, <s, s>: converged on s (the loop ends), else omega
+__global__ void k_bicg_omega(const double* __restrict__ res, PsBicg* __restrict__ st, unsigned long long hnd) {
+    PsBicg q = *st;
+    q.it += 1;
+    const double sn = sqrt(res[2]);
+    if (sn <= q.lim) {
+        q.done = 1;
+        q.rn = sn;
+        cudaGraphSetConditional((cudaGraphConditionalHandle)hnd, 0u);
+    } else {
+        q.omega = res[0] / res[1];
+    }
+    *st = q;
+}
+// X += alpha y (+ omega z), r = s - omega t (unless converged on s)
+__global__ void k_bicg_xr(size_t n, const PsBicg* __restrict__ st, double* X, const double* __restrict__ y,
+                          const double* __restrict__ z, const double* __restrict__ s, const double* __restrict__ t,
+                          double* __restrict__ r) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const PsBicg q = *st;
+    if (q.done) {
+        X[i] = 1.0 * X[i] + q.alpha * y[i];
+    } else {
+        X[i] = 1.0 * X[i] + q.alpha * y[i] + q.omega * z[i];
+        r[i] = 1.0 * s[i] + (-q.omega) * t[i];
+    }
+}
+// res: <r, r>, <rh, r>: the residual norm, the next rho and the loop condition
+__global__ void k_bicg_rho(const double* __restrict__ res, PsBicg* __restrict__ st, int maxit,
+                           unsigned long long hnd) {
+    PsBicg q = *st;
+    if (q.done) return;                               // the condition was cleared at convergence on s
+    q.rho = q.rho_new;
+    q.rn = sqrt(res[0]);
+    q.rho_new = res[1];
+    *st = q;
+    cudaGraphSetConditional((cudaGraphConditionalHandle)hnd, (q.rn > q.lim && q.it < maxit) ? 1u : 0u);
+}
+
+cudaError_t record_ps_bicg(cudaGraph_t g, cudaStream_t cs, const PsBicgArgs& a, const char** where) {
+    cudaError_t e = cudaSuccess;
+#define PS_GTRY(call)                \
+    do {                             \
+        e = (call);                  \
+        if (e != cudaSuccess) {      \
+            *where = #call;          \
+            return e;                \
+        }                            \
+    } while (0)
+    const size_t n = a.n;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    cudaGraphConditionalHandle hnd;
+    PS_GTRY(cudaGraphConditionalHandleCreate(&hnd, g, 1, cudaGraphCondAssignDefault));
+    // set-up: r = B - (c0 X - c1 D X), rh = r, <B, B>, <r, r>, the stopping level
+    PS_GTRY(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    {
+        cudaError_t x = launch_ps_diff(a.d, a.X, a.c0, -a.c1, nullptr, 0.0, a.r, cs);
+        if (x == cudaSuccess) x = launch_ps_axpy(n, 1.0, a.B, -1.0, a.r, 0.0, nullptr, nullptr, a.r, cs);
+        if (x == cudaSuccess) x = cudaMemcpyAsync(a.rh, a.r, n * 8, cudaMemcpyDeviceToDevice, cs);
+        if (x == cudaSuccess) x = launch_ps_dots(n, 2, PsDots{{a.B, a.r, nullptr}, {a.B, a.r, nullptr}}, a.part, a.res, cs);
+        if (x == cudaSuccess) {
+            k_bicg_init<<<1, 1, 0, cs>>>(a.res, a.st, a.maxit, (unsigned long long)hnd);
+            x = cudaGetLastError();
+        }
+        cudaGraph_t got = nullptr;
+        const cudaError_t x2 = cudaStreamEndCapture(cs, &got);
+        if (x != cudaSuccess) { *where = "BiCGSTAB set-up launches"; return x; }
+        if (x2 != cudaSuccess) { *where = "cudaStreamEndCapture(set-up)"; return x2; }
+    }
+    // the set-up is a chain: its last node has no dependents
+    size_t nn = 0;
+    PS_GTRY(cudaGraphGetNodes(g, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    PS_GTRY(cudaGraphGetNodes(g, nodes.data(), &nn));
+    std::vector<cudaGraphNode_t> leaves;
+    for (auto nd : nodes) {
+        size_t nd_out = 0;
+        PS_GTRY(cudaGraphNodeGetDependentNodes(nd, nullptr, nullptr, &nd_out));
+        if (nd_out == 0) leaves.push_back(nd);
+    }
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hnd;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t loop = nullptr;
+    PS_GTRY(cudaGraphAddNode(&loop, g, leaves.data(), nullptr, leaves.size(), &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    // one BiCGSTAB iteration
+    PS_GTRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    {
+        cudaError_t x = cudaSuccess;
+        k_bicg_p<<<nb, 256, 0, cs>>>(n, a.st, a.r, a.p, a.v);
+        x = cudaGetLastError();
+        if (x == cudaSuccess) x = launch_ps_axpy(n, 1.0, a.p, 0.0, nullptr, 0.0, nullptr, a.dinv, a.y, cs);
+        if (x == cudaSuccess) x = launch_ps_diff(a.d, a.y, a.c0, -a.c1, nullptr, 0.0, a.v, cs);
+        if (x == cudaSuccess) x = launch_ps_dots(n, 1, PsDots{{a.rh, nullptr, nullptr}, {a.v, nullptr, nullptr}}, a.part, a.res, cs);
+        if (x == cudaSuccess) {
+            k_bicg_alpha<<<1, 1, 0, cs>>>(a.res, a.st);
+            x = cudaGetLastError();
+        }
+        if (x == cudaSuccess) {
+            k_bicg_s<<<nb, 256, 0, cs>>>(n, a.st, a.r, a.v, a.s);
+            x = cudaGetLastError();
+        }
+        if (x == cudaSuccess) x = launch_ps_axpy(n, 1.0, a.s, 0.0, nullptr, 0.0, nullptr, a.dinv, a.z, cs);
+        if (x == cudaSuccess) x = launch_ps_diff(a.d, a.z, a.c0, -a.c1, nullptr, 0.0, a.t, cs);
+        if (x == cudaSuccess) x = launch_ps_dots(n, 3, PsDots{{a.t, a.t, a.s}, {a.s, a.t, a.s}}, a.part, a.res, cs);
+        if (x == cudaSuccess) {
+            k_bicg_omega<<<1, 1, 0, cs>>>(a.res, a.st, (unsigned long long)hnd);
+            x = cudaGetLastError();
+        }
+        if (x == cudaSuccess) {
+            k_bicg_xr<<<nb, 256, 0, cs>>>(n, a.st, a.X, a.y, a.z, a.s, a.t, a.r);
+            x = cudaGetLastError();
+        }
+        if (x == cudaSuccess) x = launch_ps_dots(n, 2, PsDots{{a.r, a.rh, nullptr}, {a.r, a.r, nullptr}}, a.part, a.res, cs);
+        if (x == cudaSuccess) {
+            k_bicg_rho<<<1, 1, 0, cs>>>(a.res, a.st, a.maxit, (unsigned long long)hnd);
+            x = cudaGetLastError();
+        }
+        cudaGraph_t got = nullptr;
+        const cudaError_t x2 = cudaStreamEndCapture(cs, &got);
+        if (x != cudaSuccess) { *where = "BiCGSTAB iteration launches"; return x; }
+        if (x2 != cudaSuccess) { *where = "cudaStreamEndCapture(iteration)"; return x2; }
+    }
+#undef PS_GTRY
+    return cudaSuccess;
+}
+
 cudaError_t launch_ps_maxrel(size_t n, const double* a, const double* b, double* part, double* res, cudaStream_t s) {
     k_ps_maxrel<<<kPsRedBlocks, 256, 0, s>>>(n, a, b, part);
     k_ps_finish<<<1, 256, 0, s>>>(part, kPsRedBlocks, 1, 1, res);
