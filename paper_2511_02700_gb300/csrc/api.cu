@@ -1051,6 +1051,8 @@ static pide2d_status bv0_fp64(pide2d* H) {
     const double* glp = dgl + 2 * (kGlNear + kGlFar + kGlEdge);
     PIDE_CUDA(launch_payoff<double>(gd, H->at<double>(R_E1D), H->at<double>(R_E2D), H->s_lo1, H->s_lo2, H->h,
                                     H->contract.strike, H->contract.payoff, glp, glp + kGlPay, kGlPay, V64, s));
+    // the state V^0 is the same FP64 payoff split into (hi, lo)
+    PIDE_CUDA(launch_state_from_double<float>(g, V64, g.ldS, (St<float>*)H->field(0), s));
     FwdArgs<double> fa{};
     fa.g = gd;
     fa.mode = FWD_FULL;
@@ -1145,16 +1147,17 @@ static pide2d_status do_create(pide2d* H) {
     H->freel.assign({4, 3, 2, 1});
     H->bv = 5;
     H->by = 6;
-    const double* glp = dgl + 2 * (kGlNear + kGlFar + kGlEdge);
-    PIDE_CUDA(launch_payoff<R>(g, H->at<double>(R_E1D), H->at<double>(R_E2D), H->s_lo1, H->s_lo2, H->h,
-                               H->contract.strike, H->contract.payoff, glp, glp + kGlPay, kGlPay,
-                               (St<R>*)H->field(0), s));
     if constexpr (sizeof(R) == 4) {
+        // V^0 and B_w V^0 from the FP64 payoff and an FP64 sweep
         const pide2d_status bs = bv0_fp64(H);
         if (bs != PIDE2D_OK) return bs;
         PIDE_CUDA(cudaStreamSynchronize(s));
         return PIDE2D_OK;
     }
+    const double* glp = dgl + 2 * (kGlNear + kGlFar + kGlEdge);
+    PIDE_CUDA(launch_payoff<R>(g, H->at<double>(R_E1D), H->at<double>(R_E2D), H->s_lo1, H->s_lo2, H->h,
+                               H->contract.strike, H->contract.payoff, glp, glp + kGlPay, kGlPay,
+                               (St<R>*)H->field(0), s));
     FwdArgs<R> fa{};
     fa.g = g;
     fa.mode = FWD_FULL;

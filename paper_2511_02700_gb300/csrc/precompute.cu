@@ -83,10 +83,27 @@ __device__ double levy_density(const LevyParams& L, double z1, double z2) {
     return exp(L.logpref + log_ek(L, x) - x - L.nu * log(zn) + L.b1 * z1 + L.b2 * z2);
 }
 
-// the table of log_ek: ln(e^x K_nu(x)) at x = e^{u0 + i du}, i < n
+// the table of log_ek: ln(e^x K_nu(x)) at x = e^{u0 + i du}, i < n.  One warp per
+// entry: lane l sums the trapezoidal terms k = l + 1 + 32 j of bessel_k_scaled
+// until they fall below 1e-18 of its partial sum (past the integrand's peak they
+// only decrease), then the warp adds the lane sums
 __global__ void k_ktab(double nu, double u0, double du, int n, double* tab) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) tab[i] = log(bessel_k_scaled(nu, exp(u0 + (double)i * du)));
+    const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;                               // uniform across the warp
+    const double x = exp(u0 + (double)i * du);
+    const double h = fmin(1.0 / 6.0, 0.6 / sqrt(x));
+    double s = 0.0;
+    for (int k = lane + 1; k < 4000; k += 32) {
+        const double t = k * h;
+        const double sh = sinh(0.5 * t);
+        const double term = exp(-2.0 * x * sh * sh) * cosh(nu * t);
+        s += term;
+        if (term < 1e-18 * s || term == 0.0) break;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) tab[i] = log((0.5 + s) * h);
 }
 
 // ---------------------------------------------------------------------------
@@ -412,7 +429,7 @@ cudaError_t launch_finalize(const double* partials, int nblocks, const double* m
     return cudaGetLastError();
 }
 cudaError_t launch_ktab(double nu, double u0, double du, int n, double* tab, cudaStream_t s) {
-    k_ktab<<<(n + 127) / 128, 128, 0, s>>>(nu, u0, du, n, tab);
+    k_ktab<<<(n + 3) / 4, 128, 0, s>>>(nu, u0, du, n, tab);      // four entries per block
     return cudaGetLastError();
 }
 cudaError_t launch_tables(int N, double s_lo1, double s_lo2, double h, double* E1d, double* E2d, float* E1f,
