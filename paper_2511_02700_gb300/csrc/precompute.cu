@@ -106,6 +106,47 @@ __global__ void k_ktab(double nu, double u0, double du, int n, double* tab) {
     if (lane == 0) tab[i] = log((0.5 + s) * h);
 }
 
+// R_II cells up to this ||z_l||_inf / h (the 10-point rule, 100 nodes) take a
+// warp each (k_weights_near); the cells beyond, with 36 or 16 nodes, are
+// numerous enough to fill the GPU one thread per cell, at full lane use
+__host__ __device__ __forceinline__ int weights_warp_zone(const WeightJob& j) { return j.M2 < 8 ? j.M2 : 8; }
+
+// the R_II cell integral at node (a, b) of its product rule (eq. 3.5 with the
+// |z|^2 factor of the modified midpoint rule)
+__device__ __forceinline__ double rii_node(const LevyParams& L, double c1, double c2, double h, const double* gx,
+                                           const double* gw, int a, int b) {
+    const double za = c1 + 0.5 * h * gx[a], zb = c2 + 0.5 * h * gx[b];
+    return gw[a] * gw[b] * (za * za + zb * zb) * levy_density(L, za, zb);
+}
+
+// R_II cells with ||z_l||_inf / h in (2, weights_warp_zone]: one warp per cell of
+// the square around the origin, the rule's 100 nodes strided over the lanes
+// (at GB300's FP64 rate a cell's 100 density evaluations on one thread are the
+// tail of k_weights otherwise); the lane sums are added in a fixed order
+__global__ void k_weights_near(LevyParams L, WeightJob j, double* omega) {
+    const int Z = weights_warp_zone(j);
+    const int side = 2 * Z;
+    const int wcell = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (wcell >= side * side) return;                 // uniform across the warp
+    const int q2 = wcell / side, q1 = wcell - q2 * side;
+    const int l1 = q1 - Z, l2 = q2 - Z;               // cells l = -Z .. Z - 1 around the origin
+    const double inf = fmax(fabs(l1 + 0.5), fabs(l2 + 0.5));
+    if (inf <= 2.0 || inf > (double)Z) return;
+    const int n = j.n_near;                           // inf <= 8: the 10-point rule
+    const double* gx = j.gl_near_x;
+    const double* gw = j.gl_near_w;
+    const double c1 = (l1 + 0.5) * j.h, c2 = (l2 + 0.5) * j.h;
+    double acc = 0.0;
+    for (int k = lane; k < n * n; k += 32) acc += rii_node(L, c1, c2, j.h, gx, gw, k / n, k - (k / n) * n);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+        const int N = j.N;
+        omega[(size_t)(l2 + N / 2) * N + (l1 + N / 2)] = acc * 0.25 * j.h * j.h / (c1 * c1 + c2 * c2);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // weights, eq. 3.5; one thread per cell, per-block partial sums of
 // (w, w (e^{z1} - 1), w (e^{z2} - 1)) for the deterministic final reduction
@@ -121,6 +162,8 @@ __global__ void k_weights(LevyParams L, WeightJob j, double* omega, double* part
         const double inf = fmax(fabs(l1 + 0.5), fabs(l2 + 0.5));   // ||z_l||_inf / h
         if (inf <= 2.0) {
             w = 0.0;                                               // R_I
+        } else if (inf <= (double)weights_warp_zone(j)) {
+            w = omega[cell];                                       // R_II near the origin: k_weights_near
         } else if (inf <= (double)j.M2) {                          // R_II
             // Gauss-Legendre order by distance from the singular origin (in
             // cells): 10 up to 8 cells, 6 up to 24 cells (or on coarse grids),
@@ -410,6 +453,10 @@ cudaError_t launch_weights(const LevyParams& L, const WeightJob& j, double* omeg
     const int cells = j.N * j.N;
     const int nb = (cells + 255) / 256;
     *nblocks = nb;
+    const int side = 2 * weights_warp_zone(j);
+    k_weights_near<<<(side * side + 7) / 8, 256, 0, s>>>(L, j, omega);       // eight cells per block
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     k_weights<<<nb, 256, 0, s>>>(L, j, omega, partials);
     return cudaGetLastError();
 }
