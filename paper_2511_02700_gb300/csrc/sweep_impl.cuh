@@ -1183,10 +1183,8 @@ __global__ void k_explicit_jobs(const PrepArgs<R>* __restrict__ arr) {
 }
 
 template <typename R, int NTAP>
-__device__ __forceinline__ void prep_body(const PrepArgs<R>& a) {
+__device__ __forceinline__ void prep_node(const PrepArgs<R>& a, int m1, int m2) {
     const int N = a.g.N;
-    const int m1 = blockIdx.x * blockDim.x + threadIdx.x;
-    const int m2 = blockIdx.y * blockDim.y + threadIdx.y;
     if (m1 > N || m2 > N) return;
     const int ld = a.g.ldS, ldR = a.g.ldR;
     const size_t idx = (size_t)m2 * ld + m1;
@@ -1258,6 +1256,135 @@ __device__ __forceinline__ void prep_body(const PrepArgs<R>& a) {
         e = R(-6) * st_diff(a.V[1][idx], v) + R(4) * st_diff(a.V[2][idx], v) - st_diff(a.V[3][idx], v);
     }
     a.Y[idx] = st_add(v, e);
+}
+
+// NC consecutive values of a row from position q (q's parity fixed per launch):
+// 16-byte loads of state pairs (8-byte loads of R pairs) where aligned
+template <int NC, int C>
+__device__ __forceinline__ void load_pairs(const float2* row, int q, float2* v) {
+    if constexpr (C + 1 < NC) {
+        const float4 t = *reinterpret_cast<const float4*>(row + q + C);
+        v[C] = make_float2(t.x, t.y);
+        v[C + 1] = make_float2(t.z, t.w);
+        load_pairs<NC, C + 2>(row, q, v);
+    } else if constexpr (C < NC) {
+        v[C] = row[q + C];
+    }
+}
+template <int NC, int C>
+__device__ __forceinline__ void load_pairs(const float* row, int q, float* v) {
+    if constexpr (C + 1 < NC) {
+        const float2 t = *reinterpret_cast<const float2*>(row + q + C);
+        v[C] = t.x;
+        v[C + 1] = t.y;
+        load_pairs<NC, C + 2>(row, q, v);
+    } else if constexpr (C < NC) {
+        v[C] = row[q + C];
+    }
+}
+template <int NC, typename T>
+__device__ __forceinline__ void load_run(const T* row, int q, T* v) {
+    if (q & 1) {
+        v[0] = row[q];
+        load_pairs<NC, 1>(row, q, v);
+    } else {
+        load_pairs<NC, 0>(row, q, v);
+    }
+}
+
+// FP32-bulk: the interior nodes (m1, m2) and (m1 + 1, m2), m1 even, from one
+// window of NTAP rows by NTAP + 1 columns (the same arithmetic per node as
+// prep_node's interior path).  False, with nothing written, when a node is not
+// interior or a tap leaves the interior.
+template <int NTAP>
+__device__ __forceinline__ bool prep_pair_f32(const PrepArgs<float>& a, int m1, int m2) {
+    const int N = a.g.N;
+    const int q0 = m1 + a.o1, r0 = m2 + a.o2;
+    if (!(m1 >= 2 && m1 + 1 <= N - 1 && m2 >= 1 && m2 <= N - 1 && q0 >= 1 && q0 + NTAP <= N - 1 && r0 >= 1 &&
+          r0 + NTAP - 1 <= N - 1))
+        return false;
+    constexpr int NC = NTAP + 1;
+    const int ld = a.g.ldS, ldR = a.g.ldR;
+    const size_t idx = (size_t)m2 * ld + m1;
+    const float2* V = a.V[0];
+    const float4 vp = *reinterpret_cast<const float4*>(V + idx);
+    const float2 v0 = make_float2(vp.x, vp.y), v1 = make_float2(vp.z, vp.w);
+    const bool expl = a.htm != 0.f;
+    float czm0 = 0.f, czm1 = 0.f;
+    if (expl) {
+        const float2 c = *reinterpret_cast<const float2*>(a.cz + (size_t)m2 * ldR + m1);
+        czm0 = c.x;
+        czm1 = c.y;
+    }
+    float w1[NTAP], w2[NTAP];
+#pragma unroll
+    for (int c = 0; c < NTAP; ++c) {
+        w1[c] = a.w1[c];
+        w2[c] = a.w2[c];
+    }
+    float corr0 = czm0, corr1 = czm1;
+#pragma unroll
+    for (int b = 0; b < NTAP; ++b) {
+        float2 vv[NC];
+        float cc[NC];
+        load_run<NC>(V + (size_t)(r0 + b) * ld, q0, vv);
+        if (expl) {
+            load_run<NC>(a.cz + (size_t)(r0 + b) * ldR, q0, cc);
+        } else {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) cc[c] = 0.f;
+        }
+        float row0 = 0.f, row1 = 0.f;
+#pragma unroll
+        for (int c = 0; c < NTAP; ++c) {
+            row0 += w1[c] * (st_diff(vv[c], v0) + cc[c] - czm0);
+            row1 += w1[c] * (st_diff(vv[c + 1], v1) + cc[c + 1] - czm1);
+        }
+        corr0 += w2[b] * row0;
+        corr1 += w2[b] * row1;
+    }
+    const float2 W0 = st_add(v0, corr0), W1 = st_add(v1, corr1);
+    *reinterpret_cast<float4*>(a.W + idx) = make_float4(W0.x, W0.y, W1.x, W1.y);
+    float e0 = 0.f, e1 = 0.f;
+    auto hist = [&](int k, float2& h0, float2& h1) {
+        const float4 t = *reinterpret_cast<const float4*>(a.V[k] + idx);
+        h0 = make_float2(t.x, t.y);
+        h1 = make_float2(t.z, t.w);
+    };
+    if (a.hcount == 2) {
+        float2 p0, p1;
+        hist(1, p0, p1);
+        e0 = -st_diff(p0, v0);
+        e1 = -st_diff(p1, v1);
+    } else if (a.hcount == 3) {
+        float2 p0, p1, q0v, q1v;
+        hist(1, p0, p1);
+        hist(2, q0v, q1v);
+        e0 = -3.f * st_diff(p0, v0) + st_diff(q0v, v0);
+        e1 = -3.f * st_diff(p1, v1) + st_diff(q1v, v1);
+    } else if (a.hcount >= 4) {
+        float2 p0, p1, q0v, q1v, u0, u1;
+        hist(1, p0, p1);
+        hist(2, q0v, q1v);
+        hist(3, u0, u1);
+        e0 = -6.f * st_diff(p0, v0) + 4.f * st_diff(q0v, v0) - st_diff(u0, v0);
+        e1 = -6.f * st_diff(p1, v1) + 4.f * st_diff(q1v, v1) - st_diff(u1, v1);
+    }
+    const float2 Y0 = st_add(v0, e0), Y1 = st_add(v1, e1);
+    *reinterpret_cast<float4*>(a.Y + idx) = make_float4(Y0.x, Y0.y, Y1.x, Y1.y);
+    return true;
+}
+
+// each thread prepares the nodes (2 tx, m2) and (2 tx + 1, m2)
+template <typename R, int NTAP>
+__device__ __forceinline__ void prep_body(const PrepArgs<R>& a) {
+    const int m1 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int m2 = blockIdx.y * blockDim.y + threadIdx.y;
+    if constexpr (sizeof(R) == 4) {
+        if (prep_pair_f32<NTAP>(a, m1, m2)) return;
+    }
+    prep_node<R, NTAP>(a, m1, m2);
+    prep_node<R, NTAP>(a, m1 + 1, m2);
 }
 
 template <typename R, int NTAP>
@@ -1702,8 +1829,9 @@ cudaError_t launch_prep_jobs(const PrepArgs<R>& a0, const PrepArgs<R>* arr, int 
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    if (a0.nt == 2) k_prep_jobs<R, 2><<<grd, blk, 0, s>>>(arr);
-    else k_prep_jobs<R, 4><<<grd, blk, 0, s>>>(arr);
+    const dim3 grp((a0.g.N + 1 + 63) / 64, (a0.g.N + 1 + 7) / 8, K);      // two nodes per thread
+    if (a0.nt == 2) k_prep_jobs<R, 2><<<grp, blk, 0, s>>>(arr);
+    else k_prep_jobs<R, 4><<<grp, blk, 0, s>>>(arr);
     return cudaGetLastError();
 }
 
@@ -1769,13 +1897,14 @@ template <typename R>
 cudaError_t launch_prep(const PrepArgs<R>& a, cudaStream_t s) {
     const dim3 blk(32, 8);
     const dim3 grd((a.g.N + 1 + 31) / 32, (a.g.N + 1 + 7) / 8);
+    const dim3 grp((a.g.N + 1 + 63) / 64, (a.g.N + 1 + 7) / 8);     // two nodes per thread
     if (a.htm != R(0)) {
         k_explicit<R><<<grd, blk, 0, s>>>(a);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    if (a.nt == 2) k_prep<R, 2><<<grd, blk, 0, s>>>(a);
-    else k_prep<R, 4><<<grd, blk, 0, s>>>(a);
+    if (a.nt == 2) k_prep<R, 2><<<grp, blk, 0, s>>>(a);
+    else k_prep<R, 4><<<grp, blk, 0, s>>>(a);
     return cudaGetLastError();
 }
 template <typename R>
