@@ -101,9 +101,12 @@ def test_plain_fp64_128_workload():
     assert stats.steps_done == w.steps
 
 
-@pytest.mark.parametrize("n,alpha", [(64, 0.25), (128, 0.5)])
-def test_fp32_bulk_solve_matches_oracle(n, alpha):
-    w = Workload("f", n=n, steps=n // 4, alpha=alpha, tol=1e-10, precision="fp32")
+@pytest.mark.parametrize("n,alpha,sl", [(64, 0.25, 3), (128, 0.5, 3), (64, 0.5, 1)])
+def test_fp32_bulk_solve_matches_oracle(n, alpha, sl):
+    """FP32-bulk solves against the FP64 oracle, with the cubic and the linear
+    departure interpolation (the preparation's two-node windows of 4 x 5 and
+    2 x 3 taps)."""
+    w = Workload("f", n=n, steps=n // 4, alpha=alpha, tol=1e-10, precision="fp32", sl_order=sl)
     s = gpu_solver(w)
     price, V, stats, st = s.solve(values=True)
     V = V.cpu().numpy()
